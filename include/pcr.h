@@ -1,0 +1,224 @@
+/*
+ * pcr.h: C interface of a CUDA library (sm_103a) for compute-based point
+ * cloud rendering, after Schuetz, Kerbl and Wimmer, "Rendering Point Clouds
+ * with Compute Shaders and Vertex Order Optimization" (EGSR 2021).
+ *
+ * What it computes:
+ *  - Sec. 3.1: every point is transformed by a 4x4 matrix, mapped to a pixel
+ *    and written with a 64-bit atomic minimum of (depth bits << 32 | point
+ *    index) into a key buffer with one word per pixel; a resolve pass turns
+ *    keys into colours.
+ *  - Sec. 3.2 to 3.4: the same result with an early depth test, a warp-wide
+ *    reduction, or full warp deduplication in front of the atomic.
+ *  - Sec. 3.5: the high-quality variant: a depth pass, then a colour pass
+ *    that sums the colours of all points within a depth band of the nearest
+ *    one, then a resolve that averages.
+ *  - Sec. 4: Morton order and shuffled Morton order (batches of 128 points)
+ *    as a one-time reordering of the point buffer.
+ *
+ * Conventions, for every entry point:
+ *  - Every call returns a pcr_status.  No C++ exception crosses this
+ *    interface and no call aborts the process.
+ *  - The caller owns all device memory.  The library borrows pointers for
+ *    the duration of the work it launches and never frees them.  Apart from
+ *    the context itself (host memory) the library allocates nothing.
+ *  - Calls that launch GPU work are asynchronous on the context's stream
+ *    (see pcr_set_stream).  Arguments are checked before anything is
+ *    launched; a call that returns PCR_ERR_ARG or PCR_ERR_WORKSPACE has
+ *    launched nothing.
+ *  - A context is used from one host thread at a time.
+ *
+ * Point record: 16 bytes, 16-byte aligned: float x, y, z, then uint32 rgba
+ * with r in the low byte (Sec. 5 gives the same size: 796M points in
+ * 12.7 GB).  Indices are 32-bit, so a cloud holds at most 2^32 - 1 points.
+ */
+#ifndef PCR_H
+#define PCR_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PCR_API __attribute__((visibility("default")))
+#else
+#define PCR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pcr_status;
+
+enum {
+    PCR_OK = 0,
+    PCR_ERR_ARG = -1,          /* bad argument; nothing was launched */
+    PCR_ERR_CUDA = -2,         /* a CUDA call failed (no device, launch error, ...) */
+    PCR_ERR_WORKSPACE = -3,    /* workspace missing or too small; nothing was launched */
+    PCR_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
+    PCR_ERR_UNSUPPORTED = -5   /* valid request this build does not provide */
+};
+
+/* Render variants (Sec. 3.1 to 3.4, and the method list of Sec. 5).  Every
+ * variant except PCR_VARIANT_JUST_SET leaves a bit-identical key buffer. */
+enum {
+    PCR_VARIANT_ATOMICMIN = 0,     /* Sec. 3.1: one 64-bit atomicMin per visible point */
+    PCR_VARIANT_EARLYZ = 1,        /* Sec. 3.2: read the pixel first, atomic only if smaller */
+    PCR_VARIANT_DEDUP = 2,         /* Sec. 3.4: one atomic per distinct pixel per warp */
+    PCR_VARIANT_DEDUP_EARLYZ = 3,  /* Sec. 3.4 with the early test ("dedup" in Sec. 5) */
+    PCR_VARIANT_REDUCE = 4,        /* Sec. 3.3: all-equal warp reduction, else pairwise */
+    PCR_VARIANT_REDUCE_EARLYZ = 5, /* Sec. 3.3 with the early test */
+    PCR_VARIANT_JUST_SET = 6       /* Sec. 5 "just-set": non-atomic store, no depth test;
+                                      a speed floor, not a correct renderer */
+};
+
+enum {
+    PCR_RESOLVE_BASIC = 0,  /* Sec. 3.1: key buffer -> colour of the winning point */
+    PCR_RESOLVE_HQ = 1      /* Sec. 3.5: colour sums -> truncating average */
+};
+
+enum {
+    PCR_CLEAR_KEYS = 1,     /* key buffer to all ones (empty) */
+    PCR_CLEAR_HQ = 2        /* HQ depth to +inf bits, HQ sums to 0 */
+};
+
+enum {
+    PCR_ORDER_MORTON = 0,            /* Sec. 5 "Morton" */
+    PCR_ORDER_MORTON_SHUFFLE128 = 1, /* Sec. 4 and Sec. 5 "Shuffled Morton" */
+    PCR_ORDER_SHUFFLE = 2            /* Sec. 5 "Shuffled" */
+};
+
+typedef struct pcr_ctx pcr_ctx;
+
+/* Create a context bound to CUDA device `device`.  Host allocation only.
+ * Errors: PCR_ERR_ARG if out is NULL; PCR_ERR_CUDA if the device does not
+ * exist or cannot be queried. */
+PCR_API pcr_status pcr_create(pcr_ctx **out, int device);
+
+/* Destroy a context (NULL is accepted).  Does not synchronise its stream. */
+PCR_API pcr_status pcr_destroy(pcr_ctx *ctx);
+
+/* Use `cuda_stream` (a cudaStream_t, e.g. PyTorch's current stream) for all
+ * later work of this context.  NULL selects the legacy default stream.  The
+ * library never synchronises a stream except in pcr_synchronize,
+ * pcr_download and pcr_last_device_error. */
+PCR_API pcr_status pcr_set_stream(pcr_ctx *ctx, void *cuda_stream);
+
+/* Borrow a device point buffer of n records (16-byte aligned, n < 2^32) for
+ * the following render and resolve calls.  No copy is made.  n = 0 is
+ * allowed (renders then write nothing).  Errors: PCR_ERR_ARG on a NULL or
+ * misaligned pointer with n > 0, or n >= 2^32. */
+PCR_API pcr_status pcr_upload_points(pcr_ctx *ctx, const void *dev_points, uint64_t n);
+
+/* Copy n records from host memory into the caller's device buffer
+ * `dev_points` (asynchronous on the stream; pinned host memory makes it
+ * truly asynchronous), then borrow it as pcr_upload_points does.  Same
+ * errors as pcr_upload_points, plus PCR_ERR_CUDA if the copy fails. */
+PCR_API pcr_status pcr_upload_points_from_host(pcr_ctx *ctx, void *dev_points, const void *host_points, uint64_t n);
+
+/* Sec. 3.1 "worldViewProj": a row-major 4x4 float matrix with
+ * clip = M (x, y, z, 1)^T.  Only rows 0, 1 and 3 are used: clip.w is the
+ * linear depth and there is no near or far plane test.  The matrix is copied.
+ * Errors: PCR_ERR_ARG if m is NULL. */
+PCR_API pcr_status pcr_set_matrix(pcr_ctx *ctx, const float m[16]);
+
+/* Framebuffer size in pixels, 1..16384 each.  Pixel p = x + y * width with
+ * row 0 at the bottom.  Errors: PCR_ERR_ARG out of range. */
+PCR_API pcr_status pcr_set_viewport(pcr_ctx *ctx, int width, int height);
+
+/* Borrow the caller's framebuffer storage, each sized for the viewport:
+ *   dev_keys      uint64[width*height]  (Sec. 3.1 key buffer), 8-byte aligned
+ *   dev_hq_depth  uint32[width*height]  (Sec. 3.5 depth buffer), 4-byte aligned
+ *   dev_hq_rg     uint64[width*height]  (Sec. 3.5 r << 32 | g sums)
+ *   dev_hq_ba     uint64[width*height]  (Sec. 3.5 b << 32 | count sums)
+ * Any may be NULL if the matching render mode is not used; a render that
+ * needs a NULL buffer returns PCR_ERR_ARG.  The buffers must not overlap. */
+PCR_API pcr_status pcr_set_framebuffer(pcr_ctx *ctx, void *dev_keys, void *dev_hq_depth, void *dev_hq_rg,
+                               void *dev_hq_ba);
+
+/* Start a frame (Sec. 3, Fig. "pipeline": buffers are reset before the
+ * geometry passes).  `what` is a bit set of PCR_CLEAR_KEYS and PCR_CLEAR_HQ.
+ * Errors: PCR_ERR_ARG for an empty or unknown bit set, a missing viewport or
+ * a missing buffer. */
+PCR_API pcr_status pcr_clear(pcr_ctx *ctx, int what);
+
+/* Sec. 3.1 to 3.4: render the borrowed points into the key buffer.  With
+ * clear != 0 the key buffer is first set to all ones (empty); with clear == 0
+ * the points are merged into what the buffer holds (a minimum, so several
+ * calls over parts of a cloud give the same buffer as one call over all of
+ * it, provided index payloads do not collide).  Key of point i:
+ * float_bits(w) << 32 | i.  Errors: PCR_ERR_ARG for an unknown variant, a
+ * missing matrix, viewport or key buffer. */
+PCR_API pcr_status pcr_render_basic(pcr_ctx *ctx, int variant, int clear);
+
+/* Sec. 3.5: depth pass (32-bit minimum of float_bits(w)), then colour pass:
+ * each visible point with w <= float(depth[p]) * depth_factor (float32
+ * product; the paper uses 1.01) adds (r << 32 | g) to rg[p] and
+ * (b << 32 | 1) to ba[p] with 64-bit integer adds.  clear != 0 first sets
+ * depth to +inf and the sums to 0.  `variant` selects the form of the depth
+ * pass (ATOMICMIN, EARLYZ, DEDUP, DEDUP_EARLYZ); the DEDUP forms also sum the
+ * colours of same-pixel points within a warp before the adds.  Results do
+ * not depend on the variant.  Channel sums are exact while each stays below
+ * 2^32 (about 16.8M points per pixel at full intensity).  Errors: PCR_ERR_ARG
+ * for a bad variant or depth_factor (not finite or <= 0), missing matrix,
+ * viewport or HQ buffers. */
+PCR_API pcr_status pcr_render_hq(pcr_ctx *ctx, float depth_factor, int variant, int clear);
+
+/* Screen pass, writing uint32 rgba per pixel into dev_rgba_out
+ * (4-byte aligned, width*height words).
+ *   PCR_RESOLVE_BASIC (Sec. 3.1): the rgba word of the point whose index the
+ *     key holds; background_rgba where the key is all ones or names no point
+ *     of the borrowed cloud.
+ *   PCR_RESOLVE_HQ (Sec. 3.5): r = (rg >> 32) / count, g = (rg & 0xffffffff)
+ *     / count, b = (ba >> 32) / count with truncating division, each clamped
+ *     to 255, alpha 255; background_rgba where count is 0.
+ * Errors: PCR_ERR_ARG for an unknown mode, NULL output or missing buffers. */
+PCR_API pcr_status pcr_resolve(pcr_ctx *ctx, int mode, void *dev_rgba_out, uint32_t background_rgba);
+
+/* Copy `bytes` from device memory to host memory on the context's stream and
+ * wait for it.  Errors: PCR_ERR_ARG on NULL pointers with bytes > 0,
+ * PCR_ERR_CUDA if the copy fails. */
+PCR_API pcr_status pcr_download(pcr_ctx *ctx, void *host_dst, const void *dev_src, uint64_t bytes);
+
+/* Wait for all work queued on the context's stream.  Reports PCR_ERR_CUDA
+ * if any of it failed. */
+PCR_API pcr_status pcr_synchronize(pcr_ctx *ctx);
+
+/* Bytes of device workspace pcr_reorder_morton_shuffle128 needs for n
+ * points (host-only computation, no CUDA call).  Errors: PCR_ERR_ARG if bytes
+ * is NULL or n >= 2^32. */
+PCR_API pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t *bytes);
+
+/* Sec. 4 and Sec. 5: reorder a device point buffer in place.
+ *   PCR_ORDER_MORTON: stable sort by a 30-bit Morton code (10 bits per axis;
+ *     x in bit 3i+2, y in 3i+1, z in 3i) over the cube whose corner is the
+ *     minimum of the bounds and whose side is their largest extent; a
+ *     coordinate quantises to floor((v - min) * (1024 / extent)) clamped to
+ *     [0, 1023]; a zero or non-finite extent gives every point code 0.
+ *   PCR_ORDER_MORTON_SHUFFLE128: the Morton order cut into batches of 128
+ *     points (the last may be shorter); batch b gets key = high 32 bits of
+ *     output b of SplitMix64 seeded with `seed`; batches are stably sorted by
+ *     key and keep their inner order.
+ *   PCR_ORDER_SHUFFLE: point i gets key = high 32 bits of SplitMix64 output
+ *     i; points are stably sorted by key.
+ * dev_points: n records, 16-byte aligned.  dev_workspace: at least the
+ * pcr_reorder_workspace_size bytes, 256-byte aligned; its contents are
+ * scratch.  dev_perm_out: NULL or uint32[n], receives perm[new] = old.
+ * Errors: PCR_ERR_ARG for a bad mode, pointer or n; PCR_ERR_WORKSPACE if
+ * workspace_bytes is too small or the workspace is NULL. */
+PCR_API pcr_status pcr_reorder_morton_shuffle128(pcr_ctx *ctx, void *dev_points, uint64_t n, uint64_t seed, int mode,
+                                         void *dev_workspace, uint64_t workspace_bytes, uint32_t *dev_perm_out);
+
+/* Static, human-readable name of a status code. */
+PCR_API const char *pcr_status_string(pcr_status status);
+
+/* Read and clear the device-side error word of the context's device
+ * (synchronises the stream).  Bit 0: a resolve found a key naming a point
+ * index outside the borrowed cloud (the pixel took the background colour).
+ * *code is 0 when nothing was reported.  Errors: PCR_ERR_ARG if code is NULL,
+ * PCR_ERR_CUDA if the read fails. */
+PCR_API pcr_status pcr_last_device_error(pcr_ctx *ctx, uint32_t *code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCR_H */

@@ -1,0 +1,39 @@
+// Host-side launchers shared between the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace pcr {
+
+// Launch geometry: persistent grids sized from the SM count.
+struct Device {
+  int id = 0;
+  int num_sms = 0;
+};
+
+cudaError_t launch_fill_u64(unsigned long long* p, uint64_t count, unsigned long long value, cudaStream_t s,
+                            const Device& d);
+cudaError_t launch_clear_hq(uint32_t* depth, unsigned long long* rg, unsigned long long* ba, uint64_t npx,
+                            cudaStream_t s, const Device& d);
+cudaError_t launch_render_basic(int variant, const uint4* pts, uint32_t n, const ViewParams& v,
+                                unsigned long long* keys, cudaStream_t s, const Device& d);
+cudaError_t launch_hq_depth(int variant, const uint4* pts, uint32_t n, const ViewParams& v, uint32_t* depth,
+                            cudaStream_t s, const Device& d);
+cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor,
+                            const uint32_t* depth, unsigned long long* rg, unsigned long long* ba, cudaStream_t s,
+                            const Device& d);
+cudaError_t launch_resolve_basic(const unsigned long long* keys, uint64_t npx, const uint4* pts, uint32_t n,
+                                 uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
+cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
+                              uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
+cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
+
+// Vertex order (reorder.cu).
+uint64_t reorder_workspace_bytes(uint64_t n);
+cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void* workspace, uint32_t* perm_out,
+                           cudaStream_t s, const Device& d);
+
+}  // namespace pcr

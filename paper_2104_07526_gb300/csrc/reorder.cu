@@ -1,0 +1,484 @@
+// Vertex-order kernels (Sec. 4, and the orderings listed in Sec. 5):
+// bounds, 30-bit Morton codes, a stable LSD radix sort of (32-bit key,
+// 32-bit index) pairs, the 128-point batch shuffle and the record gather.
+//
+// Radix sort: 8-bit digits, one pass per digit, three steps per pass:
+//   1. k_sort_hist: per tile of 8192 keys, count each digit.
+//   2. exclusive scan of the counts in digit-major order, which gives every
+//      (digit, tile) its first output slot;
+//   3. k_sort_scatter: per tile, rank each key among the earlier keys of its
+//      tile with the same digit (rounds of 256 keys in index order; inside a
+//      warp by match/popc, across warps by a shared prefix) and write it.
+// Ranks follow index order, so each pass, and the sort, is stable.
+#include <cstdint>
+
+#include "../../include/pcr.h"
+#include "common.cuh"
+#include "launch.h"
+
+namespace pcr {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortRounds = 32;
+constexpr uint32_t kTile = kSortThreads * kSortRounds;
+constexpr int kDigitBits = 8;
+constexpr int kRadix = 1 << kDigitBits;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr uint32_t kScanSeg = kScanThreads * kScanItems;
+constexpr uint32_t kBatch = 128;  // Sec. 4: batches of 128 points
+
+static_assert(kRadix == kSortThreads, "one digit per thread in the sort kernels");
+
+uint64_t align_up(uint64_t v) { return (v + 255) & ~uint64_t(255); }
+
+uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Workspace layout; every region starts on a 256-byte boundary.
+struct Layout {
+  uint64_t pts_copy, keys0, keys1, vals0, vals1, counts, partials, bkeys0, bkeys1, bvals0, bvals1, misc, total;
+};
+
+Layout layout(uint64_t n) {
+  const uint64_t nb = ceil_div(n, kBatch);
+  const uint64_t tiles = ceil_div(n > nb ? n : nb, kTile);
+  const uint64_t count_words = kRadix * (tiles > 0 ? tiles : 1);
+  Layout l{};
+  uint64_t off = 0;
+  auto take = [&](uint64_t bytes) {
+    const uint64_t at = off;
+    off += align_up(bytes > 0 ? bytes : 1);
+    return at;
+  };
+  l.pts_copy = take(16 * n);
+  l.keys0 = take(4 * n);
+  l.keys1 = take(4 * n);
+  l.vals0 = take(4 * n);
+  l.vals1 = take(4 * n);
+  l.counts = take(4 * count_words);
+  l.partials = take(4 * ceil_div(count_words, kScanSeg));
+  l.bkeys0 = take(4 * nb);
+  l.bkeys1 = take(4 * nb);
+  l.bvals0 = take(4 * nb);
+  l.bvals1 = take(4 * nb);
+  l.misc = take(64);
+  l.total = off;
+  return l;
+}
+
+// --- bounds -------------------------------------------------------------------
+
+// Order-preserving map from float to uint32 (NaN excluded by the caller).
+__device__ __forceinline__ uint32_t float_order(float f) {
+  const uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float order_float(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
+}
+
+__global__ void k_bounds_init(uint32_t* misc) {
+  if (threadIdx.x < 3) {
+    misc[threadIdx.x] = 0xFF800000u;     // order of +inf: identity for min
+    misc[3 + threadIdx.x] = 0x007FFFFFu; // order of -inf: identity for max
+  }
+}
+
+// Per axis min and max over non-NaN coordinates.  -0 is folded into +0 (the
+// codes do not depend on the sign of a zero bound).
+__global__ void __launch_bounds__(256) k_bounds(const uint4* __restrict__ pts, uint32_t n, uint32_t* misc) {
+  uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+  uint32_t hi[3] = {0u, 0u, 0u};
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
+    const uint4 r = __ldcs(pts + i);
+    const float v[3] = {__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (v[a] == v[a]) {
+        const uint32_t o = float_order(__fadd_rn(v[a], 0.0f));
+        lo[a] = min(lo[a], o);
+        hi[a] = max(hi[a], o);
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(kFullMask, lo[a]);
+    hi[a] = __reduce_max_sync(kFullMask, hi[a]);
+  }
+  if (lane_id() == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (lo[a] != 0xFFFFFFFFu) atomicMin(misc + a, lo[a]);
+      if (hi[a] != 0u) atomicMax(misc + 3 + a, hi[a]);
+    }
+  }
+}
+
+// --- codes --------------------------------------------------------------------
+
+// Spread the low 10 bits of v so bit i lands on bit 3i.
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t quantise(float v, float lo, float scale) {
+  const float f = floorf(__fmul_rn(__fsub_rn(v, lo), scale));
+  if (!(f >= 0.0f)) return 0u;
+  if (f >= 1023.0f) return 1023u;
+  return static_cast<uint32_t>(f);
+}
+
+// Sec. 5: Morton code over the cube with the bounds' minimum corner and the
+// largest extent as side, 10 levels.
+__global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, uint32_t n,
+                                                const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys,
+                                                uint32_t* __restrict__ vals) {
+  const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
+  const float hi[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
+  float ext = __fsub_rn(hi[0], lo[0]);
+  const float ey = __fsub_rn(hi[1], lo[1]);
+  const float ez = __fsub_rn(hi[2], lo[2]);
+  if (ey > ext) ext = ey;
+  if (ez > ext) ext = ez;
+  const bool degenerate = !(ext > 0.0f) || !(ext < __int_as_float(kInfBits));
+  const float scale = degenerate ? 0.0f : __fdiv_rn(1024.0f, ext);
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
+    uint32_t code = 0;
+    if (!degenerate) {
+      const uint4 r = __ldcs(pts + i);
+      code = (spread3(quantise(__uint_as_float(r.x), lo[0], scale)) << 2) |
+             (spread3(quantise(__uint_as_float(r.y), lo[1], scale)) << 1) |
+             spread3(quantise(__uint_as_float(r.z), lo[2], scale));
+    }
+    keys[i] = code;
+    vals[i] = static_cast<uint32_t>(i);
+  }
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output k of the generator
+// seeded with `seed` mixes the state seed + (k + 1) * 0x9E3779B97F4A7C15.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Keys for the random orders: the high half of SplitMix64 output i.
+__global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t seed, uint32_t* __restrict__ keys,
+                                                     uint32_t* __restrict__ vals) {
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < count; i += gridDim.x * 256ull) {
+    keys[i] = static_cast<uint32_t>(splitmix64(seed, i) >> 32);
+    vals[i] = static_cast<uint32_t>(i);
+  }
+}
+
+// --- radix sort ---------------------------------------------------------------
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
+                                                            uint32_t* __restrict__ counts, uint32_t tiles) {
+  __shared__ uint32_t hist[kRadix];
+  hist[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile + threadIdx.x;
+  const uint32_t lane = lane_id();
+#pragma unroll 4
+  for (int r = 0; r < kSortRounds; ++r) {
+    const uint64_t i = base + static_cast<uint64_t>(r) * kSortThreads;
+    const bool ok = i < n;
+    const uint32_t d = ok ? (keys[i] >> shift) & (kRadix - 1) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(kFullMask, d);
+    if (ok && lane == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&hist[d], __popc(peers));
+  }
+  __syncthreads();
+  counts[static_cast<uint64_t>(threadIdx.x) * tiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                               uint32_t n, int shift,
+                                                               const uint32_t* __restrict__ offsets, uint32_t tiles) {
+  __shared__ uint32_t next[kRadix];                      // next free output slot per digit
+  __shared__ uint32_t slot[2][kSortWarps][kRadix];       // per-warp digit counts, then offsets
+  const uint32_t t = threadIdx.x;
+  const uint32_t lane = lane_id();
+  const uint32_t warp = t >> 5;
+  next[t] = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    slot[0][w][t] = 0;
+    slot[1][w][t] = 0;
+  }
+  __syncthreads();
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile + t;
+  const uint32_t below = (1u << lane) - 1u;
+  for (int r = 0; r < kSortRounds; ++r) {
+    const int p = r & 1;
+    const uint64_t i = base + static_cast<uint64_t>(r) * kSortThreads;
+    const bool ok = i < n;
+    uint32_t key = 0, val = 0, d = 0xFFFFFFFFu;
+    if (ok) {
+      key = kin[i];
+      val = vin[i];
+      d = (key >> shift) & (kRadix - 1);
+    }
+    const uint32_t peers = __match_any_sync(kFullMask, d);
+    const uint32_t rank = __popc(peers & below);
+    if (ok && rank == 0) slot[p][warp][d] = __popc(peers);
+    __syncthreads();
+    // digit t: turn this round's per-warp counts into output slots
+    uint32_t run = next[t];
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      const uint32_t c = slot[p][w][t];
+      slot[p][w][t] = run;
+      run += c;
+      slot[p ^ 1][w][t] = 0;
+    }
+    next[t] = run;
+    __syncthreads();
+    if (ok) {
+      const uint32_t pos = slot[p][warp][d] + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+  }
+}
+
+// --- exclusive scan (in place) ----------------------------------------------------
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total) {
+  __shared__ uint32_t warp_sums[NT / 32];
+  const uint32_t lane = lane_id();
+  const uint32_t warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFullMask, x, o);
+    if (lane >= static_cast<uint32_t>(o)) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < NT / 32 ? warp_sums[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFullMask, s, o);
+      if (lane >= static_cast<uint32_t>(o)) s += y;
+    }
+    if (lane < NT / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  total = warp_sums[NT / 32 - 1];
+  const uint32_t prefix = warp ? warp_sums[warp - 1] : 0u;
+  return prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ a, uint64_t len,
+                                                              uint32_t* __restrict__ partials) {
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanSeg + threadIdx.x;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads;
+    if (i < len) s += a[i];
+  }
+  s = __reduce_add_sync(kFullMask, s);
+  __shared__ uint32_t w[kScanThreads / 32];
+  if (lane_id() == 0) w[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int k = 0; k < kScanThreads / 32; ++k) t += w[k];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// One block of 1024 threads; thread t scans a contiguous run of partials.
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* __restrict__ partials, uint32_t count) {
+  const uint32_t per = (count + 1023) / 1024;
+  const uint64_t first = static_cast<uint64_t>(threadIdx.x) * per;
+  uint32_t local = 0;
+  for (uint32_t j = 0; j < per; ++j)
+    if (first + j < count) local += partials[first + j];
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<1024>(local, total);
+  for (uint32_t j = 0; j < per; ++j) {
+    if (first + j < count) {
+      const uint32_t v = partials[first + j];
+      partials[first + j] = run;
+      run += v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ a, uint64_t len,
+                                                            const uint32_t* __restrict__ partials) {
+  __shared__ uint32_t seg[kScanSeg];
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanSeg;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads + threadIdx.x;
+    seg[j * kScanThreads + threadIdx.x] = i < len ? a[i] : 0u;
+  }
+  __syncthreads();
+  uint32_t mine[kScanItems];
+  uint32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    mine[j] = seg[threadIdx.x * kScanItems + j];
+    sum += mine[j];
+  }
+  uint32_t total;
+  uint32_t run = block_exclusive_scan<kScanThreads>(sum, total) + partials[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    seg[threadIdx.x * kScanItems + j] = run;
+    run += mine[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads + threadIdx.x;
+    if (i < len) a[i] = seg[j * kScanThreads + threadIdx.x];
+  }
+}
+
+cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaStream_t s) {
+  const uint64_t blocks = ceil_div(len, kScanSeg);
+  k_scan_reduce<<<static_cast<unsigned>(blocks), kScanThreads, 0, s>>>(a, len, partials);
+  k_scan_partials<<<1, 1024, 0, s>>>(partials, static_cast<uint32_t>(blocks));
+  k_scan_down<<<static_cast<unsigned>(blocks), kScanThreads, 0, s>>>(a, len, partials);
+  return cudaGetLastError();
+}
+
+// Stable sort of count (key, value) pairs on the low key_bits bits.  The
+// result ends in buffer index `out` (0 or 1).
+cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
+                       uint32_t* partials, cudaStream_t s, int& out) {
+  out = 0;
+  if (count == 0) return cudaSuccess;
+  const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
+  for (int shift = 0; shift < key_bits; shift += kDigitBits) {
+    k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
+    cudaError_t e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
+    if (e != cudaSuccess) return e;
+    k_sort_scatter<<<tiles, kSortThreads, 0, s>>>(keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count, shift,
+                                                  counts, tiles);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    out ^= 1;
+  }
+  return cudaSuccess;
+}
+
+// --- shuffled Morton: batches -> permutation -------------------------------------
+
+// Position, in the sorted batch order, of the last (possibly short) batch.
+__global__ void k_find_last_batch(const uint32_t* __restrict__ order, uint32_t nb, uint32_t* misc) {
+  for (uint64_t t = blockIdx.x * 256ull + threadIdx.x; t < nb; t += gridDim.x * 256ull)
+    if (order[t] == nb - 1) misc[6] = static_cast<uint32_t>(t);
+}
+
+// perm[new] = old for the shuffled Morton order: output batch slot t holds
+// batch order[t] of the Morton order; slots after the short last batch start
+// (kBatch - last_size) earlier.
+__global__ void __launch_bounds__(256) k_batch_perm(const uint32_t* __restrict__ order,
+                                                    const uint32_t* __restrict__ morton, uint32_t n, uint32_t nb,
+                                                    const uint32_t* __restrict__ misc, uint32_t* __restrict__ perm) {
+  const uint32_t t_last = misc[6];
+  const uint32_t last_size = n - (nb - 1) * kBatch;
+  const uint64_t total = static_cast<uint64_t>(nb) * kBatch;
+  for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < total; j += gridDim.x * 256ull) {
+    const uint32_t t = static_cast<uint32_t>(j / kBatch);
+    const uint32_t k = static_cast<uint32_t>(j % kBatch);
+    const uint32_t b = order[t];
+    const uint32_t size = (b == nb - 1) ? last_size : kBatch;
+    if (k < size) {
+      const uint64_t start = static_cast<uint64_t>(t) * kBatch - (t > t_last ? (kBatch - last_size) : 0u);
+      perm[start + k] = morton[static_cast<uint64_t>(b) * kBatch + k];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, uint32_t n) {
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) dst[i] = __ldcs(src + i);
+}
+
+__global__ void __launch_bounds__(256) k_gather16(const uint4* __restrict__ src, const uint32_t* __restrict__ perm,
+                                                  uint4* __restrict__ dst, uint32_t* __restrict__ perm_out,
+                                                  uint32_t n) {
+  for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < n; j += gridDim.x * 256ull) {
+    const uint32_t p = perm[j];
+    dst[j] = src[p];
+    if (perm_out) perm_out[j] = p;
+  }
+}
+
+unsigned stream_grid(uint64_t count, const Device& d) {
+  const uint64_t need = ceil_div(count, 256);
+  const uint64_t cap = static_cast<uint64_t>(d.num_sms) * 8;
+  return static_cast<unsigned>(need < cap ? (need > 0 ? need : 1) : cap);
+}
+
+}  // namespace
+
+uint64_t reorder_workspace_bytes(uint64_t n) { return layout(n).total; }
+
+cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void* workspace, uint32_t* perm_out,
+                           cudaStream_t s, const Device& d) {
+  if (n == 0) return cudaSuccess;
+  const Layout l = layout(n);
+  char* ws = static_cast<char*>(workspace);
+  uint4* copy = reinterpret_cast<uint4*>(ws + l.pts_copy);
+  uint32_t* keys[2] = {reinterpret_cast<uint32_t*>(ws + l.keys0), reinterpret_cast<uint32_t*>(ws + l.keys1)};
+  uint32_t* vals[2] = {reinterpret_cast<uint32_t*>(ws + l.vals0), reinterpret_cast<uint32_t*>(ws + l.vals1)};
+  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + l.counts);
+  uint32_t* partials = reinterpret_cast<uint32_t*>(ws + l.partials);
+  uint32_t* misc = reinterpret_cast<uint32_t*>(ws + l.misc);
+  const unsigned grid = stream_grid(n, d);
+  cudaError_t e = cudaSuccess;
+  int out = 0;
+  if (mode == PCR_ORDER_SHUFFLE) {
+    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], vals[0]);
+    e = radix_sort(keys, vals, n, 32, counts, partials, s, out);
+  } else {
+    k_bounds_init<<<1, 32, 0, s>>>(misc);
+    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc);
+    k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], vals[0]);
+    e = radix_sort(keys, vals, n, 30, counts, partials, s, out);
+  }
+  if (e != cudaSuccess) return e;
+  uint32_t* perm = vals[out];
+  if (mode == PCR_ORDER_MORTON_SHUFFLE128) {
+    const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
+    uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
+    uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
+    k_random_keys<<<stream_grid(nb, d), 256, 0, s>>>(nb, seed, bkeys[0], bvals[0]);
+    int bout = 0;
+    e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout);
+    if (e != cudaSuccess) return e;
+    k_find_last_batch<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, misc);
+    uint32_t* shuffled = keys[out];  // the sorted codes are no longer needed
+    k_batch_perm<<<stream_grid(static_cast<uint64_t>(nb) * kBatch, d), 256, 0, s>>>(bvals[bout], perm, n, nb, misc,
+                                                                                 shuffled);
+    perm = shuffled;
+  }
+  k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
+  k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
+  return cudaGetLastError();
+}
+
+}  // namespace pcr

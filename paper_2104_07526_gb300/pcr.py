@@ -1,0 +1,262 @@
+"""Python binding of libpcr.so (include/pcr.h).
+
+Argument marshalling only: every function here has the name of a C entry
+point, turns tensors into device pointers, calls the library and raises
+PcrError on a non-zero status.  All rendering work runs in the library's CUDA
+kernels; there is no Python or CPU fallback.  If the library has not been
+built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpcr.so")
+
+PCR_OK, PCR_ERR_ARG, PCR_ERR_CUDA, PCR_ERR_WORKSPACE, PCR_ERR_TIMEOUT, PCR_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+
+PCR_VARIANT_ATOMICMIN = 0
+PCR_VARIANT_EARLYZ = 1
+PCR_VARIANT_DEDUP = 2
+PCR_VARIANT_DEDUP_EARLYZ = 3
+PCR_VARIANT_REDUCE = 4
+PCR_VARIANT_REDUCE_EARLYZ = 5
+PCR_VARIANT_JUST_SET = 6
+EXACT_VARIANTS = (0, 1, 2, 3, 4, 5)
+VARIANT_NAMES = {0: "atomicMin", 1: "early-z", 2: "dedup", 3: "dedup+early-z", 4: "reduce",
+                 5: "reduce+early-z", 6: "just-set"}
+
+PCR_RESOLVE_BASIC = 0
+PCR_RESOLVE_HQ = 1
+
+PCR_CLEAR_KEYS = 1
+PCR_CLEAR_HQ = 2
+
+PCR_ORDER_MORTON = 0
+PCR_ORDER_MORTON_SHUFFLE128 = 1
+PCR_ORDER_SHUFFLE = 2
+
+
+class PcrError(RuntimeError):
+    def __init__(self, status: int, call: str):
+        self.status = status
+        super().__init__(f"{call} failed: {pcr_status_string(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP, _U64, _U32, _INT, _FLT = C.c_void_p, C.c_uint64, C.c_uint32, C.c_int, C.c_float
+_SIGS = {
+    "pcr_create": [C.POINTER(_VP), _INT],
+    "pcr_destroy": [_VP],
+    "pcr_set_stream": [_VP, _VP],
+    "pcr_upload_points": [_VP, _VP, _U64],
+    "pcr_upload_points_from_host": [_VP, _VP, _VP, _U64],
+    "pcr_set_matrix": [_VP, C.POINTER(_FLT)],
+    "pcr_set_viewport": [_VP, _INT, _INT],
+    "pcr_set_framebuffer": [_VP, _VP, _VP, _VP, _VP],
+    "pcr_clear": [_VP, _INT],
+    "pcr_render_basic": [_VP, _INT, _INT],
+    "pcr_render_hq": [_VP, _FLT, _INT, _INT],
+    "pcr_resolve": [_VP, _INT, _VP, _U32],
+    "pcr_download": [_VP, _VP, _VP, _U64],
+    "pcr_synchronize": [_VP],
+    "pcr_reorder_workspace_size": [_U64, C.POINTER(_U64)],
+    "pcr_reorder_morton_shuffle128": [_VP, _VP, _U64, _U64, _INT, _VP, _U64, _VP],
+    "pcr_last_device_error": [_VP, C.POINTER(_U32)],
+}
+
+
+def lib() -> C.CDLL:
+    """Load libpcr.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2104_07526_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _INT
+            L.pcr_status_string.argtypes = [_INT]
+            L.pcr_status_string.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int, call: str):
+    if status != PCR_OK:
+        raise PcrError(status, call)
+
+
+def _dptr(t, what: str) -> int | None:
+    """Device address of a CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return t.data_ptr()
+
+
+def _hptr(a, what: str) -> int:
+    """Host address of a CPU tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise ValueError(f"{what} must be in host memory")
+        if not a.is_contiguous():
+            raise ValueError(f"{what} must be contiguous")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{what} must be contiguous")
+    return a.ctypes.data
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size() if hasattr(t, "element_size") else t.nbytes
+
+
+def pcr_status_string(status: int) -> str:
+    return lib().pcr_status_string(status).decode()
+
+
+def pcr_create(device: int = 0) -> int:
+    h = _VP()
+    _check(lib().pcr_create(C.byref(h), device), "pcr_create")
+    return h.value
+
+
+def pcr_destroy(ctx: int):
+    _check(lib().pcr_destroy(ctx), "pcr_destroy")
+
+
+def pcr_set_stream(ctx: int, stream=None):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t address, or None."""
+    handle = getattr(stream, "cuda_stream", stream)
+    _check(lib().pcr_set_stream(ctx, handle), "pcr_set_stream")
+
+
+def pcr_upload_points(ctx: int, points, n: int | None = None):
+    if n is None:
+        n = _nbytes(points) // 16
+    _check(lib().pcr_upload_points(ctx, _dptr(points, "points"), n), "pcr_upload_points")
+
+
+def pcr_upload_points_from_host(ctx: int, dev_points, host_points, n: int | None = None):
+    if n is None:
+        n = _nbytes(host_points) // 16
+    _check(lib().pcr_upload_points_from_host(ctx, _dptr(dev_points, "dev_points"),
+                                             _hptr(host_points, "host_points"), n), "pcr_upload_points_from_host")
+
+
+def pcr_set_matrix(ctx: int, m):
+    vals = [float(v) for v in (m.reshape(-1).tolist() if hasattr(m, "reshape") else m)]
+    if len(vals) != 16:
+        raise ValueError("matrix must have 16 entries")
+    arr = (_FLT * 16)(*vals)
+    _check(lib().pcr_set_matrix(ctx, arr), "pcr_set_matrix")
+
+
+def pcr_set_viewport(ctx: int, width: int, height: int):
+    _check(lib().pcr_set_viewport(ctx, width, height), "pcr_set_viewport")
+
+
+def pcr_set_framebuffer(ctx: int, keys=None, hq_depth=None, hq_rg=None, hq_ba=None):
+    _check(lib().pcr_set_framebuffer(ctx, _dptr(keys, "keys"), _dptr(hq_depth, "hq_depth"), _dptr(hq_rg, "hq_rg"),
+                                     _dptr(hq_ba, "hq_ba")), "pcr_set_framebuffer")
+
+
+def pcr_clear(ctx: int, what: int = PCR_CLEAR_KEYS):
+    _check(lib().pcr_clear(ctx, what), "pcr_clear")
+
+
+def pcr_render_basic(ctx: int, variant: int = PCR_VARIANT_DEDUP_EARLYZ, clear: bool = True):
+    _check(lib().pcr_render_basic(ctx, variant, int(bool(clear))), "pcr_render_basic")
+
+
+def pcr_render_hq(ctx: int, depth_factor: float = 1.01, variant: int = PCR_VARIANT_DEDUP_EARLYZ, clear: bool = True):
+    _check(lib().pcr_render_hq(ctx, depth_factor, variant, int(bool(clear))), "pcr_render_hq")
+
+
+def pcr_resolve(ctx: int, mode: int, out, background_rgba: int = 0):
+    _check(lib().pcr_resolve(ctx, mode, _dptr(out, "out"), background_rgba & 0xFFFFFFFF), "pcr_resolve")
+
+
+def pcr_download(ctx: int, host_dst, dev_src, nbytes: int | None = None):
+    if nbytes is None:
+        nbytes = _nbytes(dev_src)
+    _check(lib().pcr_download(ctx, _hptr(host_dst, "host_dst"), _dptr(dev_src, "dev_src"), nbytes), "pcr_download")
+
+
+def pcr_synchronize(ctx: int):
+    _check(lib().pcr_synchronize(ctx), "pcr_synchronize")
+
+
+def pcr_reorder_workspace_size(n: int) -> int:
+    out = _U64()
+    _check(lib().pcr_reorder_workspace_size(n, C.byref(out)), "pcr_reorder_workspace_size")
+    return out.value
+
+
+def pcr_reorder_morton_shuffle128(ctx: int, points, n: int, seed: int, mode: int, workspace, perm_out=None):
+    _check(lib().pcr_reorder_morton_shuffle128(ctx, _dptr(points, "points"), n, seed & ((1 << 64) - 1), mode,
+                                               _dptr(workspace, "workspace"),
+                                               _nbytes(workspace) if workspace is not None else 0,
+                                               _dptr(perm_out, "perm_out")), "pcr_reorder_morton_shuffle128")
+
+
+def pcr_last_device_error(ctx: int) -> int:
+    code = _U32()
+    _check(lib().pcr_last_device_error(ctx, C.byref(code)), "pcr_last_device_error")
+    return code.value
+
+
+# ---------------------------------------------------------------------------
+# Small conveniences for callers that hold their buffers in torch tensors.
+# ---------------------------------------------------------------------------
+
+def alloc_framebuffer(width: int, height: int, device="cuda", hq: bool = True) -> dict:
+    """Device tensors for one viewport: keys (int64 storage of uint64),
+    hq_depth (int32 storage of uint32), hq_rg, hq_ba and the rgba image."""
+    import torch
+    npx = width * height
+    fb = {"keys": torch.empty(npx, dtype=torch.int64, device=device),
+          "image": torch.empty(npx, dtype=torch.int32, device=device)}
+    if hq:
+        fb["hq_depth"] = torch.empty(npx, dtype=torch.int32, device=device)
+        fb["hq_rg"] = torch.empty(npx, dtype=torch.int64, device=device)
+        fb["hq_ba"] = torch.empty(npx, dtype=torch.int64, device=device)
+    return fb
+
+
+class Context:
+    """Owns one pcr_ctx; `with Context(0) as c:` destroys it on exit."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.handle = pcr_create(device)
+        if stream is not None:
+            pcr_set_stream(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            pcr_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -241,12 +241,16 @@ def scan_layout(n: int, seed: int = 0, nwalls: int = 40, facade_share: float = 0
 
 
 def scan(n: int = 800_000_000, seed: int = 0, device="cpu", chunk: int = 1 << 25,
-         out: torch.Tensor | None = None) -> torch.Tensor:
-    """Facade walls in vertical scanlines, then terrain in row scanlines."""
+         out: torch.Tensor | None = None, indices: torch.Tensor | None = None) -> torch.Tensor:
+    """Facade walls in vertical scanlines, then terrain in row scanlines.
+
+    With ``indices``, only those points of the n-point cloud are made (in
+    that order); each point depends on its index alone."""
     lay = scan_layout(n, seed)
     nfac = int(lay.wall_counts.sum())
+    total = n if indices is None else int(indices.shape[0])
     if out is None:
-        out = torch.empty((n, 4), dtype=torch.int32, device=device)
+        out = torch.empty((total, 4), dtype=torch.int32, device=device)
     wstart = np.concatenate([[0], np.cumsum(lay.wall_counts)])
     # per-wall scanline grid: columns along the wall, rows bottom to top
     wrows = np.maximum(1, np.round(np.sqrt(lay.wall_counts * lay.walls[:, 4] / lay.walls[:, 3]))).astype(np.int64)
@@ -258,9 +262,12 @@ def scan(n: int = 800_000_000, seed: int = 0, device="cpu", chunk: int = 1 << 25
     t_wcols = torch.tensor(np.maximum(wcols, 1), device=device)
     base_z = _terrain_height(t_walls[:, 0], t_walls[:, 1]) - 1.0
     wr, wg, wb = _hsv_to_rgb(t_walls[:, 5], torch.full_like(t_walls[:, 5], 0.6), torch.full_like(t_walls[:, 5], 0.85))
-    for s in range(0, n, chunk):
-        e = min(n, s + chunk)
-        idx = torch.arange(s, e, dtype=torch.int64, device=device)
+    for s in range(0, total, chunk):
+        e = min(total, s + chunk)
+        if indices is None:
+            idx = torch.arange(s, e, dtype=torch.int64, device=device)
+        else:
+            idx = indices[s:e].to(device=device, dtype=torch.int64)
         is_fac = idx < nfac
         # facades
         w = torch.clamp(torch.searchsorted(t_wbounds, idx, right=True), max=len(lay.wall_counts) - 1)

@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA render path against the CPU oracle, bit for bit.
+
+Every comparison goes through the C ABI (libpcr.so).  Key buffers, HQ depth
+and sum buffers and resolved images are integers, so the bar is exact
+equality.
+"""
+import numpy as np
+import pytest
+import torch
+
+import constructed as cs
+from gpu_helpers import Renderer, U64_EMPTY
+from paper_2104_07526_gb300 import pcr, scenes
+
+pytestmark = pytest.mark.gpu
+
+EXACT = pcr.EXACT_VARIANTS
+
+
+@pytest.fixture(scope="module")
+def r():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    rend = Renderer()
+    yield rend
+    rend.close()
+
+
+@pytest.fixture(scope="module")
+def sphere():
+    # 1M-point recipe at a size the oracle renders in well under a second;
+    # 200003 points = 1563 chunks of 128 plus a ragged tail of 35.
+    return scenes.sphere_plane(200_003, seed=0).numpy()
+
+
+def test_sphere_plane_all_variants(r, oracle, sphere):
+    view = scenes.sphere_plane_views()[0]
+    expect = oracle.render_basic(sphere, view.matrix, view.width, view.height)
+    img_expect = oracle.resolve_basic(expect, sphere, 0x12345678)
+    r.upload(sphere)
+    r.view(view.matrix, view.width, view.height)
+    assert (expect != U64_EMPTY).sum() > 10000
+    for v in EXACT:
+        got = r.render_basic(v)
+        assert np.array_equal(got, expect), pcr.VARIANT_NAMES[v]
+        img = r.resolve(pcr.PCR_RESOLVE_BASIC, 0x12345678)
+        assert np.array_equal(img, img_expect), pcr.VARIANT_NAMES[v]
+
+
+def test_constructed_depth_scene(r):
+    rng = np.random.default_rng(21)
+    cloud, expected, _, _ = cs.depth_scene(rng, npix=3000, max_per_pixel=8)
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    for v in EXACT:
+        assert np.array_equal(r.render_basic(v), expected), pcr.VARIANT_NAMES[v]
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 31, 32, 33, 127, 128, 129, 4097])
+def test_ragged_sizes(r, oracle, n):
+    cloud = scenes.random_cloud(n, seed=n + 100).numpy() if n else np.zeros((0, 4), np.int32)
+    m = scenes.camera((0.2, -2.6, 1.4), (0, 0, 0), (0, 0, 1), 32, 24)
+    expect = oracle.render_basic(cloud, m, 32, 24)
+    r.upload(cloud)
+    r.view(m, 32, 24)
+    for v in EXACT:
+        assert np.array_equal(r.render_basic(v), expect), (n, pcr.VARIANT_NAMES[v])
+
+
+def test_single_pixel_contention(r, oracle):
+    """All points on one pixel: distinct depths, then equal depths (the
+    smallest index must win), across many warps and blocks."""
+    n = 300_000
+    rng = np.random.default_rng(5)
+    d = rng.integers(4, 4000, size=n) / 256.0  # exact dyadic depths
+    xyz = np.stack([np.zeros(n), np.zeros(n), cs.EYE_Z - d], 1)
+    cloud = cs.pack(xyz, np.arange(n, dtype=np.uint32))
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    expect = oracle.render_basic(cloud, cs.camera(), cs.W, cs.H)
+    for v in EXACT:
+        assert np.array_equal(r.render_basic(v), expect), pcr.VARIANT_NAMES[v]
+    same = cs.pack(np.tile([[0.0, 0.0, 1.5]], (n, 1)), np.arange(n, dtype=np.uint32))
+    r.upload(same)
+    for v in EXACT:
+        got = r.render_basic(v)
+        assert got[cs.W // 2 + (cs.H // 2) * cs.W] == (int(np.float32(2.5).view(np.uint32)) << 32), v
+
+
+def test_culling_edge_inputs(r, oracle):
+    """NaN and infinite coordinates, points behind the eye, points exactly
+    on the viewport edges."""
+    t = np.tan(np.radians(30.0))
+    rows = [[np.nan, 0, 0], [0, np.inf, 0], [0, 0, -np.inf], [0, 0, 9.0], [0, 0, 4.0],
+            [t * 2.0 * 4 / 3, 0, 2.0], [-t * 2.0 * 4 / 3, 0, 2.0], [0, t * 2.0, 2.0], [0, -t * 2.0, 2.0],
+            [1e30, 1e30, -1e30], [1e-30, -1e-30, 3.9999], [0.1, 0.1, 3.0]]
+    cloud = cs.pack(np.array(rows, dtype=np.float64), np.arange(len(rows), dtype=np.uint32))
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    expect = oracle.render_basic(cloud, cs.camera(), cs.W, cs.H)
+    for v in EXACT:
+        assert np.array_equal(r.render_basic(v), expect), pcr.VARIANT_NAMES[v]
+
+
+def test_tiny_and_wide_viewports(r, oracle):
+    cloud = scenes.random_cloud(50_000, seed=3).numpy()
+    for (W, H) in [(1, 1), (3, 1), (1, 5), (16384, 2), (2, 16384)]:
+        m = scenes.camera((0.1, -3.0, 0.2), (0, 0, 0), (0, 0, 1), W, H, 75.0)
+        expect = oracle.render_basic(cloud, m, W, H)
+        r.upload(cloud)
+        r.view(m, W, H)
+        for v in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ, pcr.PCR_VARIANT_REDUCE_EARLYZ):
+            assert np.array_equal(r.render_basic(v), expect), (W, H, v)
+
+
+def test_no_clear_accumulates(r, oracle, sphere):
+    """clear=0 merges by minimum: rendering the same cloud twice equals once,
+    and a buffer pre-filled with keys keeps the smaller of old and new."""
+    view = scenes.sphere_plane_views()[0]
+    r.upload(sphere)
+    r.view(view.matrix, view.width, view.height)
+    once = r.render_basic(pcr.PCR_VARIANT_DEDUP_EARLYZ)
+    twice = r.render_basic(pcr.PCR_VARIANT_EARLYZ, clear=False)
+    assert np.array_equal(once, twice)
+    prefill = np.full(once.size, np.uint64((int(np.float32(4.0).view(np.uint32)) << 32) | 7), np.uint64)
+    r.fb["keys"].copy_(torch.from_numpy(prefill.view(np.int64)))
+    got = r.render_basic(pcr.PCR_VARIANT_DEDUP, clear=False)
+    assert np.array_equal(got, np.minimum(prefill, once))
+
+
+def test_just_set_writes_valid_keys(r, oracle, sphere):
+    """Sec. 5 just-set has no depth test: each covered pixel holds the key of
+    some point that lands there, and the covered set equals the oracle's."""
+    view = scenes.sphere_plane_views()[0]
+    expect = oracle.render_basic(sphere, view.matrix, view.width, view.height)
+    r.upload(sphere)
+    r.view(view.matrix, view.width, view.height)
+    got = r.render_basic(pcr.PCR_VARIANT_JUST_SET)
+    assert np.array_equal(got == U64_EMPTY, expect == U64_EMPTY)
+    hit = np.nonzero(got != U64_EMPTY)[0]
+    idx = (got[hit] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    p = np.ascontiguousarray(sphere[:, :3]).view(np.float32)
+    for j in range(0, hit.size, max(1, hit.size // 2000)):
+        pr = oracle.project(view.matrix, view.width, view.height, *p[idx[j]])
+        assert pr is not None and pr[0] == hit[j]
+        assert int(got[hit[j]]) >> 32 == int(np.float32(pr[1]).view(np.uint32))
+
+
+def test_resolve_out_of_range_index(r):
+    """A key naming a point outside the cloud resolves to the background and
+    raises bit 0 of the device error word."""
+    cloud = cs.pack(np.zeros((4, 3)), np.array([1, 2, 3, 4], dtype=np.uint32))
+    r.upload(cloud)
+    r.view(np.eye(4, dtype=np.float32), 2, 2)
+    assert pcr.pcr_last_device_error(r.h) == 0
+    keys = np.array([0xFFFFFFFFFFFFFFFF, (0x3F800000 << 32) | 2, (0x3F800000 << 32) | 4, 5], dtype=np.uint64)
+    r.fb["keys"].copy_(torch.from_numpy(keys.view(np.int64)))
+    img = r.resolve(pcr.PCR_RESOLVE_BASIC, 0xDEADBEEF)
+    assert img.tolist() == [0xDEADBEEF, 3, 0xDEADBEEF, 0xDEADBEEF]
+    assert pcr.pcr_last_device_error(r.h) == 1
+    assert pcr.pcr_last_device_error(r.h) == 0
+
+
+# --- Sec. 3.5 ------------------------------------------------------------------
+
+def test_hq_constructed(r):
+    rng = np.random.default_rng(8)
+    cloud, depth, sums = cs.hq_scene(rng, npix=4000)
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    for v in (0, 1, 2, 3):
+        d, rg, ba = r.render_hq(v, 1.01)
+        assert np.array_equal(d, depth), v
+        assert np.array_equal(rg, (sums[0] << np.uint64(32)) | sums[1]), v
+        assert np.array_equal(ba, (sums[2] << np.uint64(32)) | sums[3]), v
+
+
+def test_hq_sphere_parity(r, oracle, sphere):
+    view = scenes.sphere_plane_views()[0]
+    W, H = view.width, view.height
+    r.upload(sphere)
+    r.view(view.matrix, W, H)
+    for factor in (1.01, 1.0, 1.5):
+        e = oracle.render_hq(sphere, view.matrix, W, H, factor)
+        img0 = oracle.resolve_hq(e[1], e[2], 0x01020304)
+        for v in (0, 1, 2, 3):
+            got = r.render_hq(v, factor)
+            for a, b in zip(got, e):
+                assert np.array_equal(a, b), (v, factor)
+            img = r.resolve(pcr.PCR_RESOLVE_HQ, 0x01020304)
+            assert np.array_equal(img, img0), (v, factor)
+
+
+def test_hq_single_pixel_heavy(r, oracle):
+    """200k points on one pixel within the band: 32-bit sums stay exact and
+    the warp aggregation adds up exactly."""
+    n = 200_000
+    rng = np.random.default_rng(9)
+    d = 2.0 + rng.integers(0, 4, size=n) / 1024.0
+    xyz = np.stack([np.zeros(n), np.zeros(n), cs.EYE_Z - d], 1)
+    col = rng.integers(0, 256, size=(n, 3))
+    cloud = cs.pack(xyz, cs.rgba_word(col[:, 0], col[:, 1], col[:, 2]))
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    e = oracle.render_hq(cloud, cs.camera(), cs.W, cs.H, 1.01)
+    for v in (0, 3):
+        got = r.render_hq(v, 1.01)
+        for a, b in zip(got, e):
+            assert np.array_equal(a, b), v
+    p = cs.W // 2 + (cs.H // 2) * cs.W
+    assert int(e[2][p]) & 0xFFFFFFFF == n
+
+
+def test_hq_ragged(r, oracle):
+    for n in (0, 1, 33, 129, 5000):
+        cloud = scenes.random_cloud(n, seed=n).numpy() if n else np.zeros((0, 4), np.int32)
+        m = scenes.camera((0.3, -2.2, 1.0), (0, 0, 0), (0, 0, 1), 20, 15)
+        e = oracle.render_hq(cloud, m, 20, 15, 1.01)
+        r.upload(cloud)
+        r.view(m, 20, 15)
+        for v in (0, 3):
+            got = r.render_hq(v, 1.01)
+            for a, b in zip(got, e):
+                assert np.array_equal(a, b), (n, v)
