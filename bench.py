@@ -1,0 +1,565 @@
+#!/usr/bin/env python3
+"""Benchmark of compute-based point rendering on GB300.
+
+Workload (default): the 800M-point scan-like scene (facade walls plus a
+terrain heightfield, 12.8 GB of 16-byte records), reordered once to shuffled
+Morton order (batches of 128), rendered at 1920x1080 from the overview
+camera.  One step is one basic frame: clear the key buffer, render with warp
+deduplication plus early depth test (the paper's "dedup" method), resolve to
+rgba.  The metric is points per second; the dominant kernel (the render pass)
+is also reported as achieved HBM GB/s against the measured copy bandwidth.
+
+The same JSON line carries the end-to-end number (points uploaded from pinned
+host memory through pcr_upload_points_from_host, frame, image read back
+through pcr_download, every step), per-phase times, the one-time reorder
+cost, a sweep over render variants, vertex orders and cameras, and the CPU
+oracle timed on a bounded sample of the same frame.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the CPU oracle is timed instead (rank 0 only).  Under
+torchrun each rank renders its own copy of the workload on its own GPU (weak
+scaling, replicas only: no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "points/s and HBM GB/s vs roofline per frame"
+UNIT = "points/s"
+POINT_BYTES = 16
+FALLBACK_HBM_GBS = 6800.0
+
+CONFIGS = {
+    # name: (points, generator, views, headline view)
+    "scan800M": dict(points=800_000_000, gen="scan", view="overview",
+                     desc="800M-point scan scene (facades + terrain), shuffled-Morton order, overview camera, "
+                          "1920x1080, basic frame with dedup+early-z"),
+    "scan100M": dict(points=100_000_000, gen="scan", view="overview",
+                     desc="100M-point scan scene (the 800M recipe at 1/8 size, for profiling), shuffled-Morton "
+                          "order, overview camera, 1920x1080, basic frame"),
+    "boxes50M": dict(points=50_000_000, gen="boxes", view="overview",
+                     desc="50M points on 200 boxes over a ground plane, shuffled-Morton order, overview camera, "
+                          "1920x1080, basic frame with dedup+early-z"),
+    "sphere1M": dict(points=1_000_000, gen="sphere_plane", view="front",
+                     desc="1M points on a sphere plus a plane, shuffled-Morton order, 640x480, basic frame with "
+                          "dedup+early-z"),
+}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="scan800M")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the variant x order x camera sweep")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--variant", default="dedup+early-z", help="render variant of the timed frame")
+    ap.add_argument("--no-hq", action="store_true", help="skip the high-quality frame")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world: int, backend: str):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Largest value over all ranks (timing only; not on the data path)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_throughput(points_per_rank: int, world: int, max_seconds: float) -> float:
+    """Whole-job points/s: every rank's points over the slowest rank's time."""
+    return points_per_rank * world / max_seconds
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str, interval_ms: int = 50):
+        self.gpu_id = gpu_id
+        self.interval_ms = interval_ms
+        self.proc = None
+        self.lines: list[tuple[float, str]] = []
+        self.reader = None
+        self.window = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", str(self.interval_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, start: float, end: float):
+        """Keep only samples that arrived inside [start, end] (host clock)."""
+        self.window = (start, end)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.reader.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        for t, line in self.lines:
+            if self.window is not None and not (self.window[0] <= t <= self.window[1]):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, state in zip(self.REASONS, parts[5:9]):
+                if state.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def nvsmi_id(cuda_index: int) -> str:
+    """nvidia-smi id of a CUDA device (its UUID; CUDA_VISIBLE_DEVICES may
+    renumber devices)."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(cuda_index).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(cuda_index)
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def measured_hbm_gbs() -> tuple[float, str]:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel_sources: list[str]) -> dict | None:
+    """DRAM bytes per render launch from an ncu capture, if it was taken on
+    the current kernel sources (profiles/traffic_render_scan800M.txt)."""
+    path = os.path.join(ROOT, "profiles", "traffic_render_scan800M.txt")
+    try:
+        with open(path) as f:
+            kv = dict(line.split("=", 1) for line in f.read().splitlines() if "=" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    h = hashlib.sha256()
+    for p in kernel_sources:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    if kv.get("sources_sha256", "").strip() != h.hexdigest():
+        return None
+    return {"bytes_per_launch": float(kv["bytes_per_launch"]), "note": kv.get("note", "").strip()}
+
+
+def make_cloud(cfg: dict, device, seed: int = 0):
+    from paper_2104_07526_gb300 import scenes
+    n = cfg["points"]
+    if cfg["gen"] == "scan":
+        cloud = scenes.scan(n, seed=seed, device=device)
+        views = scenes.scan_views(n, seed)
+    elif cfg["gen"] == "boxes":
+        cloud = scenes.boxes(n, seed=seed, device=device)
+        views = scenes.boxes_views(seed)
+    else:
+        cloud = scenes.sphere_plane(n, seed=seed, device=device)
+        views = scenes.sphere_plane_views()
+    return cloud, views
+
+
+def cpu_sample_indices(n: int, sample: int):
+    import torch
+    stride = max(1, n // max(sample, 1))
+    return torch.arange(0, n, stride, dtype=torch.int64)[:sample]
+
+
+def time_oracle(pts_np: np.ndarray, view, repeats: int = 1) -> float:
+    """Seconds per oracle frame (render + resolve) on this sample."""
+    from oracle import pyoracle
+    best = None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        keys = pyoracle.render_basic(pts_np, view.matrix, view.width, view.height)
+        pyoracle.resolve_basic(keys, pts_np, 0)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best
+
+
+def oracle_baseline(cloud_host_fn, n: int, view, target_s: float) -> dict:
+    """Time the CPU oracle (single thread, as it stands) on a strided sample
+    of the same cloud sized to about target_s seconds of work."""
+    pilot_n = min(n, 2_000_000)
+    pilot = cloud_host_fn(pilot_n)
+    t = time_oracle(pilot, view)
+    rate = pilot_n / max(t, 1e-6)
+    sample = int(min(n, max(pilot_n, rate * target_s)))
+    pts = cloud_host_fn(sample)
+    dt = time_oracle(pts, view)
+    return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sample} points (every {max(1, n // sample)}th of the {n}-point cloud), one frame "
+                      f"(render + resolve), single-threaded C oracle, {dt:.2f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def run_reference(args, cfg):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+    from paper_2104_07526_gb300 import scenes
+    from oracle import build as oracle_build
+    oracle_build.build()
+    n = cfg["points"]
+    _, views = make_cloud({**cfg, "points": 1024}, "cpu") if cfg["gen"] != "scan" else (None, scenes.scan_views(n, 0))
+    view = next(v for v in views if v.name == cfg["view"])
+
+    def host_sample(k):
+        idx = cpu_sample_indices(n, k)
+        if cfg["gen"] == "scan":
+            return scenes.scan(n, seed=0, indices=idx).numpy()
+        full, _ = make_cloud(cfg, "cpu")
+        return full[idx].numpy()
+
+    # size each step so warmup + steps stay within about two minutes
+    budget = 120.0
+    pilot_n = min(n, 1_000_000)
+    pilot = host_sample(pilot_n)
+    rate = pilot_n / max(time_oracle(pilot, view), 1e-6)
+    per_step = budget / max(1, args.steps + args.warmup)
+    sample = int(min(n, max(100_000, rate * per_step)))
+    pts = host_sample(sample)
+    for _ in range(args.warmup):
+        time_oracle(pts, view)
+    times = [time_oracle(pts, view) for _ in range(args.steps)]
+    step_s = sum(times) / len(times)
+    value = sample / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/u64", "data": "synthetic",
+        "config": workload_config(cfg, view),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{sample} points per step (every {max(1, n // sample)}th point of the "
+                                   f"{n}-point cloud), render + resolve, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(cfg: dict, view) -> dict:
+    return {"workload": cfg["desc"], "points": cfg["points"], "width": view.width, "height": view.height,
+            "order": "morton_shuffle128", "camera": view.name, "variant": "dedup+early-z",
+            "l2": "inputs larger than L2 (no flush needed)" if cfg["points"] * POINT_BYTES > 129e6
+            else "inputs fit in L2 (L2-resident case)", "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, cfg):
+    import torch
+    from paper_2104_07526_gb300 import build as lib_build
+    from paper_2104_07526_gb300 import pcr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = dist_init(world, "nccl")
+    lib_build.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    n = cfg["points"]
+
+    t0 = time.perf_counter()
+    cloud, views = make_cloud(cfg, dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    view = next(v for v in views if v.name == cfg["view"])
+    W, H = view.width, view.height
+
+    ctx = pcr.Context(local, stream=stream)
+    h = ctx.handle
+    fb = pcr.alloc_framebuffer(W, H, dev)
+    pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+
+    # --- one-time reorders (Sec. 4); original order kept for the sweep ----
+    ws = torch.empty(pcr.pcr_reorder_workspace_size(n), dtype=torch.uint8, device=dev)
+    orders = {"original": cloud}
+    reorder_ms = {}
+    for name, mode in (("morton", pcr.PCR_ORDER_MORTON), ("shuffle", pcr.PCR_ORDER_SHUFFLE),
+                       ("morton_shuffle128", pcr.PCR_ORDER_MORTON_SHUFFLE128)):
+        if args.no_sweep and name != "morton_shuffle128":
+            continue
+        buf = cloud.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pcr.pcr_reorder_morton_shuffle128(h, buf, n, 0x5EED, mode, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        reorder_ms[name] = e0.elapsed_time(e1)
+        orders[name] = buf
+    del ws
+    if args.no_sweep:
+        del orders["original"]
+        del cloud
+    torch.cuda.empty_cache()
+    points = orders["morton_shuffle128"]
+
+    def set_view(v):
+        pcr.pcr_set_matrix(h, v.matrix)
+        pcr.pcr_set_viewport(h, v.width, v.height)
+
+    names = {v: k for k, v in pcr.VARIANT_NAMES.items()}
+    variant = names[args.variant]
+    pcr.pcr_upload_points(h, points, n)
+    set_view(view)
+
+    def frame():
+        pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
+        pcr.pcr_render_basic(h, variant, False)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+
+    # --- timed region ---------------------------------------------------------
+    for _ in range(args.warmup):
+        frame()
+    clocks = ClockSampler(nvsmi_id(local))
+    clocks.start()
+    time.sleep(0.5)  # nvidia-smi start-up
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    torch.cuda.synchronize()
+    barrier(dist)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_begin = time.time()
+    start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
+        ev[k][1].record(stream)
+        pcr.pcr_render_basic(h, variant, False)
+        ev[k][2].record(stream)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+        ev[k][3].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    t_end = time.time()
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.mark(t_begin, t_end)
+    clock_info = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    max_total_ms = max_over_ranks(total_ms, dist, dev)
+    ms_per_step = max_total_ms / K
+    phase = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, p in
+             enumerate(("clear", "render", "resolve"))}
+    render_ms = phase["render"]
+    value = aggregate_throughput(n, world, max_total_ms / K / 1e3)
+
+    peak, peak_src = measured_hbm_gbs()
+    achieved = n * POINT_BYTES / (render_ms * 1e-3) / 1e9
+    traffic = recorded_traffic([os.path.join(ROOT, "paper_2104_07526_gb300", "csrc", f)
+                                for f in ("render.cu", "common.cuh")]) if cfg["gen"] == "scan" else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic["bytes_per_launch"] if traffic else None,
+                "kernel": f"k_render_basic<{args.variant}>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": n * POINT_BYTES}
+
+    # --- HQ frame (Sec. 3.5) ------------------------------------------------------
+    def hq_frame():
+        pcr.pcr_render_hq(h, 1.01, variant, True)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, fb["image"], 0)
+
+    hq_ms = None if args.no_hq else time_loop(hq_frame, stream, reps=max(5, min(K, 50)), warm=3)
+
+    # --- end to end through the C ABI with host buffers ---------------------------
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world,
+                      steps=max(3, min(K, 20)), warm=2)
+        pcr.pcr_upload_points(h, points, n)
+
+    # --- sweep: variants x orders x cameras ---------------------------------------
+    sweep = None
+    if not args.no_sweep:
+        sweep = run_sweep(h, pcr, orders, views, n, fb, stream)
+        pcr.pcr_upload_points(h, points, n)
+        set_view(view)
+
+    # --- CPU oracle baseline (rank 0, one GPU) -------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import build as oracle_build
+        oracle_build.build()
+        cpu = oracle_baseline(lambda k: points[cpu_sample_indices(n, k).to(dev)].cpu().numpy(), n, view,
+                              args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view),
+            "frame_gbs": n * POINT_BYTES / (ms_per_step * 1e-3) / 1e9,
+            "phases_ms": phase, "hq_frame_ms": hq_ms,
+            "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
+            "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
+            "sweep_ms": sweep,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def time_loop(fn, stream, reps: int, warm: int) -> float:
+    import torch
+    for _ in range(warm):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, steps: int, warm: int) -> dict:
+    """Points from pinned host memory -> frame -> image back to host, every
+    step, all through the C ABI."""
+    import torch
+    host = torch.empty(points.shape, dtype=points.dtype, pin_memory=True)
+    host.copy_(points)
+    img_host = torch.empty(W * H, dtype=torch.int32).pin_memory()
+
+    def step():
+        pcr.pcr_upload_points_from_host(h, points, host, n)
+        pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
+        pcr.pcr_render_basic(h, variant, False)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+        pcr.pcr_download(h, img_host, fb["image"])
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize()
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    del host
+    return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
+            "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
+            "ms_per_step": dt / steps * 1e3}
+
+
+def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
+    out = {}
+    for v in views:
+        pcr.pcr_set_matrix(h, v.matrix)
+        pcr.pcr_set_viewport(h, v.width, v.height)
+        out[v.name] = {}
+        for oname, buf in orders.items():
+            pcr.pcr_upload_points(h, buf, n)
+            row = {}
+            for var in range(7):
+                row[pcr.VARIANT_NAMES[var]] = round(time_loop(
+                    lambda: pcr.pcr_render_basic(h, var, True), stream, reps=10, warm=2), 4)
+            for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ):
+                row["hq:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
+                    lambda: pcr.pcr_render_hq(h, 1.01, var, True), stream, reps=5, warm=1), 4)
+            out[v.name][oname] = row
+    return out
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    return run_ours(args, cfg)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
