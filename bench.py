@@ -436,7 +436,7 @@ def run_ours(args, cfg):
     peak, peak_src = measured_hbm_gbs()
     achieved = n * POINT_BYTES / (render_ms * 1e-3) / 1e9
     traffic = recorded_traffic([os.path.join(ROOT, "paper_2104_07526_gb300", "csrc", f)
-                                for f in ("render.cu", "common.cuh")]) if cfg["gen"] == "scan" else None
+                                for f in ("render.cu", "common.cuh")]) if args.config == "scan800M" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic["bytes_per_launch"] if traffic else None,
                 "kernel": f"k_render_basic<{args.variant}>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"

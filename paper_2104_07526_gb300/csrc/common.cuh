@@ -53,11 +53,13 @@ __device__ __forceinline__ bool project(const ViewParams& v, float x, float y, f
 
 // 16-byte point load that streams past L1 and marks the line first for
 // eviction in L2, so the point stream does not push the framebuffer out.
+// The point buffer is read-only while a kernel runs, so the load is a pure
+// function of its address and the compiler may schedule it freely.
 __device__ __forceinline__ uint4 load_point_stream(const uint4* p, uint64_t policy) {
   uint4 r;
-  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
-               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-               : "l"(p), "l"(policy));
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+      : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+      : "l"(p), "l"(policy));
   return r;
 }
 
@@ -76,34 +78,34 @@ __device__ __forceinline__ uint64_t policy_evict_last() {
 // Unsynchronised read of a framebuffer word for the early depth test
 // (Sec. 3.2).  A relaxed load is not a data race against the atomics; a
 // stale value can only be larger than the current one (values only
-// decrease), which costs an extra atomic and never a wrong pixel.
+// decrease), which costs an extra atomic and never a wrong pixel.  These
+// reads and the atomics below are volatile (kept in program order among
+// themselves) but carry no memory clobber: nothing in a render kernel reads
+// the framebuffer through ordinary loads.
 __device__ __forceinline__ unsigned long long load_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
   return v;
 }
 
 __device__ __forceinline__ uint32_t load_relaxed_u32(const uint32_t* p) {
   uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
 
 // Fire-and-forget atomic minimum / add (the result is never read), with an
 // L2 evict-last hint so the framebuffer stays resident.
 __device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v, uint64_t policy) {
-  asm volatile("red.relaxed.gpu.global.min.u64.L2::cache_hint [%0], %1, %2;" ::"l"(p), "l"(v), "l"(policy)
-               : "memory");
+  asm volatile("red.relaxed.gpu.global.min.u64.L2::cache_hint [%0], %1, %2;" ::"l"(p), "l"(v), "l"(policy));
 }
 
 __device__ __forceinline__ void red_min_u32(uint32_t* p, uint32_t v, uint64_t policy) {
-  asm volatile("red.relaxed.gpu.global.min.u32.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(v), "l"(policy)
-               : "memory");
+  asm volatile("red.relaxed.gpu.global.min.u32.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(v), "l"(policy));
 }
 
 __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long long v, uint64_t policy) {
-  asm volatile("red.relaxed.gpu.global.add.u64.L2::cache_hint [%0], %1, %2;" ::"l"(p), "l"(v), "l"(policy)
-               : "memory");
+  asm volatile("red.relaxed.gpu.global.add.u64.L2::cache_hint [%0], %1, %2;" ::"l"(p), "l"(v), "l"(policy));
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }

@@ -8,6 +8,7 @@
 // (SM count x resident blocks) walks the chunks in order, so the GPU works on
 // a moving window of the buffer, as a vertex-order study needs.
 #include <cstdint>
+#include <type_traits>
 
 #include "../../include/pcr.h"
 #include "common.cuh"
@@ -19,43 +20,69 @@ namespace {
 
 __device__ uint32_t g_error_word;
 
+#ifndef PCR_GEOMETRY_UNROLL
+#define PCR_GEOMETRY_UNROLL 4
+#endif
+#ifndef PCR_GEOMETRY_MIN_BLOCKS
+#define PCR_GEOMETRY_MIN_BLOCKS 1
+#endif
+
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+// Points per lane per chunk, and the resident blocks per SM the geometry
+// kernels are compiled for (a register cap).
+constexpr int kUnroll = PCR_GEOMETRY_UNROLL;
+constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
+// HQ colour pass: above this many runs of equal pixels in a warp row the
+// warp adds directly instead of aggregating.
+constexpr int kAggregateMaxRuns = 12;
 
 __device__ __forceinline__ unsigned long long make_key(float w, uint32_t idx) {
   return (static_cast<unsigned long long>(__float_as_uint(w)) << 32) | idx;
 }
 
-// Walk the point chunks of this warp and call f(record, index, in_range) for
-// each slot; every lane of the warp calls f the same number of times, so f
-// may use warp-collective operations.
+// Walk the point chunks of this warp.  For each chunk, f(r, base, full)
+// gets the U records of this lane (slot u holds point base + 32u), and
+// `full` as a compile-time flag: true when every slot of the chunk lies
+// inside the cloud.  Every lane of the warp calls f the same number of times,
+// so f may use warp-collective operations.
 template <int U, class F>
-__device__ __forceinline__ void for_each_point(const uint4* __restrict__ pts, uint32_t n, uint64_t pol, F&& f) {
+__device__ __forceinline__ void for_each_chunk(const uint4* __restrict__ pts, uint32_t n, uint64_t pol, F&& f) {
   const uint64_t warps_per_block = blockDim.x >> 5;
   const uint64_t warp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const uint64_t nwarps = gridDim.x * warps_per_block;
-  const uint64_t chunk = 32ull * U;
-  const uint64_t nchunks = (static_cast<uint64_t>(n) + chunk - 1) / chunk;
+  constexpr uint64_t kChunk = 32ull * U;
+  const uint64_t nfull = n / kChunk;
   const uint32_t lane = lane_id();
-  for (uint64_t c = warp; c < nchunks; c += nwarps) {
-    const uint64_t base = c * chunk + lane;
+  uint64_t c = warp;
+  for (; c < nfull; c += nwarps) {
+    const uint32_t base = static_cast<uint32_t>(c * kChunk) + lane;
+    uint4 r[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) r[u] = load_point_stream(pts + base + 32u * u, pol);
+    f(r, base, std::true_type{});
+  }
+  if (c == nfull && nfull * kChunk < n) {  // the one ragged chunk, if any
+    const uint64_t base = c * kChunk + lane;
     uint4 r[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint64_t i = base + 32ull * u;
       r[u] = (i < n) ? load_point_stream(pts + i, pol) : make_uint4(0u, 0u, 0u, 0u);
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + 32ull * u;
-      f(r[u], static_cast<uint32_t>(i), i < n);
-    }
+    f(r, static_cast<uint32_t>(base), std::false_type{});
   }
 }
 
-__device__ __forceinline__ bool project_record(const ViewParams& v, const uint4& r, bool in_range, uint32_t& pix,
-                                               float& w) {
-  if (!in_range) return false;
+template <class Full>
+__device__ __forceinline__ bool slot_in_range(uint32_t base, int u, uint32_t n, Full) {
+  if constexpr (Full::value) {
+    return true;
+  } else {
+    return static_cast<uint64_t>(base) + 32ull * u < n;
+  }
+}
+
+__device__ __forceinline__ bool project_record(const ViewParams& v, const uint4& r, uint32_t& pix, float& w) {
   return project(v, __uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z), pix, w);
 }
 
@@ -64,8 +91,15 @@ __device__ __forceinline__ bool project_record(const ViewParams& v, const uint4&
 // ---------------------------------------------------------------------------
 
 template <int V>
+__host__ __device__ constexpr bool reads_early() {
+  return V == PCR_VARIANT_EARLYZ || V == PCR_VARIANT_DEDUP_EARLYZ || V == PCR_VARIANT_REDUCE_EARLYZ;
+}
+
+// One point slot after projection.  `seen` is this lane's earlier read of
+// its pixel (variants with the early test only).
+template <int V>
 __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix, float w,
-                                         uint32_t idx, uint64_t pol) {
+                                         uint32_t idx, unsigned long long seen, uint64_t pol) {
   const unsigned long long key = make_key(w, idx);
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
     // Sec. 3.1: atomicMin(framebuffer[pixelID], point)
@@ -73,8 +107,8 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
   } else if constexpr (V == PCR_VARIANT_EARLYZ) {
     // Sec. 3.2: only call the atomic when the point is closer than what the
     // buffer (possibly stale, never too small) holds.
-    if (vis && key < load_relaxed_u64(fb + pix)) red_min_u64(fb + pix, key, pol);
-  } else if constexpr (V == PCR_VARIANT_DEDUP || V == PCR_VARIANT_DEDUP_EARLYZ) {
+    if (vis && key < seen) red_min_u64(fb + pix, key, pol);
+  } else if constexpr (V == PCR_VARIANT_DEDUP) {
     // Sec. 3.4: lanes with the same pixel form a group; only the lane with
     // the group's smallest key writes.  Keys reduce on the full 64 bits
     // (depth, then index), so each distinct pixel costs one atomic per warp
@@ -86,8 +120,22 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
     const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
     const uint32_t hmin = __reduce_min_sync(peers, hi);
     const uint32_t tied = __ballot_sync(kFullMask, hi == hmin) & peers;
-    if (vis && lane_id() == static_cast<uint32_t>(__ffs(tied) - 1)) {
-      if (V == PCR_VARIANT_DEDUP || key < load_relaxed_u64(fb + pix)) red_min_u64(fb + pix, key, pol);
+    if (vis && lane_id() == static_cast<uint32_t>(__ffs(tied) - 1)) red_min_u64(fb + pix, key, pol);
+  } else if constexpr (V == PCR_VARIANT_DEDUP_EARLYZ) {
+    // Sec. 3.4 with Sec. 3.2, tests swapped: every visible lane has read its
+    // pixel already (cheap, mostly L2 hits); only lanes still closer than the
+    // buffer take part in the deduplication, which the whole warp skips when
+    // none is left.  A lane dropped by the early test can never hold a
+    // pixel's final minimum, so the set of writers still contains it and the
+    // buffer is the same.
+    const bool want = vis && key < seen;
+    const uint32_t active = __ballot_sync(kFullMask, want);
+    if (active != 0 && want) {
+      const uint32_t peers = __match_any_sync(active, pix);
+      const uint32_t hi = __float_as_uint(w);
+      const uint32_t hmin = __reduce_min_sync(peers, hi);
+      const uint32_t first = __reduce_min_sync(peers, hi == hmin ? lane_id() : 32u);
+      if (lane_id() == first) red_min_u64(fb + pix, key, pol);
     }
   } else if constexpr (V == PCR_VARIANT_REDUCE || V == PCR_VARIANT_REDUCE_EARLYZ) {
     // Sec. 3.3: if the whole warp targets one pixel, one lane writes the
@@ -107,9 +155,7 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
       const unsigned long long other_key = __shfl_xor_sync(kFullMask, key, 1);
       if (other_tag == tag) write = vis && key < other_key;
     }
-    if (write) {
-      if (V == PCR_VARIANT_REDUCE || key < load_relaxed_u64(fb + pix)) red_min_u64(fb + pix, key, pol);
-    }
+    if (write && (V == PCR_VARIANT_REDUCE || key < seen)) red_min_u64(fb + pix, key, pol);
   } else {
     // Sec. 5 "just-set": plain store, no depth test; the last writer wins.
     static_assert(V == PCR_VARIANT_JUST_SET, "unknown variant");
@@ -119,16 +165,28 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
   }
 }
 
+// Each chunk runs in three phases so independent memory round trips overlap:
+// project all U points, issue all U early reads, then test and write.
 template <int V, int U>
-__global__ void __launch_bounds__(kThreads) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                            unsigned long long* __restrict__ fb) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_point<U>(pts, n, pol_stream, [&](const uint4& r, uint32_t idx, bool in_range) {
-    uint32_t pix = 0;
-    float w = 0.0f;
-    const bool vis = project_record(v, r, in_range, pix, w);
-    emit_key<V>(fb, vis, pix, w, idx, pol_fb);
+  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+    uint32_t pix[U];
+    float w[U];
+    bool vis[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pix[u] = 0;
+      w[u] = 0.0f;
+      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
+    }
+    unsigned long long seen[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) seen[u] = (reads_early<V>() && vis[u]) ? load_relaxed_u64(fb + pix[u]) : 0ull;
+#pragma unroll
+    for (int u = 0; u < U; ++u) emit_key<V>(fb, vis[u], pix[u], w[u], base + 32u * u, seen[u], pol_fb);
   });
 }
 
@@ -138,33 +196,51 @@ __global__ void __launch_bounds__(kThreads) k_render_basic(const uint4* __restri
 
 template <int V>
 __device__ __forceinline__ void emit_depth(uint32_t* __restrict__ depth, bool vis, uint32_t pix, uint32_t d,
-                                           uint64_t pol) {
+                                           uint32_t seen, uint64_t pol) {
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
     if (vis) red_min_u32(depth + pix, d, pol);
   } else if constexpr (V == PCR_VARIANT_EARLYZ) {
-    if (vis && d < load_relaxed_u32(depth + pix)) red_min_u32(depth + pix, d, pol);
-  } else {
+    if (vis && d < seen) red_min_u32(depth + pix, d, pol);
+  } else if constexpr (V == PCR_VARIANT_DEDUP) {
     // The group's minimum can be written by any of its lanes: the lowest.
-    static_assert(V == PCR_VARIANT_DEDUP || V == PCR_VARIANT_DEDUP_EARLYZ, "unknown depth variant");
     const uint32_t tag = vis ? pix : kNoPixel;
     const uint32_t peers = __match_any_sync(kFullMask, tag);
     const uint32_t dmin = __reduce_min_sync(peers, vis ? d : 0xFFFFFFFFu);
-    if (vis && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
-      if (V == PCR_VARIANT_DEDUP || dmin < load_relaxed_u32(depth + pix)) red_min_u32(depth + pix, dmin, pol);
+    if (vis && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) red_min_u32(depth + pix, dmin, pol);
+  } else {
+    // Early test first, then deduplicate the lanes that are still closer.
+    static_assert(V == PCR_VARIANT_DEDUP_EARLYZ, "unknown depth variant");
+    const bool want = vis && d < seen;
+    const uint32_t active = __ballot_sync(kFullMask, want);
+    if (active != 0 && want) {
+      const uint32_t peers = __match_any_sync(active, pix);
+      const uint32_t dmin = __reduce_min_sync(peers, d);
+      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) red_min_u32(depth + pix, dmin, pol);
     }
   }
 }
 
 template <int V, int U>
-__global__ void __launch_bounds__(kThreads) k_hq_depth(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_depth(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        uint32_t* __restrict__ depth) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_point<U>(pts, n, pol_stream, [&](const uint4& r, uint32_t, bool in_range) {
-    uint32_t pix = 0;
-    float w = 0.0f;
-    const bool vis = project_record(v, r, in_range, pix, w);
-    emit_depth<V>(depth, vis, pix, __float_as_uint(w), pol_fb);
+  constexpr bool kEarly = V == PCR_VARIANT_EARLYZ || V == PCR_VARIANT_DEDUP_EARLYZ;
+  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+    uint32_t pix[U];
+    float w[U];
+    bool vis[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pix[u] = 0;
+      w[u] = 0.0f;
+      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
+    }
+    uint32_t seen[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) seen[u] = (kEarly && vis[u]) ? load_relaxed_u32(depth + pix[u]) : 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) emit_depth<V>(depth, vis[u], pix[u], __float_as_uint(w[u]), seen[u], pol_fb);
   });
 }
 
@@ -172,38 +248,67 @@ __global__ void __launch_bounds__(kThreads) k_hq_depth(const uint4* __restrict__
 // w <= depth * factor.  With AGG, lanes that contribute to the same pixel
 // first sum their colours inside the warp (at most 32 * 255 per channel,
 // so r | g << 16 and b | count << 16 cannot carry), then one lane adds.
+template <bool AGG>
+__device__ __forceinline__ void emit_color(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
+                                           bool contrib, uint32_t pix, uint32_t rgba, uint64_t pol) {
+  const uint32_t cr = rgba & 0xFFu;
+  const uint32_t cg = (rgba >> 8) & 0xFFu;
+  const uint32_t cb = (rgba >> 16) & 0xFFu;
+  if constexpr (!AGG) {
+    if (contrib) {
+      red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
+      red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
+    }
+  } else {
+    // Aggregate only when the contributing lanes share pixels: count the
+    // runs of equal pixels among neighbouring lanes (cheap), and fall back
+    // to plain adds when the warp's pixels are mostly distinct (shuffled
+    // orders), where matching would cost more than it saves.
+    const uint32_t tag = contrib ? pix : kNoPixel;
+    const uint32_t active = __ballot_sync(kFullMask, contrib);
+    const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
+    const uint32_t starts = __ballot_sync(kFullMask, contrib && (lane_id() == 0 || prev != tag));
+    if (__popc(starts) > kAggregateMaxRuns) {
+      if (contrib) {
+        red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
+        red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
+      }
+    } else if (contrib) {
+      const uint32_t peers = __match_any_sync(active, pix);
+      const uint32_t s_rg = __reduce_add_sync(peers, cr | (cg << 16));
+      const uint32_t s_bc = __reduce_add_sync(peers, cb | (1u << 16));
+      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
+        red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol);
+        red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol);
+      }
+    }
+  }
+}
+
 template <bool AGG, int U>
-__global__ void __launch_bounds__(kThreads) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        float factor, const uint32_t* __restrict__ depth,
                                                        unsigned long long* __restrict__ rg,
                                                        unsigned long long* __restrict__ ba) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_point<U>(pts, n, pol_stream, [&](const uint4& r, uint32_t, bool in_range) {
-    uint32_t pix = 0;
-    float w = 0.0f;
-    bool contrib = project_record(v, r, in_range, pix, w);
-    if (contrib) {
-      const float limit = __fmul_rn(__uint_as_float(__ldg(depth + pix)), factor);
-      contrib = w <= limit;
+  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+    uint32_t pix[U];
+    float w[U];
+    bool vis[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pix[u] = 0;
+      w[u] = 0.0f;
+      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
     }
-    const uint32_t cr = r.w & 0xFFu;
-    const uint32_t cg = (r.w >> 8) & 0xFFu;
-    const uint32_t cb = (r.w >> 16) & 0xFFu;
-    if constexpr (!AGG) {
-      if (contrib) {
-        red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol_fb);
-        red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol_fb);
-      }
-    } else {
-      const uint32_t tag = contrib ? pix : kNoPixel;
-      const uint32_t peers = __match_any_sync(kFullMask, tag);
-      const uint32_t s_rg = __reduce_add_sync(peers, contrib ? (cr | (cg << 16)) : 0u);
-      const uint32_t s_bc = __reduce_add_sync(peers, contrib ? (cb | (1u << 16)) : 0u);
-      if (contrib && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
-        red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol_fb);
-        red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol_fb);
-      }
+    uint32_t d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(depth + pix[u]) : 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool contrib = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
+      emit_color<AGG>(rg, ba, contrib, pix[u], r[u].w, pol_fb);
     }
   });
 }
