@@ -262,6 +262,10 @@ uint64_t oracle_splitmix64(uint64_t seed, uint64_t k) {
     return z ^ (z >> 31);
 }
 
+void oracle_counter_keys(uint64_t seed, uint64_t count, uint32_t *keys) {
+    for (uint64_t k = 0; k < count; ++k) keys[k] = (uint32_t)(oracle_splitmix64(seed, k) >> 32);
+}
+
 typedef struct {
     uint32_t key;
     uint32_t index;

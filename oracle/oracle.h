@@ -85,6 +85,10 @@ void oracle_morton_codes(const oracle_point *pts, uint64_t n, uint32_t *codes);
  * generator seeded with `seed`. */
 uint64_t oracle_splitmix64(uint64_t seed, uint64_t k);
 
+/* keys[k] = high 32 bits of oracle_splitmix64(seed, k), k < count: the
+ * batch (or point) keys of the shuffled orders. */
+void oracle_counter_keys(uint64_t seed, uint64_t count, uint32_t *keys);
+
 /* Sec. 4 and Sec. 5 vertex orders.  perm[new] = old.
  * mode 0: Morton order (stable sort by code).
  * mode 1: shuffled Morton: Morton order cut into batches of `batch` points,

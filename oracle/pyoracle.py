@@ -45,6 +45,7 @@ def lib():
             L.oracle_morton_codes.argtypes = [VOIDP, U64, VOIDP]
             L.oracle_splitmix64.argtypes = [U64, U64]
             L.oracle_splitmix64.restype = U64
+            L.oracle_counter_keys.argtypes = [U64, U64, VOIDP]
             L.oracle_reorder.argtypes = [VOIDP, U64, U64, INT, U32, VOIDP]
             L.oracle_reorder.restype = INT
             L.oracle_gather.argtypes = [VOIDP, U64, VOIDP, VOIDP]
@@ -83,6 +84,12 @@ def key(w: float, index: int) -> int:
 
 def splitmix64(seed: int, k: int) -> int:
     return int(lib().oracle_splitmix64(seed & ((1 << 64) - 1), k))
+
+
+def counter_keys(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.uint32)
+    lib().oracle_counter_keys(seed & ((1 << 64) - 1), count, _ptr(out))
+    return out
 
 
 def clear_keys(npx: int) -> np.ndarray:

@@ -87,6 +87,12 @@ def test_splitmix64_published_vector(oracle):
         assert oracle.splitmix64(seed, k) == out
 
 
+def test_counter_keys_match_generator(oracle):
+    keys = oracle.counter_keys(1234567, 5)
+    assert keys.tolist() == [oracle.splitmix64(1234567, k) >> 32 for k in range(5)]
+    assert keys[0] == 6457827717110365317 >> 32
+
+
 @pytest.mark.parametrize("n", [0, 1, 5, 127, 128, 129, 1000, 4097])
 def test_reorder_properties(oracle, n):
     cloud = scenes.random_cloud(n, seed=n).numpy() if n else np.zeros((0, 4), np.int32)
