@@ -208,6 +208,41 @@ PCR_API pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t *bytes);
 PCR_API pcr_status pcr_reorder_morton_shuffle128(pcr_ctx *ctx, void *dev_points, uint64_t n, uint64_t seed, int mode,
                                          void *dev_workspace, uint64_t workspace_bytes, uint32_t *dev_perm_out);
 
+/* Largest cloud pcr_reorder_morton_shuffle128_noalloc accepts. */
+#define PCR_REORDER_NOALLOC_MAX_POINTS 262144u
+
+/* Allocation-free form of pcr_reorder_morton_shuffle128.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory, so cannot provide the reorder workspace.  Examples: a plugin
+ * whose host application hands it only the point buffer; code running where
+ * another allocator (a framework's caching pool) owns the device memory, so
+ * a raw allocation would fail or fragment it; a frame loop that must not
+ * stall, because allocating and freeing device memory synchronises the
+ * device.
+ *
+ * Same orders, arguments and results as pcr_reorder_morton_shuffle128, with
+ * the workspace replaced by a fixed scratch array inside the library.  The
+ * array holds PCR_REORDER_NOALLOC_MAX_POINTS points' worth of workspace
+ * (about 8.5 MB).  It is part of the library's device code, so every GPU that
+ * loads the library holds it until the process exits.
+ *   - n > PCR_REORDER_NOALLOC_MAX_POINTS: returns PCR_ERR_WORKSPACE, launches
+ *     nothing.
+ *   - The first call on a device looks up the array's device address, with
+ *     the context's device current.  Make that first call before any stream
+ *     capture.
+ *   - All calls on a device share the one array and leave their scratch data
+ *     in it.  No call needs it cleared: every scratch word a call reads, it
+ *     has written first.
+ *   - Calls whose work overlaps on the GPU (on different streams, or from
+ *     different contexts on one device) race on the array and corrupt each
+ *     other's results.  Issue them on one stream, or give each its own
+ *     workspace through pcr_reorder_morton_shuffle128.
+ *   - Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Errors: as pcr_reorder_morton_shuffle128, plus PCR_ERR_CUDA if the array's
+ * address cannot be obtained. */
+PCR_API pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx *ctx, void *dev_points, uint64_t n, uint64_t seed,
+                                                         int mode, uint32_t *dev_perm_out);
+
 /* Static, human-readable name of a status code. */
 PCR_API const char *pcr_status_string(pcr_status status);
 

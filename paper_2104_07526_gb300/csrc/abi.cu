@@ -251,6 +251,18 @@ pcr_status pcr_reorder_morton_shuffle128(pcr_ctx* ctx, void* dev_points, uint64_
                                        dev_workspace, dev_perm_out, ctx->stream, ctx->dev));
 }
 
+pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx* ctx, void* dev_points, uint64_t n, uint64_t seed,
+                                                 int mode, uint32_t* dev_perm_out) {
+  if (!ctx || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_SHUFFLE) return PCR_ERR_ARG;
+  if (n > PCR_REORDER_NOALLOC_MAX_POINTS) return PCR_ERR_WORKSPACE;
+  if (n == 0) return PCR_OK;
+  if (!dev_points || !aligned(dev_points, 16) || (dev_perm_out && !aligned(dev_perm_out, 4))) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  return from_cuda(pcr::launch_reorder_noalloc(static_cast<uint4*>(dev_points), static_cast<uint32_t>(n), seed,
+                                               mode, dev_perm_out, ctx->stream, ctx->dev));
+}
+
 const char* pcr_status_string(pcr_status status) {
   switch (status) {
     case PCR_OK: return "ok";

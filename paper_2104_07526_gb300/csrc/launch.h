@@ -35,5 +35,9 @@ cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
 uint64_t reorder_workspace_bytes(uint64_t n);
 cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void* workspace, uint32_t* perm_out,
                            cudaStream_t s, const Device& d);
+// The same reorder on the library's fixed scratch array (no allocation);
+// the caller has made d's device current and checked n against the limit.
+cudaError_t launch_reorder_noalloc(uint4* pts, uint32_t n, uint64_t seed, int mode, uint32_t* perm_out,
+                                   cudaStream_t s, const Device& d);
 
 }  // namespace pcr

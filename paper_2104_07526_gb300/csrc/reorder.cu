@@ -11,6 +11,7 @@
 //      warp by match/popc, across warps by a shared prefix) and write it.
 // Ranks follow index order, so each pass, and the sort, is stable.
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/pcr.h"
 #include "common.cuh"
@@ -33,38 +34,39 @@ constexpr uint32_t kBatch = 128;  // Sec. 4: batches of 128 points
 
 static_assert(kRadix == kSortThreads, "one digit per thread in the sort kernels");
 
-uint64_t align_up(uint64_t v) { return (v + 255) & ~uint64_t(255); }
+constexpr uint64_t align_up(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
-uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+constexpr uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 
 // Workspace layout; every region starts on a 256-byte boundary.
 struct Layout {
   uint64_t pts_copy, keys0, keys1, vals0, vals1, counts, partials, bkeys0, bkeys1, bvals0, bvals1, misc, total;
 };
 
-Layout layout(uint64_t n) {
+constexpr uint64_t region(uint64_t& off, uint64_t bytes) {
+  const uint64_t at = off;
+  off += align_up(bytes > 0 ? bytes : 1);
+  return at;
+}
+
+constexpr Layout layout(uint64_t n) {
   const uint64_t nb = ceil_div(n, kBatch);
   const uint64_t tiles = ceil_div(n > nb ? n : nb, kTile);
   const uint64_t count_words = kRadix * (tiles > 0 ? tiles : 1);
   Layout l{};
   uint64_t off = 0;
-  auto take = [&](uint64_t bytes) {
-    const uint64_t at = off;
-    off += align_up(bytes > 0 ? bytes : 1);
-    return at;
-  };
-  l.pts_copy = take(16 * n);
-  l.keys0 = take(4 * n);
-  l.keys1 = take(4 * n);
-  l.vals0 = take(4 * n);
-  l.vals1 = take(4 * n);
-  l.counts = take(4 * count_words);
-  l.partials = take(4 * ceil_div(count_words, kScanSeg));
-  l.bkeys0 = take(4 * nb);
-  l.bkeys1 = take(4 * nb);
-  l.bvals0 = take(4 * nb);
-  l.bvals1 = take(4 * nb);
-  l.misc = take(64);
+  l.pts_copy = region(off, 16 * n);
+  l.keys0 = region(off, 4 * n);
+  l.keys1 = region(off, 4 * n);
+  l.vals0 = region(off, 4 * n);
+  l.vals1 = region(off, 4 * n);
+  l.counts = region(off, 4 * count_words);
+  l.partials = region(off, 4 * ceil_div(count_words, kScanSeg));
+  l.bkeys0 = region(off, 4 * nb);
+  l.bkeys1 = region(off, 4 * nb);
+  l.bvals0 = region(off, 4 * nb);
+  l.bvals1 = region(off, 4 * nb);
+  l.misc = region(off, 64);
   l.total = off;
   return l;
 }
@@ -435,6 +437,34 @@ unsigned stream_grid(uint64_t count, const Device& d) {
 
 }  // namespace
 
+// Scratch for the allocation-free reorder: one workspace sized for the
+// largest accepted cloud, part of the module's device memory.
+constexpr uint64_t kNoallocScratchBytes = layout(PCR_REORDER_NOALLOC_MAX_POINTS).total;
+static __device__ __align__(256) unsigned char g_reorder_scratch[kNoallocScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_reorder_scratch on `device`, looked up once per device
+// with that device current (host code cannot use the symbol itself).
+cudaError_t noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (g_scratch_addr[device] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_reorder_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[device] = p;
+  }
+  *out = g_scratch_addr[device];
+  return cudaSuccess;
+}
+
+}  // namespace
+
 uint64_t reorder_workspace_bytes(uint64_t n) { return layout(n).total; }
 
 cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void* workspace, uint32_t* perm_out,
@@ -479,6 +509,15 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
   k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
   return cudaGetLastError();
+}
+
+cudaError_t launch_reorder_noalloc(uint4* pts, uint32_t n, uint64_t seed, int mode, uint32_t* perm_out,
+                                   cudaStream_t s, const Device& d) {
+  if (n > PCR_REORDER_NOALLOC_MAX_POINTS) return cudaErrorInvalidValue;
+  void* scratch = nullptr;
+  const cudaError_t e = noalloc_scratch(d.id, &scratch);
+  if (e != cudaSuccess) return e;
+  return launch_reorder(pts, n, seed, mode, scratch, perm_out, s, d);
 }
 
 }  // namespace pcr

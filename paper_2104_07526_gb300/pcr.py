@@ -66,6 +66,7 @@ _SIGS = {
     "pcr_synchronize": [_VP],
     "pcr_reorder_workspace_size": [_U64, C.POINTER(_U64)],
     "pcr_reorder_morton_shuffle128": [_VP, _VP, _U64, _U64, _INT, _VP, _U64, _VP],
+    "pcr_reorder_morton_shuffle128_noalloc": [_VP, _VP, _U64, _U64, _INT, _VP],
     "pcr_last_device_error": [_VP, C.POINTER(_U32)],
 }
 
@@ -210,6 +211,18 @@ def pcr_reorder_morton_shuffle128(ctx: int, points, n: int, seed: int, mode: int
                                                _dptr(workspace, "workspace"),
                                                _nbytes(workspace) if workspace is not None else 0,
                                                _dptr(perm_out, "perm_out")), "pcr_reorder_morton_shuffle128")
+
+
+PCR_REORDER_NOALLOC_MAX_POINTS = 262144
+
+
+def pcr_reorder_morton_shuffle128_noalloc(ctx: int, points, n: int, seed: int, mode: int, perm_out=None):
+    """Reorder without a workspace (the library's fixed scratch array; at
+    most PCR_REORDER_NOALLOC_MAX_POINTS points; calls on one device must not
+    overlap on the GPU)."""
+    _check(lib().pcr_reorder_morton_shuffle128_noalloc(ctx, _dptr(points, "points"), n, seed & ((1 << 64) - 1), mode,
+                                                       _dptr(perm_out, "perm_out")),
+           "pcr_reorder_morton_shuffle128_noalloc")
 
 
 def pcr_last_device_error(ctx: int) -> int:
