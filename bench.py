@@ -448,7 +448,13 @@ def run_ours(args, cfg):
         pcr.pcr_render_hq(h, 1.01, variant, True)
         pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, fb["image"], 0)
 
+    def hq1r_frame():
+        pcr.pcr_render_hq1r(h, 1.01, variant, True)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ1R, fb["image"], 0)
+
+    pcr.pcr_set_hq1r_buffer(h, fb["hq1r_primary"])
     hq_ms = None if args.no_hq else time_loop(hq_frame, stream, reps=max(5, min(K, 50)), warm=3)
+    hq1r_ms = None if args.no_hq else time_loop(hq1r_frame, stream, reps=max(5, min(K, 50)), warm=3)
 
     # --- end to end through the C ABI with host buffers ---------------------------
     e2e = None
@@ -478,7 +484,7 @@ def run_ours(args, cfg):
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view),
             "frame_gbs": n * POINT_BYTES / (ms_per_step * 1e-3) / 1e9,
-            "phases_ms": phase, "hq_frame_ms": hq_ms,
+            "phases_ms": phase, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
             "sweep_ms": sweep,
@@ -549,6 +555,8 @@ def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
             for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ):
                 row["hq:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_hq(h, 1.01, var, True), stream, reps=5, warm=1), 4)
+                row["hq1r:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
+                    lambda: pcr.pcr_render_hq1r(h, 1.01, var, True), stream, reps=5, warm=1), 4)
             out[v.name][oname] = row
     return out
 

@@ -73,7 +73,8 @@ enum {
 
 enum {
     PCR_RESOLVE_BASIC = 0,  /* Sec. 3.1: key buffer -> colour of the winning point */
-    PCR_RESOLVE_HQ = 1      /* Sec. 3.5: colour sums -> truncating average */
+    PCR_RESOLVE_HQ = 1,     /* Sec. 3.5: colour sums -> truncating average */
+    PCR_RESOLVE_HQ1R = 2    /* Sec. 3.5.1: packed primary + fallback sums -> truncating average */
 };
 
 enum {
@@ -163,6 +164,31 @@ PCR_API pcr_status pcr_render_basic(pcr_ctx *ctx, int variant, int clear);
  * viewport or HQ buffers. */
 PCR_API pcr_status pcr_render_hq(pcr_ctx *ctx, float depth_factor, int variant, int clear);
 
+/* Borrow the primary buffer of the single-atomic high-quality variant
+ * (Sec. 3.5.1, "HQS1R"): uint64[width*height], 8-byte aligned, holding
+ * r << 50 | g << 36 | b << 22 | count (14, 14, 14 and 22 bits; see
+ * pcr_render_hq1r).  Its fallback sums live in the dev_hq_rg / dev_hq_ba
+ * buffers of pcr_set_framebuffer (same 32-bit layout as HQS).  NULL detaches
+ * it.  Errors: PCR_ERR_ARG if misaligned. */
+PCR_API pcr_status pcr_set_hq1r_buffer(pcr_ctx *ctx, void *dev_primary);
+
+/* Sec. 3.5.1, "HQS1R": the depth pass of pcr_render_hq, then a colour pass
+ * with one 64-bit atomic add per contributing point (or per group of
+ * same-pixel points of a warp, with the DEDUP variants) into the primary
+ * word.  The paper's 16-16-16-16 pattern leaves 2^16 - 256 counts of margin
+ * for adds that land on a full word before it is reset; a GB300 can have
+ * more adds than that in flight on one pixel, so, as the paper allows, the
+ * pattern here is 14-14-14-22: a word holds at most 64 points and the count
+ * has about 4.2M of margin.  The add whose result would hold more than 64
+ * points moves the previous contents and its own colours into the fallback
+ * sums and resets the word; adds that land while a word is past 64 points go
+ * to the fallback.  Every contribution is counted exactly once, so the
+ * combined sums, and the PCR_RESOLVE_HQ1R image, equal those of
+ * pcr_render_hq.  clear != 0 first sets depth to +inf, the primary words and
+ * the fallback sums to 0.  Errors: as pcr_render_hq, plus PCR_ERR_ARG without
+ * a primary buffer. */
+PCR_API pcr_status pcr_render_hq1r(pcr_ctx *ctx, float depth_factor, int variant, int clear);
+
 /* Screen pass, writing uint32 rgba per pixel into dev_rgba_out
  * (4-byte aligned, width*height words).
  *   PCR_RESOLVE_BASIC (Sec. 3.1): the rgba word of the point whose index the
@@ -171,6 +197,8 @@ PCR_API pcr_status pcr_render_hq(pcr_ctx *ctx, float depth_factor, int variant, 
  *   PCR_RESOLVE_HQ (Sec. 3.5): r = (rg >> 32) / count, g = (rg & 0xffffffff)
  *     / count, b = (ba >> 32) / count with truncating division, each clamped
  *     to 255, alpha 255; background_rgba where count is 0.
+ *   PCR_RESOLVE_HQ1R (Sec. 3.5.1): the same average over the primary word's
+ *     fields plus the fallback sums.
  * Errors: PCR_ERR_ARG for an unknown mode, NULL output or missing buffers. */
 PCR_API pcr_status pcr_resolve(pcr_ctx *ctx, int mode, void *dev_rgba_out, uint32_t background_rgba);
 

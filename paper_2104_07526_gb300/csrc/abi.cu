@@ -20,6 +20,7 @@ struct pcr_ctx {
   uint32_t* depth = nullptr;
   unsigned long long* rg = nullptr;
   unsigned long long* ba = nullptr;
+  unsigned long long* primary = nullptr;  // HQS1R primary words
 };
 
 namespace {
@@ -194,6 +195,32 @@ pcr_status pcr_render_hq(pcr_ctx* ctx, float depth_factor, int variant, int clea
   return from_cuda(e);
 }
 
+pcr_status pcr_set_hq1r_buffer(pcr_ctx* ctx, void* dev_primary) {
+  if (!ctx || (dev_primary && !aligned(dev_primary, 8))) return PCR_ERR_ARG;
+  ctx->primary = static_cast<unsigned long long*>(dev_primary);
+  return PCR_OK;
+}
+
+pcr_status pcr_render_hq1r(pcr_ctx* ctx, float depth_factor, int variant, int clear) {
+  if (!ctx || variant < PCR_VARIANT_ATOMICMIN || variant > PCR_VARIANT_DEDUP_EARLYZ) return PCR_ERR_ARG;
+  if (!(depth_factor > 0.0f) || !(depth_factor < 3.0e38f)) return PCR_ERR_ARG;
+  if (!view_ready(ctx) || !ctx->depth || !ctx->rg || !ctx->ba || !ctx->primary) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  const uint32_t n = static_cast<uint32_t>(ctx->n);
+  const pcr::ViewParams v = view_params(ctx);
+  cudaError_t e = cudaSuccess;
+  if (clear) {
+    e = pcr::launch_clear_hq(ctx->depth, ctx->rg, ctx->ba, pixels(ctx), ctx->stream, ctx->dev);
+    if (e == cudaSuccess) e = pcr::launch_fill_u64(ctx->primary, pixels(ctx), 0ull, ctx->stream, ctx->dev);
+  }
+  if (e == cudaSuccess) e = pcr::launch_hq_depth(variant, ctx->points, n, v, ctx->depth, ctx->stream, ctx->dev);
+  if (e == cudaSuccess)
+    e = pcr::launch_hq1r_color(variant, ctx->points, n, v, depth_factor, ctx->depth, ctx->primary, ctx->rg, ctx->ba,
+                               ctx->stream, ctx->dev);
+  return from_cuda(e);
+}
+
 pcr_status pcr_resolve(pcr_ctx* ctx, int mode, void* dev_rgba_out, uint32_t background_rgba) {
   if (!ctx || !dev_rgba_out || !aligned(dev_rgba_out, 4) || !view_ready(ctx)) return PCR_ERR_ARG;
   uint32_t* out = static_cast<uint32_t*>(dev_rgba_out);
@@ -203,6 +230,13 @@ pcr_status pcr_resolve(pcr_ctx* ctx, int mode, void* dev_rgba_out, uint32_t back
     if (!scope.ok()) return PCR_ERR_CUDA;
     return from_cuda(pcr::launch_resolve_basic(ctx->keys, pixels(ctx), ctx->points, static_cast<uint32_t>(ctx->n),
                                                background_rgba, out, ctx->stream, ctx->dev));
+  }
+  if (mode == PCR_RESOLVE_HQ1R) {
+    if (!ctx->rg || !ctx->ba || !ctx->primary) return PCR_ERR_ARG;
+    DeviceScope scope(ctx->dev.id);
+    if (!scope.ok()) return PCR_ERR_CUDA;
+    return from_cuda(pcr::launch_resolve_hq1r(ctx->primary, ctx->rg, ctx->ba, pixels(ctx), background_rgba, out,
+                                              ctx->stream, ctx->dev));
   }
   if (mode == PCR_RESOLVE_HQ) {
     if (!ctx->rg || !ctx->ba) return PCR_ERR_ARG;

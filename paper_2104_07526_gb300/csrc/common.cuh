@@ -108,6 +108,23 @@ __device__ __forceinline__ void red_add_u64(unsigned long long* p, unsigned long
   asm volatile("red.relaxed.gpu.global.add.u64.L2::cache_hint [%0], %1, %2;" ::"l"(p), "l"(v), "l"(policy));
 }
 
+// Atomic add that returns the previous value (needed by the single-atomic
+// high-quality pass to detect a full primary word).
+__device__ __forceinline__ unsigned long long atom_add_u64(unsigned long long* p, unsigned long long v,
+                                                           uint64_t policy) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.add.u64.L2::cache_hint %0, [%1], %2, %3;"
+               : "=l"(old)
+               : "l"(p), "l"(v), "l"(policy));
+  return old;
+}
+
+__device__ __forceinline__ unsigned long long atom_exch_u64(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.relaxed.gpu.global.exch.b64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v));
+  return old;
+}
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
 }  // namespace pcr

@@ -27,6 +27,12 @@ cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const Vie
                             const Device& d);
 cudaError_t launch_resolve_basic(const unsigned long long* keys, uint64_t npx, const uint4* pts, uint32_t n,
                                  uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
+cudaError_t launch_hq1r_color(int variant, const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor,
+                              const uint32_t* depth, unsigned long long* primary, unsigned long long* rg,
+                              unsigned long long* ba, cudaStream_t s, const Device& d);
+cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigned long long* rg,
+                                const unsigned long long* ba, uint64_t npx, uint32_t background, uint32_t* out,
+                                cudaStream_t s, const Device& d);
 cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
                               uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);

@@ -313,6 +313,104 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_color(const uint4* 
   });
 }
 
+// Sec. 3.5.1, "HQS1R": one 64-bit add per contributing lane, or per group of
+// same-pixel lanes with AGG, into the primary word
+//   r << 50 | g << 36 | b << 22 | count      (14, 14, 14, 22 bits).
+// The paper packs 16-16-16-16 and notes that the pattern must change when
+// more than about 65k adds to one pixel can be in flight at once; on a GB300
+// that many can (152 SMs x 2048 threads x 4 slots), so the count gets 22
+// bits (about 4.2M of margin) and a word holds at most kHq1rLimit = 64
+// points, whose channel sums (at most 64 * 255) fit 14 bits.  Group sums stay
+// below 32 * 255.  Let c be the count the word held before an add of k
+// points.  If c + k > kHq1rLimit the add does not stay in the word: when
+// c <= kHq1rLimit this add crossed the limit, so it resets the word and moves
+// the c points it held (no field has carried) together with its own k points
+// into the 32-bit fallback sums; when c > kHq1rLimit the word is already
+// past the limit (its owner is about to reset it, discarding this add's bits)
+// and the add goes to the fallback.  Each slot's atomic is issued before any
+// slot waits on a returned value.
+constexpr uint32_t kHq1rLimit = 64;
+constexpr int kHq1rShiftR = 50, kHq1rShiftG = 36, kHq1rShiftB = 22;
+constexpr unsigned long long kHq1rChannelMask = 0x3FFFull;
+constexpr unsigned long long kHq1rCountMask = 0x3FFFFFull;
+
+template <bool AGG, int U>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_hq1r_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v, float factor,
+                 const uint32_t* __restrict__ depth, unsigned long long* __restrict__ primary,
+                 unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba) {
+  const uint64_t pol_stream = policy_evict_first();
+  const uint64_t pol_fb = policy_evict_last();
+  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+    uint32_t pix[U];
+    float w[U];
+    bool vis[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pix[u] = 0;
+      w[u] = 0.0f;
+      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
+    }
+    uint32_t d[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(depth + pix[u]) : 0u;
+    bool mine[U];
+    uint32_t sr[U], sg[U], sb[U], k[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool contrib = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
+      sr[u] = r[u].w & 0xFFu;
+      sg[u] = (r[u].w >> 8) & 0xFFu;
+      sb[u] = (r[u].w >> 16) & 0xFFu;
+      k[u] = 1;
+      mine[u] = contrib;
+      if constexpr (AGG) {
+        const uint32_t tag = contrib ? pix[u] : kNoPixel;
+        const uint32_t active = __ballot_sync(kFullMask, contrib);
+        const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
+        const uint32_t starts = __ballot_sync(kFullMask, contrib && (lane_id() == 0 || prev != tag));
+        if (__popc(starts) <= kAggregateMaxRuns && contrib) {
+          const uint32_t peers = __match_any_sync(active, pix[u]);
+          const uint32_t s_rg = __reduce_add_sync(peers, sr[u] | (sg[u] << 16));
+          const uint32_t s_bc = __reduce_add_sync(peers, sb[u] | (1u << 16));
+          mine[u] = lane_id() == static_cast<uint32_t>(__ffs(peers) - 1);
+          sr[u] = s_rg & 0xFFFFu;
+          sg[u] = s_rg >> 16;
+          sb[u] = s_bc & 0xFFFFu;
+          k[u] = s_bc >> 16;
+        }
+      }
+    }
+    unsigned long long old[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      old[u] = 0;
+      if (mine[u]) {
+        const unsigned long long add = (static_cast<unsigned long long>(sr[u]) << kHq1rShiftR) |
+                                       (static_cast<unsigned long long>(sg[u]) << kHq1rShiftG) |
+                                       (static_cast<unsigned long long>(sb[u]) << kHq1rShiftB) | k[u];
+        old[u] = atom_add_u64(primary + pix[u], add, pol_fb);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!mine[u]) continue;
+      const uint32_t c = static_cast<uint32_t>(old[u] & kHq1rCountMask);
+      if (c + k[u] <= kHq1rLimit) continue;
+      uint32_t fr = sr[u], fg = sg[u], fb = sb[u], fk = k[u];
+      if (c <= kHq1rLimit) {
+        atom_exch_u64(primary + pix[u], 0ull);
+        fr += static_cast<uint32_t>((old[u] >> kHq1rShiftR) & kHq1rChannelMask);
+        fg += static_cast<uint32_t>((old[u] >> kHq1rShiftG) & kHq1rChannelMask);
+        fb += static_cast<uint32_t>((old[u] >> kHq1rShiftB) & kHq1rChannelMask);
+        fk += c;
+      }
+      red_add_u64(rg + pix[u], (static_cast<unsigned long long>(fr) << 32) | fg, pol_fb);
+      red_add_u64(ba + pix[u], (static_cast<unsigned long long>(fb) << 32) | fk, pol_fb);
+    }
+  });
+}
+
 // ---------------------------------------------------------------------------
 // Clears and resolves (screen passes)
 // ---------------------------------------------------------------------------
@@ -367,6 +465,27 @@ __global__ void k_resolve_hq(const unsigned long long* __restrict__ rg, const un
       const uint32_t g = min(static_cast<uint32_t>(s_rg) / a, 255u);
       const uint32_t b = min(static_cast<uint32_t>(s_ba >> 32) / a, 255u);
       c = r | (g << 8) | (b << 16) | 0xFF000000u;
+    }
+    out[p] = c;
+  }
+}
+
+// Sec. 3.5.1: average over the primary word's fields plus the fallback sums.
+__global__ void k_resolve_hq1r(const unsigned long long* __restrict__ primary, const unsigned long long* __restrict__ rg,
+                               const unsigned long long* __restrict__ ba, uint64_t npx, uint32_t background,
+                               uint32_t* __restrict__ out) {
+  for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < npx;
+       p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long w1 = primary[p];
+    const unsigned long long s_rg = rg[p];
+    const unsigned long long s_ba = ba[p];
+    const uint32_t a = static_cast<uint32_t>(s_ba) + static_cast<uint32_t>(w1 & kHq1rCountMask);
+    uint32_t c = background;
+    if (a != 0) {
+      const uint32_t sr = static_cast<uint32_t>(s_rg >> 32) + static_cast<uint32_t>((w1 >> kHq1rShiftR) & kHq1rChannelMask);
+      const uint32_t sg = static_cast<uint32_t>(s_rg) + static_cast<uint32_t>((w1 >> kHq1rShiftG) & kHq1rChannelMask);
+      const uint32_t sb = static_cast<uint32_t>(s_ba >> 32) + static_cast<uint32_t>((w1 >> kHq1rShiftB) & kHq1rChannelMask);
+      c = min(sr / a, 255u) | (min(sg / a, 255u) << 8) | (min(sb / a, 255u) << 16) | 0xFF000000u;
     }
     out[p] = c;
   }
@@ -471,6 +590,28 @@ cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const Vie
     constexpr auto k = k_hq_color<false, kUnroll>;
     k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, rg, ba);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hq1r_color(int variant, const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor,
+                              const uint32_t* depth, unsigned long long* primary, unsigned long long* rg,
+                              unsigned long long* ba, cudaStream_t s, const Device& d) {
+  if (n == 0) return cudaSuccess;
+  if (variant == PCR_VARIANT_DEDUP || variant == PCR_VARIANT_DEDUP_EARLYZ) {
+    constexpr auto k = k_hq1r_color<true, kUnroll>;
+    k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, primary, rg, ba);
+  } else {
+    constexpr auto k = k_hq1r_color<false, kUnroll>;
+    k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, primary, rg, ba);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigned long long* rg,
+                                const unsigned long long* ba, uint64_t npx, uint32_t background, uint32_t* out,
+                                cudaStream_t s, const Device& d) {
+  if (npx == 0) return cudaSuccess;
+  k_resolve_hq1r<<<screen_grid(npx, d), kThreads, 0, s>>>(primary, rg, ba, npx, background, out);
   return cudaGetLastError();
 }
 

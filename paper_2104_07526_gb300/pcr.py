@@ -30,6 +30,7 @@ VARIANT_NAMES = {0: "atomicMin", 1: "early-z", 2: "dedup", 3: "dedup+early-z", 4
 
 PCR_RESOLVE_BASIC = 0
 PCR_RESOLVE_HQ = 1
+PCR_RESOLVE_HQ1R = 2
 
 PCR_CLEAR_KEYS = 1
 PCR_CLEAR_HQ = 2
@@ -62,6 +63,8 @@ _SIGS = {
     "pcr_render_basic": [_VP, _INT, _INT],
     "pcr_render_hq": [_VP, _FLT, _INT, _INT],
     "pcr_resolve": [_VP, _INT, _VP, _U32],
+    "pcr_set_hq1r_buffer": [_VP, _VP],
+    "pcr_render_hq1r": [_VP, _FLT, _INT, _INT],
     "pcr_download": [_VP, _VP, _VP, _U64],
     "pcr_synchronize": [_VP],
     "pcr_reorder_workspace_size": [_U64, C.POINTER(_U64)],
@@ -186,6 +189,15 @@ def pcr_render_hq(ctx: int, depth_factor: float = 1.01, variant: int = PCR_VARIA
     _check(lib().pcr_render_hq(ctx, depth_factor, variant, int(bool(clear))), "pcr_render_hq")
 
 
+def pcr_set_hq1r_buffer(ctx: int, primary=None):
+    _check(lib().pcr_set_hq1r_buffer(ctx, _dptr(primary, "primary")), "pcr_set_hq1r_buffer")
+
+
+def pcr_render_hq1r(ctx: int, depth_factor: float = 1.01, variant: int = PCR_VARIANT_DEDUP_EARLYZ,
+                    clear: bool = True):
+    _check(lib().pcr_render_hq1r(ctx, depth_factor, variant, int(bool(clear))), "pcr_render_hq1r")
+
+
 def pcr_resolve(ctx: int, mode: int, out, background_rgba: int = 0):
     _check(lib().pcr_resolve(ctx, mode, _dptr(out, "out"), background_rgba & 0xFFFFFFFF), "pcr_resolve")
 
@@ -246,6 +258,7 @@ def alloc_framebuffer(width: int, height: int, device="cuda", hq: bool = True) -
         fb["hq_depth"] = torch.empty(npx, dtype=torch.int32, device=device)
         fb["hq_rg"] = torch.empty(npx, dtype=torch.int64, device=device)
         fb["hq_ba"] = torch.empty(npx, dtype=torch.int64, device=device)
+        fb["hq1r_primary"] = torch.empty(npx, dtype=torch.int64, device=device)
     return fb
 
 

@@ -44,6 +44,7 @@ class Renderer:
             self.fb = pcr.alloc_framebuffer(width, height)
             self.size = (width, height)
             pcr.pcr_set_framebuffer(self.h, self.fb["keys"], self.fb["hq_depth"], self.fb["hq_rg"], self.fb["hq_ba"])
+            pcr.pcr_set_hq1r_buffer(self.h, self.fb["hq1r_primary"])
 
     def render_basic(self, variant: int, clear: bool = True) -> np.ndarray:
         pcr.pcr_render_basic(self.h, variant, clear)
@@ -58,6 +59,23 @@ class Renderer:
         torch.cuda.synchronize()
         return (self.fb["hq_depth"].cpu().numpy().view(np.uint32), self.fb["hq_rg"].cpu().numpy().view(np.uint64),
                 self.fb["hq_ba"].cpu().numpy().view(np.uint64))
+
+    def render_hq1r_sums(self, variant: int, factor: float = 1.01):
+        """HQS1R render; returns (depth, r, g, b, count) with the primary
+        word's fields (r 14 bits at 50, g 14 at 36, b 14 at 22, count 22 at
+        0) added to the 32-bit fallback sums."""
+        pcr.pcr_render_hq1r(self.h, factor, variant, True)
+        torch.cuda.synchronize()
+        p = self.fb["hq1r_primary"].cpu().numpy().view(np.uint64)
+        rg = self.fb["hq_rg"].cpu().numpy().view(np.uint64)
+        ba = self.fb["hq_ba"].cpu().numpy().view(np.uint64)
+        m14, m22, m32 = np.uint64(0x3FFF), np.uint64(0x3FFFFF), np.uint64(0xFFFFFFFF)
+        r = (rg >> np.uint64(32)) + ((p >> np.uint64(50)) & m14)
+        g = (rg & m32) + ((p >> np.uint64(36)) & m14)
+        b = (ba >> np.uint64(32)) + ((p >> np.uint64(22)) & m14)
+        c = (ba & m32) + (p & m22)
+        d = self.fb["hq_depth"].cpu().numpy().view(np.uint32)
+        return d, r, g, b, c
 
     def resolve(self, mode: int, background: int = 0) -> np.ndarray:
         pcr.pcr_resolve(self.h, mode, self.fb["image"], background)

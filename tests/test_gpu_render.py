@@ -221,3 +221,62 @@ def test_hq_ragged(r, oracle):
             got = r.render_hq(v, 1.01)
             for a, b in zip(got, e):
                 assert np.array_equal(a, b), (n, v)
+
+
+# --- Sec. 3.5.1 HQS1R -----------------------------------------------------------
+
+def _hq1r_check(r, oracle, cloud, m, W, H, factor=1.01, variants=(0, 1, 2, 3)):
+    d0, rg0, ba0 = oracle.render_hq(cloud, m, W, H, factor)
+    sums = oracle.hq_channel_sums(cloud, m, W, H, d0, factor)
+    img0 = oracle.resolve_hq(rg0, ba0, 0x0A0B0C0D)
+    for v in variants:
+        d, *got = r.render_hq1r_sums(v, factor)
+        assert np.array_equal(d, d0), v
+        for a, b in zip(got, sums):
+            assert np.array_equal(a, b), v
+        assert np.array_equal(r.resolve(pcr.PCR_RESOLVE_HQ1R, 0x0A0B0C0D), img0), v
+
+
+def test_hq1r_sphere(r, oracle, sphere):
+    view = scenes.sphere_plane_views()[0]
+    r.upload(sphere)
+    r.view(view.matrix, view.width, view.height)
+    _hq1r_check(r, oracle, sphere, view.matrix, view.width, view.height)
+
+
+def test_hq1r_constructed_and_ragged(r, oracle):
+    rng = np.random.default_rng(12)
+    cloud, _, _ = cs.hq_scene(rng, npix=3000)
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    _hq1r_check(r, oracle, cloud, cs.camera(), cs.W, cs.H)
+    for n in (0, 1, 129):
+        small = scenes.random_cloud(n, seed=n).numpy() if n else np.zeros((0, 4), np.int32)
+        m = scenes.camera((0.3, -2.2, 1.0), (0, 0, 0), (0, 0, 1), 20, 15)
+        r.upload(small)
+        r.view(m, 20, 15)
+        _hq1r_check(r, oracle, small, m, 20, 15, variants=(0, 3))
+
+
+def test_hq1r_overflow_protocol(r, oracle):
+    """Hundreds of thousands of points on a few pixels: the primary word
+    crosses 255 points again and again; every contribution must still be
+    counted exactly once."""
+    n = 400_000
+    rng = np.random.default_rng(13)
+    px = rng.integers(0, 3, size=n)
+    d = 2.0 + rng.integers(0, 4, size=n) / 1024.0
+    pts = np.stack([cs.point_on_pixel(300 + int(k), 200, 2.0) for k in range(3)])
+    xyz = pts[px].copy()
+    xyz[:, 2] = cs.EYE_Z - d
+    # keep the pixel: scale x, y with the depth so each point stays on its ray
+    xyz[:, 0] *= d / 2.0
+    xyz[:, 1] *= d / 2.0
+    col = rng.integers(0, 256, size=(n, 3))
+    cloud = cs.pack(xyz, cs.rgba_word(col[:, 0], col[:, 1], col[:, 2]))
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    _hq1r_check(r, oracle, cloud, cs.camera(), cs.W, cs.H)
+    d0, *_ = oracle.render_hq(cloud, cs.camera(), cs.W, cs.H, 1.01)
+    counts = oracle.hq_channel_sums(cloud, cs.camera(), cs.W, cs.H, d0, 1.01)[3]
+    assert sorted(counts[counts > 0].tolist())[-1] > 100_000  # heavy pixels really were exercised
