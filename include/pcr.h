@@ -277,8 +277,6 @@ PCR_API const char *pcr_status_string(pcr_status status);
 /* Read and clear the device-side error word of the context's device
  * (synchronises the stream).  Bit 0: a resolve found a key naming a point
  * index outside the borrowed cloud (the pixel took the background colour).
- * Bit 1: a bounded device-side wait gave up (the kernel stopped early, so its
- * output is incomplete).
  * *code is 0 when nothing was reported.  Errors: PCR_ERR_ARG if code is NULL,
  * PCR_ERR_CUDA if the read fails. */
 PCR_API pcr_status pcr_last_device_error(pcr_ctx *ctx, uint32_t *code);
