@@ -20,8 +20,9 @@
  *  - Every call returns a pcr_status.  No C++ exception crosses this
  *    interface and no call aborts the process.
  *  - The caller owns all device memory.  The library borrows pointers for
- *    the duration of the work it launches and never frees them.  Apart from
- *    the context itself (host memory) the library allocates nothing.
+ *    the duration of the work it launches and never frees them.  It
+ *    allocates no device buffers; the context is host memory, and the graphs
+ *    and events some calls create hold only driver resources.
  *  - Calls that launch GPU work are asynchronous on the context's stream
  *    (see pcr_set_stream).  Arguments are checked before anything is
  *    launched; a call that returns PCR_ERR_ARG or PCR_ERR_WORKSPACE has
@@ -235,6 +236,87 @@ PCR_API pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t *bytes);
  * workspace_bytes is too small or the workspace is NULL. */
 PCR_API pcr_status pcr_reorder_morton_shuffle128(pcr_ctx *ctx, void *dev_points, uint64_t n, uint64_t seed, int mode,
                                          void *dev_workspace, uint64_t workspace_bytes, uint32_t *dev_perm_out);
+
+/* ------------------------------------------------------------------------ */
+/* Batched rendering: many (cloud, view, resolution) jobs at once.  The paper  */
+/* renders one view per dispatch (Sec. 5 notes the per-dispatch overhead and   */
+/* the cost of many small buffers, Sec. 5.4); this interface renders all views */
+/* of several clouds in one sequence of four kernels that can be captured as   */
+/* one CUDA graph, reading each cloud's points once per phase for all of its   */
+/* views.                                                                      */
+/* ------------------------------------------------------------------------ */
+
+#define PCR_BATCH_MAX_CLOUDS 256u
+#define PCR_BATCH_MAX_VIEWS 256u
+
+enum {
+    PCR_BATCH_BASIC = 1,  /* basic frame: key buffer (dedup + early-z) and image */
+    PCR_BATCH_HQ = 2      /* high-quality frame: depth, sums and image */
+};
+
+typedef struct pcr_batch_cloud {
+    const void *points;   /* device, n 16-byte records, 16-byte aligned */
+    uint64_t n;           /* < 2^32 */
+} pcr_batch_cloud;
+
+typedef struct pcr_batch_view {
+    float matrix[16];     /* row-major, as pcr_set_matrix */
+    int32_t width;        /* 1..16384 */
+    int32_t height;       /* 1..16384 */
+    uint32_t cloud;       /* index into the clouds array */
+    uint32_t flags;       /* PCR_BATCH_BASIC and/or PCR_BATCH_HQ */
+    void *keys;           /* BASIC: uint64[w*h], 8-byte aligned */
+    void *image;          /* BASIC: uint32[w*h] rgba, or NULL to skip the resolve */
+    void *hq_depth;       /* HQ: uint32[w*h] */
+    void *hq_rg;          /* HQ: uint64[w*h] */
+    void *hq_ba;          /* HQ: uint64[w*h] */
+    void *hq_image;       /* HQ: uint32[w*h] rgba, or NULL to skip the resolve */
+} pcr_batch_view;
+
+/* Bytes of device workspace a batch needs (host-only computation). */
+PCR_API pcr_status pcr_batch_workspace_size(uint64_t *bytes);
+
+/* Number of launch configurations pcr_batch_launch accepts (0 .. n-1);
+ * pcr_batch_autotune picks among them. */
+PCR_API pcr_status pcr_batch_num_configs(int *count);
+
+/* Describe a batch: copy the job tables (clouds, views grouped by cloud)
+ * into dev_workspace (256-byte aligned, at least pcr_batch_workspace_size
+ * bytes) on the context's stream, and wait for the copy.  The arrays are
+ * read during the call only; the buffers they point to are borrowed by every
+ * later launch of this workspace.  Each view gets the frames its flags name,
+ * with the results of pcr_render_basic(PCR_VARIANT_DEDUP_EARLYZ, clear) +
+ * pcr_resolve(BASIC) and of pcr_render_hq(depth_factor, DEDUP_EARLYZ, clear) +
+ * pcr_resolve(HQ), bit for bit.  Errors: PCR_ERR_ARG for counts of 0 or
+ * above the maxima, a bad cloud index, size, flags, pointer or alignment, or
+ * a bad depth_factor; PCR_ERR_WORKSPACE for a missing or small workspace. */
+PCR_API pcr_status pcr_batch_prepare(pcr_ctx *ctx, const pcr_batch_cloud *clouds, uint32_t num_clouds,
+                                     const pcr_batch_view *views, uint32_t num_views, float depth_factor,
+                                     uint32_t background_rgba, void *dev_workspace, uint64_t workspace_bytes);
+
+/* Render a prepared batch: clear, geometry phase 1 (keys and HQ depth),
+ * geometry phase 2 (HQ colours), resolve; four kernel launches on the
+ * context's stream with launch configuration `config`.  Makes no other CUDA
+ * call, so it can be recorded by stream capture.  Errors: PCR_ERR_ARG for a
+ * bad config or workspace pointer. */
+PCR_API pcr_status pcr_batch_launch(pcr_ctx *ctx, const void *dev_workspace, int config);
+
+/* Time every launch configuration on the prepared batch (each rendered a few
+ * times; the outputs are overwritten) and return the fastest in *config.
+ * Synchronises the stream.  Errors: PCR_ERR_ARG on NULL arguments. */
+PCR_API pcr_status pcr_batch_autotune(pcr_ctx *ctx, const void *dev_workspace, int *config);
+
+/* Record pcr_batch_launch(config) into a CUDA graph and instantiate it;
+ * *graph_exec receives a cudaGraphExec_t.  Launch it with pcr_graph_launch,
+ * free it with pcr_graph_destroy.  Errors: PCR_ERR_ARG on NULL arguments or
+ * a bad config, PCR_ERR_CUDA if capture or instantiation fails. */
+PCR_API pcr_status pcr_batch_capture(pcr_ctx *ctx, const void *dev_workspace, int config, void **graph_exec);
+
+/* Launch an instantiated graph on the context's stream. */
+PCR_API pcr_status pcr_graph_launch(pcr_ctx *ctx, void *graph_exec);
+
+/* Destroy an instantiated graph (NULL is accepted). */
+PCR_API pcr_status pcr_graph_destroy(void *graph_exec);
 
 /* Largest cloud pcr_reorder_morton_shuffle128_noalloc accepts. */
 #define PCR_REORDER_NOALLOC_MAX_POINTS 262144u

@@ -297,6 +297,128 @@ pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx* ctx, void* dev_points,
                                                mode, dev_perm_out, ctx->stream, ctx->dev));
 }
 
+pcr_status pcr_batch_workspace_size(uint64_t* bytes) {
+  if (!bytes) return PCR_ERR_ARG;
+  *bytes = pcr::batch_workspace_bytes();
+  return PCR_OK;
+}
+
+pcr_status pcr_batch_num_configs(int* count) {
+  if (!count) return PCR_ERR_ARG;
+  *count = pcr::batch_num_configs();
+  return PCR_OK;
+}
+
+pcr_status pcr_batch_prepare(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t num_clouds,
+                             const pcr_batch_view* views, uint32_t num_views, float depth_factor,
+                             uint32_t background_rgba, void* dev_workspace, uint64_t workspace_bytes) {
+  if (!ctx || !clouds || !views) return PCR_ERR_ARG;
+  if (num_clouds == 0 || num_clouds > PCR_BATCH_MAX_CLOUDS || num_views == 0 || num_views > PCR_BATCH_MAX_VIEWS)
+    return PCR_ERR_ARG;
+  if (!(depth_factor > 0.0f) || !(depth_factor < 3.0e38f)) return PCR_ERR_ARG;
+  for (uint32_t c = 0; c < num_clouds; ++c) {
+    if (clouds[c].n > kMaxPoints) return PCR_ERR_ARG;
+    if (clouds[c].n > 0 && (!clouds[c].points || !aligned(clouds[c].points, 16))) return PCR_ERR_ARG;
+  }
+  for (uint32_t i = 0; i < num_views; ++i) {
+    const pcr_batch_view& v = views[i];
+    if (v.cloud >= num_clouds || v.width < 1 || v.height < 1 || v.width > kMaxViewport || v.height > kMaxViewport)
+      return PCR_ERR_ARG;
+    if (v.flags == 0 || (v.flags & ~static_cast<uint32_t>(PCR_BATCH_BASIC | PCR_BATCH_HQ))) return PCR_ERR_ARG;
+    if ((v.flags & PCR_BATCH_BASIC) &&
+        (!v.keys || !aligned(v.keys, 8) || (v.image && !aligned(v.image, 4))))
+      return PCR_ERR_ARG;
+    if ((v.flags & PCR_BATCH_HQ) && (!v.hq_depth || !aligned(v.hq_depth, 4) || !v.hq_rg || !aligned(v.hq_rg, 8) ||
+                                     !v.hq_ba || !aligned(v.hq_ba, 8) || (v.hq_image && !aligned(v.hq_image, 4))))
+      return PCR_ERR_ARG;
+  }
+  if (!dev_workspace || !aligned(dev_workspace, 256) || workspace_bytes < pcr::batch_workspace_bytes())
+    return PCR_ERR_WORKSPACE;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  return from_cuda(pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba,
+                                      dev_workspace, ctx->stream));
+}
+
+pcr_status pcr_batch_launch(pcr_ctx* ctx, const void* dev_workspace, int config) {
+  if (!ctx || !dev_workspace || !aligned(dev_workspace, 256) || config < 0 || config >= pcr::batch_num_configs())
+    return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  return from_cuda(pcr::batch_launch(dev_workspace, config, ctx->stream, ctx->dev));
+}
+
+pcr_status pcr_batch_autotune(pcr_ctx* ctx, const void* dev_workspace, int* config) {
+  if (!ctx || !dev_workspace || !config || !aligned(dev_workspace, 256)) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return PCR_ERR_CUDA;
+  }
+  int best = 0;
+  float best_ms = 0.0f;
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < pcr::batch_num_configs() && e == cudaSuccess; ++c) {
+    e = pcr::batch_launch(dev_workspace, c, ctx->stream, ctx->dev);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = pcr::batch_launch(dev_workspace, c, ctx->stream, ctx->dev);
+    if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && (c == 0 || ms < best_ms)) {
+      best = c;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return PCR_ERR_CUDA;
+  *config = best;
+  return PCR_OK;
+}
+
+pcr_status pcr_batch_capture(pcr_ctx* ctx, const void* dev_workspace, int config, void** graph_exec) {
+  if (!ctx || !dev_workspace || !graph_exec || !aligned(dev_workspace, 256) || config < 0 ||
+      config >= pcr::batch_num_configs())
+    return PCR_ERR_ARG;
+  *graph_exec = nullptr;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  cudaError_t e = pcr::batch_prewarm(ctx->dev);  // occupancy queries happen before the capture
+  if (e != cudaSuccess) return PCR_ERR_CUDA;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PCR_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t le = pcr::batch_launch(dev_workspace, config, cs, ctx->dev);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (le != cudaSuccess) e = le;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return PCR_ERR_CUDA;
+  *graph_exec = exec;
+  return PCR_OK;
+}
+
+pcr_status pcr_graph_launch(pcr_ctx* ctx, void* graph_exec) {
+  if (!ctx || !graph_exec) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  return from_cuda(cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), ctx->stream));
+}
+
+pcr_status pcr_graph_destroy(void* graph_exec) {
+  if (graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec));
+  return PCR_OK;
+}
+
 const char* pcr_status_string(pcr_status status) {
   switch (status) {
     case PCR_OK: return "ok";

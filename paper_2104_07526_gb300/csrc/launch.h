@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/pcr.h"
 #include "common.cuh"
 
 namespace pcr {
@@ -36,6 +37,53 @@ cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigne
 cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
                               uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
+
+// Batched rendering (batch.cu).  Tables live in the caller's workspace;
+// views are grouped by cloud.
+constexpr uint32_t kBatchMaxClouds = PCR_BATCH_MAX_CLOUDS;
+constexpr uint32_t kBatchMaxViews = PCR_BATCH_MAX_VIEWS;
+
+struct BatchHeader {
+  uint32_t num_clouds;
+  uint32_t num_views;
+  uint64_t total_slots;   // sum of cloud sizes, each padded to 128 points
+  uint64_t total_pixels;  // sum of view sizes
+  uint32_t hq_views;
+  uint32_t background;
+  float depth_factor;
+  uint32_t pad;
+};
+
+struct BatchCloud {
+  const uint4* pts;
+  uint32_t n;
+  uint32_t first_view;  // this cloud's views are [first_view, first_view + num_views)
+  uint32_t num_views;
+  uint32_t hq_views;
+  uint64_t first_slot;  // offset of this cloud in the padded point sequence
+};
+
+struct BatchView {
+  ViewParams vp;
+  uint32_t cloud;
+  uint32_t flags;
+  unsigned long long* keys;
+  uint32_t* image;
+  uint32_t* depth;
+  unsigned long long* rg;
+  unsigned long long* ba;
+  uint32_t* hq_image;
+  uint64_t first_pixel;  // offset of this view in the concatenated pixels
+};
+
+uint64_t batch_workspace_bytes();
+int batch_num_configs();
+cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
+                          uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
+                          cudaStream_t s);
+cudaError_t batch_launch(const void* workspace, int config, cudaStream_t s, const Device& d);
+// Run the occupancy queries of every configuration once (before a capture).
+cudaError_t batch_prewarm(const Device& d);
 
 // Vertex order (reorder.cu).
 uint64_t reorder_workspace_bytes(uint64_t n);

@@ -12,11 +12,14 @@
 
 #include "../../include/pcr.h"
 #include "common.cuh"
+#include "geometry.cuh"
 #include "launch.h"
 
 namespace pcr {
 
 namespace {
+
+using namespace geom;
 
 __device__ uint32_t g_error_word;
 
@@ -32,139 +35,6 @@ constexpr int kThreads = 256;
 // kernels are compiled for (a register cap).
 constexpr int kUnroll = PCR_GEOMETRY_UNROLL;
 constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
-// HQ colour pass: above this many runs of equal pixels in a warp row the
-// warp adds directly instead of aggregating.
-constexpr int kAggregateMaxRuns = 12;
-
-__device__ __forceinline__ unsigned long long make_key(float w, uint32_t idx) {
-  return (static_cast<unsigned long long>(__float_as_uint(w)) << 32) | idx;
-}
-
-// Walk the point chunks of this warp.  For each chunk, f(r, base, full)
-// gets the U records of this lane (slot u holds point base + 32u), and
-// `full` as a compile-time flag: true when every slot of the chunk lies
-// inside the cloud.  Every lane of the warp calls f the same number of times,
-// so f may use warp-collective operations.
-template <int U, class F>
-__device__ __forceinline__ void for_each_chunk(const uint4* __restrict__ pts, uint32_t n, uint64_t pol, F&& f) {
-  const uint64_t warps_per_block = blockDim.x >> 5;
-  const uint64_t warp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
-  const uint64_t nwarps = gridDim.x * warps_per_block;
-  constexpr uint64_t kChunk = 32ull * U;
-  const uint64_t nfull = n / kChunk;
-  const uint32_t lane = lane_id();
-  uint64_t c = warp;
-  for (; c < nfull; c += nwarps) {
-    const uint32_t base = static_cast<uint32_t>(c * kChunk) + lane;
-    uint4 r[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) r[u] = load_point_stream(pts + base + 32u * u, pol);
-    f(r, base, std::true_type{});
-  }
-  if (c == nfull && nfull * kChunk < n) {  // the one ragged chunk, if any
-    const uint64_t base = c * kChunk + lane;
-    uint4 r[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + 32ull * u;
-      r[u] = (i < n) ? load_point_stream(pts + i, pol) : make_uint4(0u, 0u, 0u, 0u);
-    }
-    f(r, static_cast<uint32_t>(base), std::false_type{});
-  }
-}
-
-template <class Full>
-__device__ __forceinline__ bool slot_in_range(uint32_t base, int u, uint32_t n, Full) {
-  if constexpr (Full::value) {
-    return true;
-  } else {
-    return static_cast<uint64_t>(base) + 32ull * u < n;
-  }
-}
-
-__device__ __forceinline__ bool project_record(const ViewParams& v, const uint4& r, uint32_t& pix, float& w) {
-  return project(v, __uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z), pix, w);
-}
-
-// ---------------------------------------------------------------------------
-// Sec. 3.1-3.4: basic key render
-// ---------------------------------------------------------------------------
-
-template <int V>
-__host__ __device__ constexpr bool reads_early() {
-  return V == PCR_VARIANT_EARLYZ || V == PCR_VARIANT_DEDUP_EARLYZ || V == PCR_VARIANT_REDUCE_EARLYZ;
-}
-
-// One point slot after projection.  `seen` is this lane's earlier read of
-// its pixel (variants with the early test only).
-template <int V>
-__device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix, float w,
-                                         uint32_t idx, unsigned long long seen, uint64_t pol) {
-  const unsigned long long key = make_key(w, idx);
-  if constexpr (V == PCR_VARIANT_ATOMICMIN) {
-    // Sec. 3.1: atomicMin(framebuffer[pixelID], point)
-    if (vis) red_min_u64(fb + pix, key, pol);
-  } else if constexpr (V == PCR_VARIANT_EARLYZ) {
-    // Sec. 3.2: only call the atomic when the point is closer than what the
-    // buffer (possibly stale, never too small) holds.
-    if (vis && key < seen) red_min_u64(fb + pix, key, pol);
-  } else if constexpr (V == PCR_VARIANT_DEDUP) {
-    // Sec. 3.4: lanes with the same pixel form a group; only the lane with
-    // the group's smallest key writes.  Keys reduce on the full 64 bits
-    // (depth, then index), so each distinct pixel costs one atomic per warp
-    // even when depths tie.  Within a row of the chunk the index grows with
-    // the lane, so the smallest index among the smallest depths is the
-    // lowest such lane.
-    const uint32_t tag = vis ? pix : kNoPixel;
-    const uint32_t peers = __match_any_sync(kFullMask, tag);
-    const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
-    const uint32_t hmin = __reduce_min_sync(peers, hi);
-    const uint32_t tied = __ballot_sync(kFullMask, hi == hmin) & peers;
-    if (vis && lane_id() == static_cast<uint32_t>(__ffs(tied) - 1)) red_min_u64(fb + pix, key, pol);
-  } else if constexpr (V == PCR_VARIANT_DEDUP_EARLYZ) {
-    // Sec. 3.4 with Sec. 3.2, tests swapped: every visible lane has read its
-    // pixel already (cheap, mostly L2 hits); only lanes still closer than the
-    // buffer take part in the deduplication, which the whole warp skips when
-    // none is left.  A lane dropped by the early test can never hold a
-    // pixel's final minimum, so the set of writers still contains it and the
-    // buffer is the same.
-    const bool want = vis && key < seen;
-    const uint32_t active = __ballot_sync(kFullMask, want);
-    if (active != 0 && want) {
-      const uint32_t peers = __match_any_sync(active, pix);
-      const uint32_t hi = __float_as_uint(w);
-      const uint32_t hmin = __reduce_min_sync(peers, hi);
-      const uint32_t first = __reduce_min_sync(peers, hi == hmin ? lane_id() : 32u);
-      if (lane_id() == first) red_min_u64(fb + pix, key, pol);
-    }
-  } else if constexpr (V == PCR_VARIANT_REDUCE || V == PCR_VARIANT_REDUCE_EARLYZ) {
-    // Sec. 3.3: if the whole warp targets one pixel, one lane writes the
-    // warp's minimum; otherwise pairs of neighbouring lanes merge when they
-    // share a pixel (the smaller key writes).
-    const uint32_t tag = vis ? pix : kNoPixel;
-    int all_equal = 0;
-    __match_all_sync(kFullMask, tag, &all_equal);
-    bool write = vis;
-    if (all_equal) {
-      const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
-      const uint32_t hmin = __reduce_min_sync(kFullMask, hi);
-      const uint32_t tied = __ballot_sync(kFullMask, hi == hmin);
-      write = vis && lane_id() == static_cast<uint32_t>(__ffs(tied) - 1);
-    } else {
-      const uint32_t other_tag = __shfl_xor_sync(kFullMask, tag, 1);
-      const unsigned long long other_key = __shfl_xor_sync(kFullMask, key, 1);
-      if (other_tag == tag) write = vis && key < other_key;
-    }
-    if (write && (V == PCR_VARIANT_REDUCE || key < seen)) red_min_u64(fb + pix, key, pol);
-  } else {
-    // Sec. 5 "just-set": plain store, no depth test; the last writer wins.
-    static_assert(V == PCR_VARIANT_JUST_SET, "unknown variant");
-    if (vis) {
-      asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(fb + pix), "l"(key));
-    }
-  }
-}
-
 // Each chunk runs in three phases so independent memory round trips overlap:
 // project all U points, issue all U early reads, then test and write.
 template <int V, int U>
@@ -194,32 +64,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_basic(const uin
 // Sec. 3.5: high-quality passes
 // ---------------------------------------------------------------------------
 
-template <int V>
-__device__ __forceinline__ void emit_depth(uint32_t* __restrict__ depth, bool vis, uint32_t pix, uint32_t d,
-                                           uint32_t seen, uint64_t pol) {
-  if constexpr (V == PCR_VARIANT_ATOMICMIN) {
-    if (vis) red_min_u32(depth + pix, d, pol);
-  } else if constexpr (V == PCR_VARIANT_EARLYZ) {
-    if (vis && d < seen) red_min_u32(depth + pix, d, pol);
-  } else if constexpr (V == PCR_VARIANT_DEDUP) {
-    // The group's minimum can be written by any of its lanes: the lowest.
-    const uint32_t tag = vis ? pix : kNoPixel;
-    const uint32_t peers = __match_any_sync(kFullMask, tag);
-    const uint32_t dmin = __reduce_min_sync(peers, vis ? d : 0xFFFFFFFFu);
-    if (vis && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) red_min_u32(depth + pix, dmin, pol);
-  } else {
-    // Early test first, then deduplicate the lanes that are still closer.
-    static_assert(V == PCR_VARIANT_DEDUP_EARLYZ, "unknown depth variant");
-    const bool want = vis && d < seen;
-    const uint32_t active = __ballot_sync(kFullMask, want);
-    if (active != 0 && want) {
-      const uint32_t peers = __match_any_sync(active, pix);
-      const uint32_t dmin = __reduce_min_sync(peers, d);
-      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) red_min_u32(depth + pix, dmin, pol);
-    }
-  }
-}
-
 template <int V, int U>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_depth(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        uint32_t* __restrict__ depth) {
@@ -244,47 +88,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_depth(const uint4* 
   });
 }
 
-// Colour pass (Listing "hqs_render"): a visible point contributes when
-// w <= depth * factor.  With AGG, lanes that contribute to the same pixel
-// first sum their colours inside the warp (at most 32 * 255 per channel,
-// so r | g << 16 and b | count << 16 cannot carry), then one lane adds.
-template <bool AGG>
-__device__ __forceinline__ void emit_color(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
-                                           bool contrib, uint32_t pix, uint32_t rgba, uint64_t pol) {
-  const uint32_t cr = rgba & 0xFFu;
-  const uint32_t cg = (rgba >> 8) & 0xFFu;
-  const uint32_t cb = (rgba >> 16) & 0xFFu;
-  if constexpr (!AGG) {
-    if (contrib) {
-      red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
-      red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
-    }
-  } else {
-    // Aggregate only when the contributing lanes share pixels: count the
-    // runs of equal pixels among neighbouring lanes (cheap), and fall back
-    // to plain adds when the warp's pixels are mostly distinct (shuffled
-    // orders), where matching would cost more than it saves.
-    const uint32_t tag = contrib ? pix : kNoPixel;
-    const uint32_t active = __ballot_sync(kFullMask, contrib);
-    const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
-    const uint32_t starts = __ballot_sync(kFullMask, contrib && (lane_id() == 0 || prev != tag));
-    if (__popc(starts) > kAggregateMaxRuns) {
-      if (contrib) {
-        red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
-        red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
-      }
-    } else if (contrib) {
-      const uint32_t peers = __match_any_sync(active, pix);
-      const uint32_t s_rg = __reduce_add_sync(peers, cr | (cg << 16));
-      const uint32_t s_bc = __reduce_add_sync(peers, cb | (1u << 16));
-      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
-        red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol);
-        red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol);
-      }
-    }
-  }
-}
-
+// Colour pass (Listing "hqs_render"): see emit_color.
 template <bool AGG, int U>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        float factor, const uint32_t* __restrict__ depth,

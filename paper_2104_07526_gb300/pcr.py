@@ -35,9 +35,26 @@ PCR_RESOLVE_HQ1R = 2
 PCR_CLEAR_KEYS = 1
 PCR_CLEAR_HQ = 2
 
+PCR_BATCH_BASIC = 1
+PCR_BATCH_HQ = 2
+PCR_BATCH_MAX_CLOUDS = 256
+PCR_BATCH_MAX_VIEWS = 256
+
 PCR_ORDER_MORTON = 0
 PCR_ORDER_MORTON_SHUFFLE128 = 1
 PCR_ORDER_SHUFFLE = 2
+
+
+class PcrBatchCloud(C.Structure):
+    """pcr_batch_cloud"""
+    _fields_ = [("points", C.c_void_p), ("n", C.c_uint64)]
+
+
+class PcrBatchView(C.Structure):
+    """pcr_batch_view"""
+    _fields_ = [("matrix", C.c_float * 16), ("width", C.c_int32), ("height", C.c_int32), ("cloud", C.c_uint32),
+                ("flags", C.c_uint32), ("keys", C.c_void_p), ("image", C.c_void_p), ("hq_depth", C.c_void_p),
+                ("hq_rg", C.c_void_p), ("hq_ba", C.c_void_p), ("hq_image", C.c_void_p)]
 
 
 class PcrError(RuntimeError):
@@ -71,6 +88,14 @@ _SIGS = {
     "pcr_reorder_morton_shuffle128": [_VP, _VP, _U64, _U64, _INT, _VP, _U64, _VP],
     "pcr_reorder_morton_shuffle128_noalloc": [_VP, _VP, _U64, _U64, _INT, _VP],
     "pcr_last_device_error": [_VP, C.POINTER(_U32)],
+    "pcr_batch_workspace_size": [C.POINTER(_U64)],
+    "pcr_batch_num_configs": [C.POINTER(_INT)],
+    "pcr_batch_prepare": [_VP, C.POINTER(PcrBatchCloud), _U32, C.POINTER(PcrBatchView), _U32, _FLT, _U32, _VP, _U64],
+    "pcr_batch_launch": [_VP, _VP, _INT],
+    "pcr_batch_autotune": [_VP, _VP, C.POINTER(_INT)],
+    "pcr_batch_capture": [_VP, _VP, _INT, C.POINTER(_VP)],
+    "pcr_graph_launch": [_VP, _VP],
+    "pcr_graph_destroy": [_VP],
 }
 
 
@@ -235,6 +260,65 @@ def pcr_reorder_morton_shuffle128_noalloc(ctx: int, points, n: int, seed: int, m
     _check(lib().pcr_reorder_morton_shuffle128_noalloc(ctx, _dptr(points, "points"), n, seed & ((1 << 64) - 1), mode,
                                                        _dptr(perm_out, "perm_out")),
            "pcr_reorder_morton_shuffle128_noalloc")
+
+
+def batch_cloud(points, n: int | None = None) -> PcrBatchCloud:
+    """pcr_batch_cloud for a CUDA tensor of 16-byte records (None: empty)."""
+    if points is None:
+        return PcrBatchCloud(None, 0)
+    return PcrBatchCloud(_dptr(points, "points"), n if n is not None else _nbytes(points) // 16)
+
+
+def batch_view(matrix, width: int, height: int, cloud: int, flags: int, keys=None, image=None, hq_depth=None,
+               hq_rg=None, hq_ba=None, hq_image=None) -> PcrBatchView:
+    vals = [float(v) for v in (matrix.reshape(-1).tolist() if hasattr(matrix, "reshape") else matrix)]
+    return PcrBatchView((C.c_float * 16)(*vals), width, height, cloud, flags, _dptr(keys, "keys"),
+                        _dptr(image, "image"), _dptr(hq_depth, "hq_depth"), _dptr(hq_rg, "hq_rg"),
+                        _dptr(hq_ba, "hq_ba"), _dptr(hq_image, "hq_image"))
+
+
+def pcr_batch_workspace_size() -> int:
+    out = _U64()
+    _check(lib().pcr_batch_workspace_size(C.byref(out)), "pcr_batch_workspace_size")
+    return out.value
+
+
+def pcr_batch_num_configs() -> int:
+    out = _INT()
+    _check(lib().pcr_batch_num_configs(C.byref(out)), "pcr_batch_num_configs")
+    return out.value
+
+
+def pcr_batch_prepare(ctx: int, clouds, views, depth_factor: float, background_rgba: int, workspace):
+    ca = (PcrBatchCloud * len(clouds))(*clouds)
+    va = (PcrBatchView * len(views))(*views)
+    _check(lib().pcr_batch_prepare(ctx, ca, len(clouds), va, len(views), depth_factor, background_rgba & 0xFFFFFFFF,
+                                   _dptr(workspace, "workspace"), _nbytes(workspace) if workspace is not None else 0),
+           "pcr_batch_prepare")
+
+
+def pcr_batch_launch(ctx: int, workspace, config: int = 0):
+    _check(lib().pcr_batch_launch(ctx, _dptr(workspace, "workspace"), config), "pcr_batch_launch")
+
+
+def pcr_batch_autotune(ctx: int, workspace) -> int:
+    out = _INT()
+    _check(lib().pcr_batch_autotune(ctx, _dptr(workspace, "workspace"), C.byref(out)), "pcr_batch_autotune")
+    return out.value
+
+
+def pcr_batch_capture(ctx: int, workspace, config: int) -> int:
+    out = _VP()
+    _check(lib().pcr_batch_capture(ctx, _dptr(workspace, "workspace"), config, C.byref(out)), "pcr_batch_capture")
+    return out.value
+
+
+def pcr_graph_launch(ctx: int, graph_exec: int):
+    _check(lib().pcr_graph_launch(ctx, graph_exec), "pcr_graph_launch")
+
+
+def pcr_graph_destroy(graph_exec: int):
+    _check(lib().pcr_graph_destroy(graph_exec), "pcr_graph_destroy")
 
 
 def pcr_last_device_error(ctx: int) -> int:

@@ -1,0 +1,160 @@
+"""Batched rendering (many clouds x views in one launch sequence or one CUDA
+graph) against the CPU oracle, bit for bit, for every launch configuration."""
+import numpy as np
+import pytest
+import torch
+
+import constructed as cs
+from gpu_helpers import ensure_built
+from paper_2104_07526_gb300 import pcr, scenes
+
+pytestmark = pytest.mark.gpu
+
+BASIC, HQ = pcr.PCR_BATCH_BASIC, pcr.PCR_BATCH_HQ
+BG = 0x20304050
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    ensure_built()
+    c = pcr.Context(0, stream=torch.cuda.current_stream())
+    yield c.handle
+    c.close()
+
+
+def _buffers(W, H):
+    npx = W * H
+    return {"keys": torch.empty(npx, dtype=torch.int64, device="cuda"),
+            "image": torch.empty(npx, dtype=torch.int32, device="cuda"),
+            "hq_depth": torch.empty(npx, dtype=torch.int32, device="cuda"),
+            "hq_rg": torch.empty(npx, dtype=torch.int64, device="cuda"),
+            "hq_ba": torch.empty(npx, dtype=torch.int64, device="cuda"),
+            "hq_image": torch.empty(npx, dtype=torch.int32, device="cuda")}
+
+
+def _make_batch():
+    """Three clouds (one ragged, one scanline-ordered, one constructed) and
+    eight views of mixed size, flags and cameras."""
+    rng = np.random.default_rng(31)
+    c0 = scenes.random_cloud(1003, seed=1).numpy()
+    c1 = scenes.sphere_plane(50_003, seed=2).numpy()
+    c2, _, _ = cs.hq_scene(rng, npix=2000)
+    clouds = [c0, c1, c2]
+    views = [  # (cloud, matrix, W, H, flags)
+        (1, scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), 160, 120), 160, 120, BASIC | HQ),
+        (0, scenes.camera((0.2, -2.6, 1.4), (0, 0, 0), (0, 0, 1), 64, 48), 64, 48, BASIC),
+        (2, cs.camera(), cs.W, cs.H, BASIC | HQ),
+        (1, scenes.camera((1.5, 2.5, 2.0), (0, 0, 0), (0, 0, 1), 333, 77), 333, 77, HQ),
+        (0, scenes.camera((0.2, -2.6, 1.4), (0, 0, 0), (0, 0, 1), 40, 30), 40, 30, HQ),
+        (1, scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), 1, 1), 1, 1, BASIC | HQ),
+        (2, cs.camera(), 320, 240, BASIC),
+        (1, scenes.camera((-3.0, 0.5, 0.5), (0, 0, 0), (0, 0, 1), 96, 96), 96, 96, BASIC | HQ),
+    ]
+    return clouds, views
+
+
+def _expected(oracle, clouds, views):
+    out = []
+    for c, m, W, H, flags in views:
+        e = {}
+        if flags & BASIC:
+            k = oracle.render_basic(clouds[c], m, W, H)
+            e["keys"] = k
+            e["image"] = oracle.resolve_basic(k, clouds[c], BG)
+        if flags & HQ:
+            d, rg, ba = oracle.render_hq(clouds[c], m, W, H, 1.01)
+            e.update(hq_depth=d, hq_rg=rg, hq_ba=ba, hq_image=oracle.resolve_hq(rg, ba, BG))
+        out.append(e)
+    return out
+
+
+_VIEWS = {"keys": np.uint64, "image": np.uint32, "hq_depth": np.uint32, "hq_rg": np.uint64, "hq_ba": np.uint64,
+          "hq_image": np.uint32}
+
+
+def _check(bufs, expected, tag):
+    torch.cuda.synchronize()
+    for i, (b, e) in enumerate(zip(bufs, expected)):
+        for name, want in e.items():
+            got = b[name].cpu().numpy().view(_VIEWS[name])
+            assert np.array_equal(got, want), (tag, i, name)
+
+
+def _prepare(ctx, clouds, views):
+    dev = [torch.from_numpy(c.copy()).cuda() if c.shape[0] else None for c in clouds]
+    bufs = [_buffers(W, H) for (_, _, W, H, _) in views]
+    vs = []
+    for (c, m, W, H, flags), b in zip(views, bufs):
+        kw = {}
+        if flags & BASIC:
+            kw.update(keys=b["keys"], image=b["image"])
+        if flags & HQ:
+            kw.update(hq_depth=b["hq_depth"], hq_rg=b["hq_rg"], hq_ba=b["hq_ba"], hq_image=b["hq_image"])
+        vs.append(pcr.batch_view(m, W, H, c, flags, **kw))
+    ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device="cuda")
+    pcr.pcr_batch_prepare(ctx, [pcr.batch_cloud(d) for d in dev], vs, 1.01, BG, ws)
+    return dev, bufs, ws
+
+
+def _poison(bufs):
+    for b in bufs:
+        for t in b.values():
+            t.fill_(0x5A5A5A5A)
+
+
+def test_batch_every_config_and_graph(ctx, oracle):
+    clouds, views = _make_batch()
+    expected = _expected(oracle, clouds, views)
+    dev, bufs, ws = _prepare(ctx, clouds, views)
+    for config in range(pcr.pcr_batch_num_configs()):
+        _poison(bufs)
+        pcr.pcr_batch_launch(ctx, ws, config)
+        _check(bufs, expected, f"config {config}")
+    best = pcr.pcr_batch_autotune(ctx, ws)
+    assert 0 <= best < pcr.pcr_batch_num_configs()
+    _check(bufs, expected, "autotune")
+    g = pcr.pcr_batch_capture(ctx, ws, best)
+    try:
+        for rep in range(2):
+            _poison(bufs)
+            pcr.pcr_graph_launch(ctx, g)
+            _check(bufs, expected, f"graph {rep}")
+    finally:
+        pcr.pcr_graph_destroy(g)
+
+
+def test_batch_empty_cloud_and_single_view(ctx, oracle):
+    clouds = [np.zeros((0, 4), np.int32), scenes.random_cloud(129, seed=5).numpy()]
+    views = [(0, np.eye(4, dtype=np.float32), 8, 8, BASIC | HQ),
+             (1, scenes.camera((0.2, -2.6, 1.4), (0, 0, 0), (0, 0, 1), 16, 16), 16, 16, BASIC | HQ)]
+    expected = _expected(oracle, clouds, views)
+    dev, bufs, ws = _prepare(ctx, clouds, views)
+    _poison(bufs)
+    pcr.pcr_batch_launch(ctx, ws, 0)
+    _check(bufs, expected, "empty")
+
+
+def test_batch_rejects_bad_descriptions(ctx):
+    cloud = torch.zeros((10, 4), dtype=torch.int32, device="cuda")
+    b = _buffers(4, 4)
+    ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device="cuda")
+    good = dict(keys=b["keys"], image=b["image"])
+    m = np.eye(4, dtype=np.float32)
+    cases = [
+        ([pcr.batch_cloud(cloud)], [pcr.batch_view(m, 4, 4, 1, BASIC, **good)], pcr.PCR_ERR_ARG),  # bad cloud index
+        ([pcr.batch_cloud(cloud)], [pcr.batch_view(m, 0, 4, 0, BASIC, **good)], pcr.PCR_ERR_ARG),  # bad size
+        ([pcr.batch_cloud(cloud)], [pcr.batch_view(m, 4, 4, 0, 4, **good)], pcr.PCR_ERR_ARG),  # bad flags
+        ([pcr.batch_cloud(cloud)], [pcr.batch_view(m, 4, 4, 0, HQ, **good)], pcr.PCR_ERR_ARG),  # missing HQ buffers
+        ([pcr.batch_cloud(cloud)], [], pcr.PCR_ERR_ARG),  # no views
+    ]
+    for clouds, views, status in cases:
+        with pytest.raises(pcr.PcrError) as e:
+            pcr.pcr_batch_prepare(ctx, clouds, views, 1.01, 0, ws)
+        assert e.value.status == status
+    with pytest.raises(pcr.PcrError) as e:
+        pcr.pcr_batch_prepare(ctx, [pcr.batch_cloud(cloud)], [pcr.batch_view(m, 4, 4, 0, BASIC, **good)], 1.01, 0,
+                              ws[:-256])
+    assert e.value.status == pcr.PCR_ERR_WORKSPACE
+    with pytest.raises(pcr.PcrError):
+        pcr.pcr_batch_launch(ctx, ws, pcr.pcr_batch_num_configs())
