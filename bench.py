@@ -74,6 +74,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--variant", default="dedup+early-z", help="render variant of the timed frame")
     ap.add_argument("--no-hq", action="store_true", help="skip the high-quality frame")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (8 clouds x 8 views) measurement")
     return ap.parse_args(argv)
 
 
@@ -470,6 +471,14 @@ def run_ours(args, cfg):
         pcr.pcr_upload_points(h, points, n)
         set_view(view)
 
+    # --- batched: 8 clouds x 8 views, per-view calls vs one graph -----------------
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(h, pcr, stream, dev, reps=max(3, min(K, 10)))
+        pcr.pcr_upload_points(h, points, n)
+        set_view(view)
+        pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+
     # --- CPU oracle baseline (rank 0, one GPU) -------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -487,7 +496,7 @@ def run_ours(args, cfg):
             "phases_ms": phase, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
-            "sweep_ms": sweep,
+            "sweep_ms": sweep, "batched": batched,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -538,6 +547,64 @@ def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, step
     return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
             "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
             "ms_per_step": dt / steps * 1e3}
+
+
+def run_batched(h, pcr, stream, dev, reps: int) -> dict:
+    """8 boxes clouds (1M..200M points) x 8 orbit views (256^2..2048^2), basic
+    and HQ frames: every view through the single-view calls (7 launches per
+    view) against the prepared batch replayed as one CUDA graph; outputs
+    compared bit for bit."""
+    import torch
+    from paper_2104_07526_gb300 import scenes
+    t0 = time.perf_counter()
+    clouds = [scenes.boxes(nc, seed=i, device=dev) for i, nc in enumerate(scenes.BATCH_CLOUD_SIZES)]
+    views = scenes.batch_views(len(clouds))
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+
+    def buffers(W, H):
+        npx = W * H
+        return {"keys": torch.empty(npx, dtype=torch.int64, device=dev),
+                "image": torch.empty(npx, dtype=torch.int32, device=dev),
+                "hq_depth": torch.empty(npx, dtype=torch.int32, device=dev),
+                "hq_rg": torch.empty(npx, dtype=torch.int64, device=dev),
+                "hq_ba": torch.empty(npx, dtype=torch.int64, device=dev),
+                "hq_image": torch.empty(npx, dtype=torch.int32, device=dev)}
+
+    per = [buffers(v.width, v.height) for _, v in views]
+    bat = [buffers(v.width, v.height) for _, v in views]
+    var = pcr.PCR_VARIANT_DEDUP_EARLYZ
+
+    def per_request():
+        for (c, v), b in zip(views, per):
+            pcr.pcr_upload_points(h, clouds[c], clouds[c].shape[0])
+            pcr.pcr_set_matrix(h, v.matrix)
+            pcr.pcr_set_viewport(h, v.width, v.height)
+            pcr.pcr_set_framebuffer(h, b["keys"], b["hq_depth"], b["hq_rg"], b["hq_ba"])
+            pcr.pcr_render_basic(h, var, True)
+            pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, b["image"], 0)
+            pcr.pcr_render_hq(h, 1.01, var, True)
+            pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, b["hq_image"], 0)
+
+    per_ms = time_loop(per_request, stream, reps=reps, warm=1)
+    ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device=dev)
+    flags = pcr.PCR_BATCH_BASIC | pcr.PCR_BATCH_HQ
+    pcr.pcr_batch_prepare(h, [pcr.batch_cloud(c) for c in clouds],
+                          [pcr.batch_view(v.matrix, v.width, v.height, c, flags, **b) for (c, v), b in zip(views, bat)],
+                          1.01, 0, ws)
+    config = pcr.pcr_batch_autotune(h, ws)
+    graph = pcr.pcr_batch_capture(h, ws, config)
+    try:
+        batched_ms = time_loop(lambda: pcr.pcr_graph_launch(h, graph), stream, reps=reps, warm=2)
+    finally:
+        pcr.pcr_graph_destroy(graph)
+    torch.cuda.synchronize()
+    identical = all(torch.equal(p_[k], b_[k]) for p_, b_ in zip(per, bat) for k in p_)
+    point_views = sum(clouds[c].shape[0] for c, _ in views)
+    return {"workload": "8 boxes clouds (1M..200M points, 388M total) x 8 orbit views (256^2..2048^2), basic + HQ",
+            "per_request_ms": per_ms, "per_request_launches": 7 * len(views), "batched_graph_ms": batched_ms,
+            "batched_launches": 4, "speedup": per_ms / batched_ms, "identical": identical, "config": config,
+            "point_views_per_s": point_views / (batched_ms * 1e-3), "generate_s": gen_s}
 
 
 def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:

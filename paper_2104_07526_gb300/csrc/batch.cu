@@ -2,16 +2,18 @@
 // sequence (clear, geometry phase 1, geometry phase 2, resolve), capturable
 // as one CUDA graph.
 //
-// Each cloud's points are read once per phase and projected for every view
-// of that cloud.  Phase 1 writes the basic key (Sec. 3.1-3.4, warp
+// Each pass over a cloud's points projects every point for a group of that
+// cloud's views.  Phase 1 writes the basic key (Sec. 3.1-3.4, warp
 // deduplication plus early depth test) and the high-quality depth (Sec. 3.5)
-// from one projection; phase 2, after the depth buffers are complete, adds
-// the high-quality colours.  A frame of V views of a cloud thus reads its
-// points twice instead of 3V times.  Clouds of uneven size are laid out as
-// one sequence of 128-point slots (each cloud padded to a multiple of 128),
-// which a persistent grid walks in uniform chunks, so no work queue and no
-// waiting is needed.  Results equal the per-view calls bit for bit: minima
-// and integer sums do not depend on order.
+// from one projection; phase 2, after all depth buffers are complete, adds
+// the high-quality colours.  A group holds as many views as fit an L2 budget
+// (framebuffer bytes the pass touches), packed first-fit by decreasing size,
+// so the atomics and early depth reads of a pass stay in L2 while the point
+// stream passes through.  The passes of a phase are laid out as one sequence
+// of 128-point slots (each pass padded to a multiple of 128) that a
+// persistent grid walks in uniform chunks: clouds of uneven size need no work
+// queue and nothing waits.  Results equal the per-view calls bit for bit:
+// minima and integer sums do not depend on order.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -32,25 +34,45 @@ using namespace geom;
 constexpr int kThreads = 256;
 constexpr uint64_t kSlot = 128;  // cloud padding and the largest chunk (32 lanes x 4)
 
+#ifndef PCR_BATCH_L2_BUDGET
+#define PCR_BATCH_L2_BUDGET (64ull << 20)
+#endif
+constexpr uint64_t kL2Budget = PCR_BATCH_L2_BUDGET;
+
 struct Tables {
   BatchHeader hdr;
   BatchCloud clouds[kBatchMaxClouds];
   BatchView views[kBatchMaxViews];
+  BatchGroup groups[2][kBatchMaxViews];
+  uint16_t order[2][kBatchMaxViews];
+};
+
+struct Shared {
+  BatchHeader hdr;
+  BatchCloud clouds[kBatchMaxClouds];
+  BatchView views[kBatchMaxViews];
+  BatchGroup groups[kBatchMaxViews];
+  uint16_t order[kBatchMaxViews];
 };
 
 constexpr uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
-__device__ __forceinline__ void load_tables(const Tables* __restrict__ g, BatchHeader& hdr, BatchCloud* clouds,
-                                            BatchView* views) {
-  if (threadIdx.x == 0) hdr = g->hdr;
+// Copy the header, clouds, views and (phase >= 0) that phase's groups into
+// shared memory.
+__device__ __forceinline__ void load_tables(const Tables* __restrict__ g, int phase, Shared& sh) {
+  if (threadIdx.x == 0) sh.hdr = g->hdr;
   __syncthreads();
-  const uint32_t nc = hdr.num_clouds, nv = hdr.num_views;
-  const uint32_t* src = reinterpret_cast<const uint32_t*>(g->clouds);
-  uint32_t* dst = reinterpret_cast<uint32_t*>(clouds);
-  for (uint32_t i = threadIdx.x; i < nc * (sizeof(BatchCloud) / 4); i += blockDim.x) dst[i] = src[i];
-  src = reinterpret_cast<const uint32_t*>(g->views);
-  dst = reinterpret_cast<uint32_t*>(views);
-  for (uint32_t i = threadIdx.x; i < nv * (sizeof(BatchView) / 4); i += blockDim.x) dst[i] = src[i];
+  auto copy = [](const void* src, void* dst, uint32_t bytes) {
+    const uint32_t* s4 = static_cast<const uint32_t*>(src);
+    uint32_t* d4 = static_cast<uint32_t*>(dst);
+    for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d4[i] = s4[i];
+  };
+  copy(g->clouds, sh.clouds, sh.hdr.num_clouds * sizeof(BatchCloud));
+  copy(g->views, sh.views, sh.hdr.num_views * sizeof(BatchView));
+  if (phase >= 0) {
+    copy(g->groups[phase], sh.groups, sh.hdr.num_groups[phase] * sizeof(BatchGroup));
+    copy(g->order[phase], sh.order, (sh.hdr.num_views * sizeof(uint16_t) + 3) / 4 * 4);
+  }
   __syncthreads();
 }
 
@@ -65,23 +87,23 @@ __device__ __forceinline__ uint32_t last_not_above(uint32_t count, uint64_t x, K
   return lo;
 }
 
-// Walk the chunks (32 * U points) of all clouds; f(cloud, r, base, ok) for
-// each chunk of this warp whose cloud passes `want` (others are not read).
-template <int U, class W, class F>
-__device__ __forceinline__ void for_each_batch_chunk(const BatchHeader& hdr, const BatchCloud* clouds, uint64_t pol,
-                                                     W&& want, F&& f) {
+// Walk the chunks (32 * U points) of every pass of a phase; f(group, r,
+// base, ok) for each chunk of this warp.
+template <int U, class F>
+__device__ __forceinline__ void for_each_batch_chunk(const Shared& sh, int phase, uint64_t pol, F&& f) {
   const uint64_t warps_per_block = blockDim.x >> 5;
   const uint64_t warp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const uint64_t nwarps = gridDim.x * warps_per_block;
   constexpr uint64_t kChunk = 32ull * U;
-  const uint64_t nchunks = hdr.total_slots / kChunk;
+  const uint64_t nchunks = sh.hdr.total_slots[phase] / kChunk;
   const uint32_t lane = lane_id();
   for (uint64_t g = warp; g < nchunks; g += nwarps) {
     const uint64_t slot0 = g * kChunk;
-    const uint32_t c = last_not_above(hdr.num_clouds, slot0, [&](uint32_t i) { return clouds[i].first_slot; });
-    const BatchCloud& cl = clouds[c];
-    if (!want(cl)) continue;
-    const uint32_t base = static_cast<uint32_t>(slot0 - cl.first_slot) + lane;
+    const uint32_t gi =
+        last_not_above(sh.hdr.num_groups[phase], slot0, [&](uint32_t i) { return sh.groups[i].first_slot; });
+    const BatchGroup& grp = sh.groups[gi];
+    const BatchCloud& cl = sh.clouds[grp.cloud];
+    const uint32_t base = static_cast<uint32_t>(slot0 - grp.first_slot) + lane;
     uint4 r[U];
     bool ok[U];
 #pragma unroll
@@ -90,7 +112,7 @@ __device__ __forceinline__ void for_each_batch_chunk(const BatchHeader& hdr, con
       ok[u] = i < cl.n;
       r[u] = ok[u] ? load_point_stream(cl.pts + i, pol) : make_uint4(0u, 0u, 0u, 0u);
     }
-    f(c, r, base, ok);
+    f(grp, r, base, ok);
   }
 }
 
@@ -106,64 +128,59 @@ __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&
   }
 }
 
-// Phase 1: per view of the chunk's cloud, basic key (dedup + early-z) and
-// HQ depth (dedup + early-z), both from one projection.
+// Phase 1: per view of the pass, basic key (dedup + early-z) and HQ depth
+// (dedup + early-z), both from one projection.
 template <int U>
 __global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restrict__ tables) {
-  __shared__ BatchHeader hdr;
-  __shared__ BatchCloud clouds[kBatchMaxClouds];
-  __shared__ BatchView views[kBatchMaxViews];
-  load_tables(tables, hdr, clouds, views);
+  __shared__ Shared sh;
+  load_tables(tables, 0, sh);
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  auto any_view = [](const BatchCloud& cl) { return cl.num_views > 0; };
-  for_each_batch_chunk<U>(hdr, clouds, pol_stream, any_view, [&](uint32_t c, const uint4(&r)[U], uint32_t base,
-                                                                 const bool(&ok)[U]) {
-    const BatchCloud& cl = clouds[c];
-    for (uint32_t vi = cl.first_view; vi < cl.first_view + cl.num_views; ++vi) {
-      const BatchView& bv = views[vi];
+  for_each_batch_chunk<U>(sh, 0, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t base,
+                                                 const bool(&ok)[U]) {
+    for (uint32_t i = grp.first; i < grp.first + grp.count; ++i) {
+      const BatchView& bv = sh.views[sh.order[i]];
       uint32_t pix[U];
       float w[U];
       bool vis[U];
       project_all<U>(bv.vp, r, ok, pix, w, vis);
-      if (bv.flags & PCR_BATCH_BASIC) {
-        unsigned long long seen[U];
+      // both early reads of every slot first: one L2 round trip per view
+      const bool basic = bv.flags & PCR_BATCH_BASIC;
+      const bool hq = bv.flags & PCR_BATCH_HQ;
+      unsigned long long seen_key[U];
+      uint32_t seen_depth[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) seen[u] = vis[u] ? load_relaxed_u64(bv.keys + pix[u]) : 0ull;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-          emit_key<PCR_VARIANT_DEDUP_EARLYZ>(bv.keys, vis[u], pix[u], w[u], base + 32u * u, seen[u], pol_fb);
+      for (int u = 0; u < U; ++u) {
+        seen_key[u] = (basic && vis[u]) ? load_relaxed_u64(bv.keys + pix[u]) : 0ull;
+        seen_depth[u] = (hq && vis[u]) ? load_relaxed_u32(bv.depth + pix[u]) : 0u;
       }
-      if (bv.flags & PCR_BATCH_HQ) {
-        uint32_t seen[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) seen[u] = vis[u] ? load_relaxed_u32(bv.depth + pix[u]) : 0u;
+      if (basic) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          emit_depth<PCR_VARIANT_DEDUP_EARLYZ>(bv.depth, vis[u], pix[u], __float_as_uint(w[u]), seen[u], pol_fb);
+          emit_key<PCR_VARIANT_DEDUP_EARLYZ>(bv.keys, vis[u], pix[u], w[u], base + 32u * u, seen_key[u], pol_fb);
+      }
+      if (hq) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          emit_depth<PCR_VARIANT_DEDUP_EARLYZ>(bv.depth, vis[u], pix[u], __float_as_uint(w[u]), seen_depth[u],
+                                               pol_fb);
       }
     }
   });
 }
 
-// Phase 2: HQ colours (warp-aggregated adds) for every HQ view.
+// Phase 2: HQ colours (warp-aggregated adds) for the HQ views of the pass.
 template <int U>
 __global__ void __launch_bounds__(kThreads) k_batch_phase2(const Tables* __restrict__ tables) {
-  __shared__ BatchHeader hdr;
-  __shared__ BatchCloud clouds[kBatchMaxClouds];
-  __shared__ BatchView views[kBatchMaxViews];
-  load_tables(tables, hdr, clouds, views);
-  if (hdr.hq_views == 0) return;
+  __shared__ Shared sh;
+  load_tables(tables, 1, sh);
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  const float factor = hdr.depth_factor;
-  auto any_hq = [](const BatchCloud& cl) { return cl.hq_views > 0; };
-  for_each_batch_chunk<U>(hdr, clouds, pol_stream, any_hq, [&](uint32_t c, const uint4(&r)[U], uint32_t,
-                                                               const bool(&ok)[U]) {
-    const BatchCloud& cl = clouds[c];
-    for (uint32_t vi = cl.first_view; vi < cl.first_view + cl.num_views; ++vi) {
-      const BatchView& bv = views[vi];
-      if (!(bv.flags & PCR_BATCH_HQ)) continue;
+  const float factor = sh.hdr.depth_factor;
+  for_each_batch_chunk<U>(sh, 1, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t,
+                                                 const bool(&ok)[U]) {
+    for (uint32_t i = grp.first; i < grp.first + grp.count; ++i) {
+      const BatchView& bv = sh.views[sh.order[i]];
       uint32_t pix[U];
       float w[U];
       bool vis[U];
@@ -180,15 +197,31 @@ __global__ void __launch_bounds__(kThreads) k_batch_phase2(const Tables* __restr
   });
 }
 
-// Clear and resolve walk the pixels of all views as one sequence.
+// Clear and resolve walk the pixels of all views as one sequence.  The view
+// of a pixel is found by one search per warp (lane 0's pixel); lanes whose
+// pixel lies past that view's end search on their own.
+__device__ __forceinline__ uint32_t view_of_pixel(const Shared& sh, uint64_t p) {
+  const uint64_t p0 = __shfl_sync(kFullMask, p, 0);
+  uint32_t vi = 0;
+  if (lane_id() == 0)
+    vi = last_not_above(sh.hdr.num_views, p0, [&](uint32_t i) { return sh.views[i].first_pixel; });
+  vi = __shfl_sync(kFullMask, vi, 0);
+  const uint64_t end = vi + 1 < sh.hdr.num_views ? sh.views[vi + 1].first_pixel : sh.hdr.total_pixels;
+  if (p >= end) vi = last_not_above(sh.hdr.num_views, p, [&](uint32_t i) { return sh.views[i].first_pixel; });
+  return vi;
+}
+
 __global__ void __launch_bounds__(kThreads) k_batch_clear(const Tables* __restrict__ tables) {
-  __shared__ BatchHeader hdr;
-  __shared__ BatchCloud clouds[kBatchMaxClouds];
-  __shared__ BatchView views[kBatchMaxViews];
-  load_tables(tables, hdr, clouds, views);
-  for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < hdr.total_pixels;
-       p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t vi = last_not_above(hdr.num_views, p, [&](uint32_t i) { return views[i].first_pixel; });
+  __shared__ Shared sh;
+  load_tables(tables, -1, sh);
+  const BatchHeader& hdr = sh.hdr;
+  const BatchView* views = sh.views;
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t rounds = (hdr.total_pixels + stride - 1) / stride;  // every lane runs the same rounds
+  for (uint64_t k = 0; k < rounds; ++k) {
+    const uint64_t p = k * stride + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+    const uint32_t vi = view_of_pixel(sh, p < hdr.total_pixels ? p : hdr.total_pixels - 1);
+    if (p >= hdr.total_pixels) continue;
     const BatchView& bv = views[vi];
     const uint64_t q = p - bv.first_pixel;
     if (bv.flags & PCR_BATCH_BASIC) bv.keys[q] = kEmptyKey;
@@ -201,14 +234,18 @@ __global__ void __launch_bounds__(kThreads) k_batch_clear(const Tables* __restri
 }
 
 __global__ void __launch_bounds__(kThreads) k_batch_resolve(const Tables* __restrict__ tables) {
-  __shared__ BatchHeader hdr;
-  __shared__ BatchCloud clouds[kBatchMaxClouds];
-  __shared__ BatchView views[kBatchMaxViews];
-  load_tables(tables, hdr, clouds, views);
+  __shared__ Shared sh;
+  load_tables(tables, -1, sh);
+  const BatchHeader& hdr = sh.hdr;
+  const BatchView* views = sh.views;
+  const BatchCloud* clouds = sh.clouds;
   const uint32_t background = hdr.background;
-  for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < hdr.total_pixels;
-       p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t vi = last_not_above(hdr.num_views, p, [&](uint32_t i) { return views[i].first_pixel; });
+  const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
+  const uint64_t rounds = (hdr.total_pixels + stride - 1) / stride;  // every lane runs the same rounds
+  for (uint64_t k = 0; k < rounds; ++k) {
+    const uint64_t p = k * stride + blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x;
+    const uint32_t vi = view_of_pixel(sh, p < hdr.total_pixels ? p : hdr.total_pixels - 1);
+    if (p >= hdr.total_pixels) continue;
     const BatchView& bv = views[vi];
     const uint64_t q = p - bv.first_pixel;
     if ((bv.flags & PCR_BATCH_BASIC) && bv.image) {
@@ -233,13 +270,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_resolve(const Tables* __rest
   }
 }
 
-// Launch configurations the autotuner chooses among: points per lane, and
-// resident blocks per SM (0 = as many as fit).
+// Launch configurations the autotuner chooses among: points per lane of
+// the two geometry phases (phase 2 keeps more state per point).
 struct BatchConfig {
-  int unroll;
-  int blocks_per_sm;
+  int unroll1;
+  int unroll2;
 };
-constexpr BatchConfig kConfigs[] = {{4, 0}, {2, 0}, {4, 2}, {2, 2}};
+constexpr BatchConfig kConfigs[] = {{4, 4}, {4, 2}, {2, 4}, {2, 2}};
 constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
 
 template <auto K>
@@ -252,15 +289,9 @@ int batch_resident() {
   return blocks;
 }
 
-template <int U>
-cudaError_t launch_phases(const Tables* t, int bps, cudaStream_t s, const Device& d) {
-  constexpr auto p1 = k_batch_phase1<U>;
-  constexpr auto p2 = k_batch_phase2<U>;
-  const int b1 = bps > 0 ? std::min(bps, batch_resident<p1>()) : batch_resident<p1>();
-  const int b2 = bps > 0 ? std::min(bps, batch_resident<p2>()) : batch_resident<p2>();
-  p1<<<d.num_sms * b1, kThreads, 0, s>>>(t);
-  p2<<<d.num_sms * b2, kThreads, 0, s>>>(t);
-  return cudaGetLastError();
+template <auto K>
+void launch_persistent(const Tables* t, cudaStream_t s, const Device& d) {
+  K<<<d.num_sms * batch_resident<K>(), kThreads, 0, s>>>(t);
 }
 
 }  // namespace
@@ -269,35 +300,73 @@ uint64_t batch_workspace_bytes() { return align256(sizeof(Tables)); }
 
 int batch_num_configs() { return kNumConfigs; }
 
+namespace {
+
+// Pack the views of each cloud that take part in a phase into passes whose
+// framebuffer bytes fit the L2 budget (first fit, largest first); a view
+// larger than the budget gets a pass of its own.
+void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
+                  uint32_t num_views, int phase) {
+  uint32_t ng = 0, nord = 0;
+  uint64_t slot = 0;
+  for (uint32_t c = 0; c < num_clouds; ++c) {
+    std::vector<std::pair<uint64_t, uint32_t>> mine;  // (bytes, view)
+    for (uint32_t i = 0; i < num_views; ++i) {
+      const pcr_batch_view& v = views[i];
+      if (v.cloud != c) continue;
+      const uint64_t px = static_cast<uint64_t>(v.width) * static_cast<uint64_t>(v.height);
+      uint64_t bytes = 0;
+      if (phase == 0) bytes = px * (((v.flags & PCR_BATCH_BASIC) ? 8u : 0u) + ((v.flags & PCR_BATCH_HQ) ? 4u : 0u));
+      else if (v.flags & PCR_BATCH_HQ) bytes = px * 20u;  // depth read, two 64-bit sums
+      if (bytes > 0) mine.emplace_back(bytes, i);
+    }
+    std::stable_sort(mine.begin(), mine.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<std::vector<uint32_t>> bins;
+    std::vector<uint64_t> used;
+    for (const auto& [bytes, vi] : mine) {
+      size_t b = 0;
+      while (b < bins.size() && used[b] + bytes > kL2Budget) ++b;
+      if (b == bins.size()) {
+        bins.emplace_back();
+        used.push_back(0);
+      }
+      bins[b].push_back(vi);
+      used[b] += bytes;
+    }
+    const uint64_t padded = (clouds[c].n + kSlot - 1) / kSlot * kSlot;
+    for (const auto& bin : bins) {
+      BatchGroup& g = t->groups[phase][ng++];
+      g.cloud = c;
+      g.first = nord;
+      g.count = static_cast<uint32_t>(bin.size());
+      g.first_slot = slot;
+      slot += padded;
+      for (uint32_t vi : bin) t->order[phase][nord++] = static_cast<uint16_t>(vi);
+    }
+  }
+  t->hdr.num_groups[phase] = ng;
+  t->hdr.total_slots[phase] = slot;
+}
+
+}  // namespace
+
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                           uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
                           cudaStream_t s) {
-  std::vector<uint32_t> order(num_views);
-  for (uint32_t i = 0; i < num_views; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](uint32_t a, uint32_t b) { return views[a].cloud < views[b].cloud; });
   Tables* t = new (std::nothrow) Tables();
   if (!t) return cudaErrorMemoryAllocation;
   t->hdr.num_clouds = num_clouds;
   t->hdr.num_views = num_views;
   t->hdr.depth_factor = depth_factor;
   t->hdr.background = background;
-  uint64_t slot = 0;
   for (uint32_t c = 0; c < num_clouds; ++c) {
-    BatchCloud& bc = t->clouds[c];
-    bc.pts = static_cast<const uint4*>(clouds[c].points);
-    bc.n = static_cast<uint32_t>(clouds[c].n);
-    bc.first_slot = slot;
-    slot += (clouds[c].n + kSlot - 1) / kSlot * kSlot;
-    bc.first_view = 0;
-    bc.num_views = 0;
-    bc.hq_views = 0;
+    t->clouds[c].pts = static_cast<const uint4*>(clouds[c].points);
+    t->clouds[c].n = static_cast<uint32_t>(clouds[c].n);
   }
-  t->hdr.total_slots = slot;
   uint64_t pixel = 0;
   uint32_t hq = 0;
   for (uint32_t j = 0; j < num_views; ++j) {
-    const pcr_batch_view& in = views[order[j]];
+    const pcr_batch_view& in = views[j];
     BatchView& bv = t->views[j];
     for (int k = 0; k < 4; ++k) {
       bv.vp.r0[k] = in.matrix[k];
@@ -319,13 +388,11 @@ cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, co
     bv.first_pixel = pixel;
     pixel += static_cast<uint64_t>(in.width) * static_cast<uint64_t>(in.height);
     if (in.flags & PCR_BATCH_HQ) ++hq;
-    BatchCloud& bc = t->clouds[in.cloud];
-    if (bc.num_views == 0) bc.first_view = j;
-    ++bc.num_views;
-    if (in.flags & PCR_BATCH_HQ) ++bc.hq_views;
   }
   t->hdr.total_pixels = pixel;
   t->hdr.hq_views = hq;
+  build_groups(t, clouds, num_clouds, views, num_views, 0);
+  build_groups(t, clouds, num_clouds, views, num_views, 1);
   cudaError_t e = cudaMemcpyAsync(workspace, t, sizeof(Tables), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   delete t;
@@ -344,11 +411,12 @@ cudaError_t batch_launch(const void* workspace, int config, cudaStream_t s, cons
   if (config < 0 || config >= kNumConfigs) return cudaErrorInvalidValue;
   const Tables* t = static_cast<const Tables*>(workspace);
   const int screen_blocks = d.num_sms * 8;
-  k_batch_clear<<<screen_blocks, kThreads, 0, s>>>(t);
   const BatchConfig cfg = kConfigs[config];
-  cudaError_t e = cfg.unroll == 4 ? launch_phases<4>(t, cfg.blocks_per_sm, s, d)
-                                  : launch_phases<2>(t, cfg.blocks_per_sm, s, d);
-  if (e != cudaSuccess) return e;
+  k_batch_clear<<<screen_blocks, kThreads, 0, s>>>(t);
+  if (cfg.unroll1 == 4) launch_persistent<k_batch_phase1<4>>(t, s, d);
+  else launch_persistent<k_batch_phase1<2>>(t, s, d);
+  if (cfg.unroll2 == 4) launch_persistent<k_batch_phase2<4>>(t, s, d);
+  else launch_persistent<k_batch_phase2<2>>(t, s, d);
   k_batch_resolve<<<screen_blocks, kThreads, 0, s>>>(t);
   return cudaGetLastError();
 }

@@ -46,21 +46,30 @@ constexpr uint32_t kBatchMaxViews = PCR_BATCH_MAX_VIEWS;
 struct BatchHeader {
   uint32_t num_clouds;
   uint32_t num_views;
-  uint64_t total_slots;   // sum of cloud sizes, each padded to 128 points
   uint64_t total_pixels;  // sum of view sizes
   uint32_t hq_views;
   uint32_t background;
   float depth_factor;
+  uint32_t num_groups[2];  // per geometry phase
   uint32_t pad;
+  uint64_t total_slots[2];  // per phase: sum over groups of the group's cloud size, padded to 128 points
+};
+
+// A group is a set of views of one cloud rendered in one pass over the
+// cloud's points; its framebuffers fit the L2 budget.  order[] lists the
+// group's view indices.
+struct BatchGroup {
+  uint32_t cloud;
+  uint32_t first;  // into the phase's order[]
+  uint32_t count;
+  uint32_t pad;
+  uint64_t first_slot;  // offset of this group's pass in the phase's padded sequence
 };
 
 struct BatchCloud {
   const uint4* pts;
   uint32_t n;
-  uint32_t first_view;  // this cloud's views are [first_view, first_view + num_views)
-  uint32_t num_views;
-  uint32_t hq_views;
-  uint64_t first_slot;  // offset of this cloud in the padded point sequence
+  uint32_t pad;
 };
 
 struct BatchView {

@@ -388,3 +388,25 @@ def scan_views(n: int = 800_000_000, seed: int = 0) -> list[View]:
 def as_numpy_points(cloud: torch.Tensor) -> np.ndarray:
     """Contiguous (n, 4) int32 host copy of a cloud (bytes unchanged)."""
     return np.ascontiguousarray(cloud.cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# Batched workload: 8 clouds of uneven size (the boxes recipe, seeds 0..7),
+# 8 views each at 256^2 .. 2048^2, cameras on an orbit around the scene.
+# ---------------------------------------------------------------------------
+
+BATCH_CLOUD_SIZES = (1_000_000, 2_000_000, 5_000_000, 10_000_000, 20_000_000, 50_000_000, 100_000_000,
+                     200_000_000)
+BATCH_VIEW_SIZES = (256, 512, 768, 1024, 1280, 1536, 1792, 2048)
+
+
+def batch_views(num_clouds: int = 8, sizes=BATCH_VIEW_SIZES) -> list[tuple[int, View]]:
+    """(cloud index, view) pairs: each cloud seen from len(sizes) orbit
+    cameras, one per square resolution, the orbit phase shifted per cloud."""
+    out = []
+    for c in range(num_clouds):
+        for k, size in enumerate(sizes):
+            a = 2.0 * math.pi * (k + 0.37 * c) / len(sizes)
+            eye = (80.0 * math.cos(a), 80.0 * math.sin(a), 40.0 + 5.0 * (k % 3))
+            out.append((c, View(f"cloud{c}/orbit{k}", camera(eye, (0, 0, 0), (0, 0, 1), size, size), size, size)))
+    return out
