@@ -318,6 +318,108 @@ PCR_API pcr_status pcr_graph_launch(pcr_ctx *ctx, void *graph_exec);
 /* Destroy an instantiated graph (NULL is accepted). */
 PCR_API pcr_status pcr_graph_destroy(void *graph_exec);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: resident clouds, frame slots and continuous batching of view       */
+/* requests on the batched renderer.  The paper renders one view per frame;   */
+/* this loop is the build's own addition for many concurrent viewers.         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct pcr_server pcr_server;
+
+typedef struct pcr_server_config {
+    void *dev_arena;           /* caller-owned device memory, 256-byte aligned: */
+    uint64_t arena_bytes;      /*   frame slots, batch workspaces, then resident clouds */
+    uint32_t max_width;        /* largest request, 1..16384 */
+    uint32_t max_height;
+    uint32_t num_slots;        /* frame slots: requests that can be rendering or awaiting release */
+    uint32_t max_batch_views;  /* requests per batch, 1..PCR_BATCH_MAX_VIEWS */
+    uint32_t max_inflight;     /* batches on the GPU at once (one stream each), 1..8 */
+    int32_t batch_config;      /* launch configuration of pcr_batch_launch */
+    float depth_factor;        /* HQ depth band, e.g. 1.01 */
+    uint32_t background_rgba;
+} pcr_server_config;
+
+typedef struct pcr_request {
+    uint32_t cloud_id;
+    float matrix[16];
+    int32_t width;
+    int32_t height;
+    uint32_t flags;            /* PCR_BATCH_BASIC and/or PCR_BATCH_HQ */
+} pcr_request;
+
+typedef struct pcr_server_result {
+    int32_t width, height;
+    uint32_t flags;
+    uint32_t pad;
+    void *keys, *image;                         /* device, in the request's frame slot */
+    void *hq_depth, *hq_rg, *hq_ba, *hq_image;  /* (NULL when the flag is not set) */
+    double submit_us, launch_us, done_us;       /* host steady clock, microseconds */
+    uint64_t points;                            /* size of the rendered cloud */
+} pcr_server_result;
+
+typedef struct pcr_server_stats {
+    uint64_t submitted, completed, batches, views_launched;
+    uint64_t uploads, evictions, bytes_uploaded, points_rendered;
+    uint64_t peak_queue, queued, resident_clouds, resident_bytes;
+} pcr_server_stats;
+
+enum { PCR_REQUEST_QUEUED = 0, PCR_REQUEST_RUNNING = 1, PCR_REQUEST_DONE = 2 };
+
+/* Create a server on the context's device.  Frame slots (36 bytes per pixel
+ * of max_width x max_height each) and one batch workspace per in-flight batch
+ * are carved from the front of the arena; the rest holds resident clouds.
+ * Creates one stream, one event and a pinned host staging area per in-flight
+ * batch.  Errors: PCR_ERR_ARG for bad fields, PCR_ERR_WORKSPACE if the
+ * arena cannot hold the slots and workspaces, PCR_ERR_CUDA. */
+PCR_API pcr_status pcr_server_create(pcr_ctx *ctx, const pcr_server_config *cfg, pcr_server **out);
+
+/* Wait for the server's streams, then free its host resources (NULL is
+ * accepted).  The arena stays the caller's. */
+PCR_API pcr_status pcr_server_destroy(pcr_server *srv);
+
+/* Register cloud `cloud_id` with its points in host memory (pinned memory
+ * makes uploads asynchronous; it must stay valid while the server lives).
+ * The cloud is uploaded into the arena when a request first needs it and may
+ * be evicted (least recently used, never while a batch in flight reads it)
+ * to make room for another.  Errors: PCR_ERR_ARG for a duplicate id, NULL
+ * points with n > 0, n >= 2^32. */
+PCR_API pcr_status pcr_server_add_cloud(pcr_server *srv, uint32_t cloud_id, const void *host_points, uint64_t n);
+
+/* Register a cloud already in device memory (caller-owned, 16-byte aligned,
+ * valid while the server lives); it is never uploaded or evicted. */
+PCR_API pcr_status pcr_server_add_device_cloud(pcr_server *srv, uint32_t cloud_id, const void *dev_points,
+                                               uint64_t n);
+
+/* Queue a view request; *ticket identifies it.  Time stamps use the host
+ * steady clock.  Errors: PCR_ERR_ARG for an unknown cloud, a size above the
+ * maxima or bad flags; PCR_ERR_WORKSPACE if the cloud can never fit. */
+PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, uint64_t *ticket);
+
+/* One turn of the serving loop, never blocking on the GPU: retire batches
+ * that have finished (their requests become PCR_REQUEST_DONE), then launch new
+ * batches on free streams from the queued requests, in arrival order, as far
+ * as frame slots and cloud memory allow (a request whose cloud cannot be
+ * placed now waits while later ones go ahead).  *completed (may be NULL)
+ * counts the requests this call retired.  A batch renders each request
+ * exactly as pcr_batch_launch would, so a result does not depend on which
+ * other requests shared its batch. */
+PCR_API pcr_status pcr_server_step(pcr_server *srv, uint32_t *completed);
+
+/* PCR_REQUEST_QUEUED, _RUNNING or _DONE for a ticket not yet released. */
+PCR_API pcr_status pcr_server_state(pcr_server *srv, uint64_t ticket, int *state);
+
+/* Result of a finished request: device pointers into its frame slot (valid
+ * until pcr_server_release) and its time stamps. */
+PCR_API pcr_status pcr_server_get_result(pcr_server *srv, uint64_t ticket, pcr_server_result *out);
+
+/* Give a finished request's frame slot back.  Reads of the slot issued on
+ * other streams must have completed first: the slot may be rewritten by the
+ * next batch. */
+PCR_API pcr_status pcr_server_release(pcr_server *srv, uint64_t ticket);
+
+/* Counters since creation, plus the current queue length and residency. */
+PCR_API pcr_status pcr_server_stats_get(pcr_server *srv, pcr_server_stats *out);
+
 /* Largest cloud pcr_reorder_morton_shuffle128_noalloc accepts. */
 #define PCR_REORDER_NOALLOC_MAX_POINTS 262144u
 

@@ -73,6 +73,10 @@ bool view_ready(const pcr_ctx* c) { return c->has_matrix && c->width > 0 && c->h
 
 }  // namespace
 
+namespace pcr {
+Device ctx_device(pcr_ctx* ctx) { return ctx->dev; }
+}  // namespace pcr
+
 extern "C" {
 
 pcr_status pcr_create(pcr_ctx** out, int device) {

@@ -350,11 +350,11 @@ void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds,
 
 }  // namespace
 
-cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
-                          uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
-                          cudaStream_t s) {
-  Tables* t = new (std::nothrow) Tables();
-  if (!t) return cudaErrorMemoryAllocation;
+uint64_t batch_tables_bytes() { return sizeof(Tables); }
+
+void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
+                        uint32_t num_views, float depth_factor, uint32_t background, void* host_tables) {
+  Tables* t = new (host_tables) Tables();
   t->hdr.num_clouds = num_clouds;
   t->hdr.num_views = num_views;
   t->hdr.depth_factor = depth_factor;
@@ -393,9 +393,18 @@ cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, co
   t->hdr.hq_views = hq;
   build_groups(t, clouds, num_clouds, views, num_views, 0);
   build_groups(t, clouds, num_clouds, views, num_views, 1);
-  cudaError_t e = cudaMemcpyAsync(workspace, t, sizeof(Tables), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
+                          uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
+                          cudaStream_t s) {
+  void* host = ::operator new(sizeof(Tables), std::nothrow);
+  if (!host) return cudaErrorMemoryAllocation;
+  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host);
+  cudaError_t e = cudaMemcpyAsync(workspace, host, sizeof(Tables), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  delete t;
+  static_cast<Tables*>(host)->~Tables();
+  ::operator delete(host);
   return e;
 }
 

@@ -86,6 +86,11 @@ struct BatchView {
 };
 
 uint64_t batch_workspace_bytes();
+// Size of the job tables, and building them into caller-provided host
+// memory (e.g. pinned staging for an asynchronous copy into a workspace).
+uint64_t batch_tables_bytes();
+void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
+                        uint32_t num_views, float depth_factor, uint32_t background, void* host_tables);
 int batch_num_configs();
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                           uint32_t num_views, float depth_factor, uint32_t background, void* workspace,

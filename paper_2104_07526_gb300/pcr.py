@@ -57,6 +57,38 @@ class PcrBatchView(C.Structure):
                 ("hq_rg", C.c_void_p), ("hq_ba", C.c_void_p), ("hq_image", C.c_void_p)]
 
 
+class PcrServerConfig(C.Structure):
+    """pcr_server_config"""
+    _fields_ = [("dev_arena", C.c_void_p), ("arena_bytes", C.c_uint64), ("max_width", C.c_uint32),
+                ("max_height", C.c_uint32), ("num_slots", C.c_uint32), ("max_batch_views", C.c_uint32),
+                ("max_inflight", C.c_uint32), ("batch_config", C.c_int32), ("depth_factor", C.c_float),
+                ("background_rgba", C.c_uint32)]
+
+
+class PcrRequest(C.Structure):
+    """pcr_request"""
+    _fields_ = [("cloud_id", C.c_uint32), ("matrix", C.c_float * 16), ("width", C.c_int32), ("height", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+class PcrServerResult(C.Structure):
+    """pcr_server_result"""
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("flags", C.c_uint32), ("pad", C.c_uint32),
+                ("keys", C.c_void_p), ("image", C.c_void_p), ("hq_depth", C.c_void_p), ("hq_rg", C.c_void_p),
+                ("hq_ba", C.c_void_p), ("hq_image", C.c_void_p), ("submit_us", C.c_double),
+                ("launch_us", C.c_double), ("done_us", C.c_double), ("points", C.c_uint64)]
+
+
+class PcrServerStats(C.Structure):
+    """pcr_server_stats"""
+    _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "batches", "views_launched", "uploads",
+                                          "evictions", "bytes_uploaded", "points_rendered", "peak_queue", "queued",
+                                          "resident_clouds", "resident_bytes")]
+
+
+PCR_REQUEST_QUEUED, PCR_REQUEST_RUNNING, PCR_REQUEST_DONE = 0, 1, 2
+
+
 class PcrError(RuntimeError):
     def __init__(self, status: int, call: str):
         self.status = status
@@ -96,6 +128,16 @@ _SIGS = {
     "pcr_batch_capture": [_VP, _VP, _INT, C.POINTER(_VP)],
     "pcr_graph_launch": [_VP, _VP],
     "pcr_graph_destroy": [_VP],
+    "pcr_server_create": [_VP, C.POINTER(PcrServerConfig), C.POINTER(_VP)],
+    "pcr_server_destroy": [_VP],
+    "pcr_server_add_cloud": [_VP, _U32, _VP, _U64],
+    "pcr_server_add_device_cloud": [_VP, _U32, _VP, _U64],
+    "pcr_server_submit": [_VP, C.POINTER(PcrRequest), C.POINTER(_U64)],
+    "pcr_server_step": [_VP, C.POINTER(_U32)],
+    "pcr_server_state": [_VP, _U64, C.POINTER(_INT)],
+    "pcr_server_get_result": [_VP, _U64, C.POINTER(PcrServerResult)],
+    "pcr_server_release": [_VP, _U64],
+    "pcr_server_stats_get": [_VP, C.POINTER(PcrServerStats)],
 }
 
 
@@ -319,6 +361,72 @@ def pcr_graph_launch(ctx: int, graph_exec: int):
 
 def pcr_graph_destroy(graph_exec: int):
     _check(lib().pcr_graph_destroy(graph_exec), "pcr_graph_destroy")
+
+
+def pcr_server_create(ctx: int, arena, max_width: int, max_height: int, num_slots: int, max_batch_views: int = 64,
+                      max_inflight: int = 2, batch_config: int = 0, depth_factor: float = 1.01,
+                      background_rgba: int = 0) -> int:
+    """arena: CUDA uint8 tensor (the server's device memory)."""
+    cfg = PcrServerConfig(_dptr(arena, "arena"), _nbytes(arena), max_width, max_height, num_slots, max_batch_views,
+                          max_inflight, batch_config, depth_factor, background_rgba & 0xFFFFFFFF)
+    out = _VP()
+    _check(lib().pcr_server_create(ctx, C.byref(cfg), C.byref(out)), "pcr_server_create")
+    return out.value
+
+
+def pcr_server_destroy(srv: int):
+    _check(lib().pcr_server_destroy(srv), "pcr_server_destroy")
+
+
+def pcr_server_add_cloud(srv: int, cloud_id: int, host_points, n: int | None = None):
+    """host_points must stay alive as long as the server."""
+    if n is None:
+        n = _nbytes(host_points) // 16
+    _check(lib().pcr_server_add_cloud(srv, cloud_id, _hptr(host_points, "host_points") if n else None, n),
+           "pcr_server_add_cloud")
+
+
+def pcr_server_add_device_cloud(srv: int, cloud_id: int, dev_points, n: int | None = None):
+    if n is None:
+        n = _nbytes(dev_points) // 16
+    _check(lib().pcr_server_add_device_cloud(srv, cloud_id, _dptr(dev_points, "dev_points") if n else None, n),
+           "pcr_server_add_device_cloud")
+
+
+def pcr_server_submit(srv: int, cloud_id: int, matrix, width: int, height: int, flags: int) -> int:
+    vals = [float(v) for v in (matrix.reshape(-1).tolist() if hasattr(matrix, "reshape") else matrix)]
+    req = PcrRequest(cloud_id, (C.c_float * 16)(*vals), width, height, flags)
+    t = _U64()
+    _check(lib().pcr_server_submit(srv, C.byref(req), C.byref(t)), "pcr_server_submit")
+    return t.value
+
+
+def pcr_server_step(srv: int) -> int:
+    done = _U32()
+    _check(lib().pcr_server_step(srv, C.byref(done)), "pcr_server_step")
+    return done.value
+
+
+def pcr_server_state(srv: int, ticket: int) -> int:
+    st = _INT()
+    _check(lib().pcr_server_state(srv, ticket, C.byref(st)), "pcr_server_state")
+    return st.value
+
+
+def pcr_server_get_result(srv: int, ticket: int) -> PcrServerResult:
+    out = PcrServerResult()
+    _check(lib().pcr_server_get_result(srv, ticket, C.byref(out)), "pcr_server_get_result")
+    return out
+
+
+def pcr_server_release(srv: int, ticket: int):
+    _check(lib().pcr_server_release(srv, ticket), "pcr_server_release")
+
+
+def pcr_server_stats_get(srv: int) -> dict:
+    out = PcrServerStats()
+    _check(lib().pcr_server_stats_get(srv, C.byref(out)), "pcr_server_stats_get")
+    return {k: getattr(out, k) for k, _ in PcrServerStats._fields_}
 
 
 def pcr_last_device_error(ctx: int) -> int:

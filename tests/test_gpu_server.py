@@ -1,0 +1,188 @@
+"""Serving loop: continuous batching of view requests over resident clouds.
+
+Every result must equal the request rendered alone (the CPU oracle), bit for
+bit, whatever batch it shared; eviction under a small arena must not change
+results."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import constructed as cs
+from gpu_helpers import ensure_built
+from paper_2104_07526_gb300 import pcr, scenes
+
+pytestmark = pytest.mark.gpu
+
+BASIC, HQ = pcr.PCR_BATCH_BASIC, pcr.PCR_BATCH_HQ
+BG = 0x01010101
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    ensure_built()
+    c = pcr.Context(0, stream=torch.cuda.current_stream())
+    yield c.handle
+    c.close()
+
+
+def _download(h, ptr, count, dtype):
+    out = np.empty(count, dtype=dtype)
+    pcr.pcr_download(h, out, ptr, out.nbytes)
+    return out
+
+
+def _check_result(h, srv, ticket, cloud, m, W, H, flags, oracle):
+    res = pcr.pcr_server_get_result(srv, ticket)
+    assert (res.width, res.height, res.flags) == (W, H, flags)
+    npx = W * H
+    if flags & BASIC:
+        k = oracle.render_basic(cloud, m, W, H)
+        assert np.array_equal(_download(h, res.keys, npx, np.uint64), k)
+        assert np.array_equal(_download(h, res.image, npx, np.uint32), oracle.resolve_basic(k, cloud, BG))
+    if flags & HQ:
+        d, rg, ba = oracle.render_hq(cloud, m, W, H, 1.01)
+        assert np.array_equal(_download(h, res.hq_depth, npx, np.uint32), d)
+        assert np.array_equal(_download(h, res.hq_rg, npx, np.uint64), rg)
+        assert np.array_equal(_download(h, res.hq_ba, npx, np.uint64), ba)
+        assert np.array_equal(_download(h, res.hq_image, npx, np.uint32), oracle.resolve_hq(rg, ba, BG))
+    assert res.done_us >= res.launch_us >= res.submit_us > 0
+
+
+def _drain(srv, tickets, on_done=None, timeout_s=60.0):
+    """Step until every ticket is done; on_done(ticket) runs (and may
+    release the slot) as each one finishes, as a client would."""
+    pending = list(tickets)
+    t0 = time.time()
+    while pending:
+        pcr.pcr_server_step(srv)
+        still = []
+        for t in pending:
+            if pcr.pcr_server_state(srv, t) == pcr.PCR_REQUEST_DONE:
+                if on_done:
+                    on_done(t)
+            else:
+                still.append(t)
+        pending = still
+        assert time.time() - t0 < timeout_s, "server did not finish"
+
+
+def _clouds():
+    rng = np.random.default_rng(41)
+    hq_cloud, _, _ = cs.hq_scene(rng, npix=1500)
+    return [scenes.sphere_plane(60_003, seed=1).numpy(), scenes.random_cloud(7001, seed=2).numpy(), hq_cloud,
+            scenes.scan(120_005, seed=3).numpy()]
+
+
+def _requests(rng, clouds, count, max_w, max_h):
+    out = []
+    for _ in range(count):
+        c = int(rng.integers(0, len(clouds)))
+        W = int(rng.integers(1, max_w + 1))
+        H = int(rng.integers(1, max_h + 1))
+        flags = int(rng.choice([BASIC, HQ, BASIC | HQ]))
+        if c == 2:
+            m = cs.camera()
+        elif c == 3:
+            m = scenes.camera((0, -300, 200), (0, 0, 0), (0, 0, 1), W, H)
+        else:
+            a = rng.uniform(0, 2 * np.pi)
+            m = scenes.camera((3 * np.cos(a), 3 * np.sin(a), 1.5), (0, 0, 0), (0, 0, 1), W, H)
+        out.append((c, m, W, H, flags))
+    return out
+
+
+def test_mixed_requests_match_rendering_alone(ctx, oracle):
+    clouds = _clouds()
+    dev = [torch.from_numpy(c.copy()).cuda() for c in clouds]
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, 200, 150, num_slots=12, max_batch_views=7, max_inflight=3,
+                                background_rgba=BG)
+    try:
+        host = [np.ascontiguousarray(c) for c in clouds]
+        pcr.pcr_server_add_device_cloud(srv, 10, dev[0])
+        pcr.pcr_server_add_cloud(srv, 11, host[1])
+        pcr.pcr_server_add_device_cloud(srv, 12, dev[2])
+        pcr.pcr_server_add_cloud(srv, 13, host[3])
+        rng = np.random.default_rng(42)
+        reqs = _requests(rng, clouds, 30, 200, 150)
+        by_ticket = {}
+
+        def finish(t):
+            c, m, W, H, flags = by_ticket.pop(t)
+            _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+            pcr.pcr_server_release(srv, t)
+
+        # submit in waves while earlier requests are still on the GPU
+        tickets = []
+        for i, req in enumerate(reqs):
+            c, m, W, H, flags = req
+            t = pcr.pcr_server_submit(srv, 10 + c, m, W, H, flags)
+            by_ticket[t] = req
+            tickets.append(t)
+            if i % 4 == 3:
+                pcr.pcr_server_step(srv)
+        _drain(srv, tickets, finish)
+        assert not by_ticket
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["completed"] == len(reqs) and st["batches"] >= 3 and st["queued"] == 0
+        # the same request alone, in a fresh batch of one, gives the same result
+        c, m, W, H, flags = reqs[0]
+        t = pcr.pcr_server_submit(srv, 10 + c, m, W, H, flags)
+        _drain(srv, [t])
+        _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+        pcr.pcr_server_release(srv, t)
+    finally:
+        pcr.pcr_server_destroy(srv)
+
+
+def test_lru_eviction_keeps_results_exact(ctx, oracle):
+    """An arena that holds two of the four clouds: requests cycle through
+    them, so clouds are evicted and uploaded again."""
+    clouds = [scenes.random_cloud(50_000 + 17 * i, seed=10 + i).numpy() for i in range(4)]
+    W, H = 64, 48
+    slots = 4
+    slot_bytes = 3 * ((8 * W * H + 255) // 256 * 256) + 3 * ((4 * W * H + 255) // 256 * 256)
+    ws = (pcr.pcr_batch_workspace_size() + 255) // 256 * 256
+    cloud_room = 2 * ((clouds[-1].nbytes + 255) // 256 * 256) + 1024
+    arena = torch.empty(slots * slot_bytes + 2 * ws + cloud_room, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, W, H, num_slots=slots, max_batch_views=2, max_inflight=2,
+                                background_rgba=BG)
+    try:
+        host = [np.ascontiguousarray(c) for c in clouds]
+        for i, c in enumerate(host):
+            pcr.pcr_server_add_cloud(srv, i, c)
+        m = scenes.camera((0.2, -2.6, 1.4), (0, 0, 0), (0, 0, 1), W, H)
+        order = [0, 1, 2, 3, 0, 2, 1, 3, 3, 0]
+        for c in order:
+            t = pcr.pcr_server_submit(srv, c, m, W, H, BASIC | HQ)
+            _drain(srv, [t])
+            _check_result(ctx, srv, t, clouds[c], m, W, H, BASIC | HQ, oracle)
+            pcr.pcr_server_release(srv, t)
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["evictions"] >= 4 and st["uploads"] >= 6
+        assert st["resident_clouds"] <= 2
+    finally:
+        pcr.pcr_server_destroy(srv)
+
+
+def test_submit_rejections(ctx):
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, 32, 32, num_slots=2)
+    try:
+        cloud = torch.zeros((10, 4), dtype=torch.int32, device="cuda")
+        pcr.pcr_server_add_device_cloud(srv, 1, cloud)
+        m = np.eye(4, dtype=np.float32)
+        for args in [(2, m, 8, 8, BASIC), (1, m, 33, 8, BASIC), (1, m, 8, 8, 0), (1, m, 8, 8, 8)]:
+            with pytest.raises(pcr.PcrError) as e:
+                pcr.pcr_server_submit(srv, *args)
+            assert e.value.status == pcr.PCR_ERR_ARG
+        with pytest.raises(pcr.PcrError):
+            pcr.pcr_server_add_device_cloud(srv, 1, cloud)  # duplicate id
+    finally:
+        pcr.pcr_server_destroy(srv)
+    with pytest.raises(pcr.PcrError) as e:
+        pcr.pcr_server_create(ctx, torch.empty(1 << 20, dtype=torch.uint8, device="cuda"), 1024, 1024, 4)
+    assert e.value.status == pcr.PCR_ERR_WORKSPACE
