@@ -75,6 +75,8 @@ def parse_args(argv=None):
     ap.add_argument("--variant", default="dedup+early-z", help="render variant of the timed frame")
     ap.add_argument("--no-hq", action="store_true", help="skip the high-quality frame")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (8 clouds x 8 views) measurement")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson request stream) measurement")
+    ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the served request stream")
     return ap.parse_args(argv)
 
 
@@ -487,6 +489,14 @@ def run_ours(args, cfg):
         cpu = oracle_baseline(lambda k: points[cpu_sample_indices(n, k).to(dev)].cpu().numpy(), n, view,
                               args.cpu_seconds)
 
+    # --- served: Poisson request stream, continuous batching vs plain launches --
+    served = None
+    if not args.no_served:
+        orders.clear()
+        points = cloud = None
+        torch.cuda.empty_cache()
+        served = run_served(h, pcr, stream, dev, args.served_seconds)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -496,7 +506,7 @@ def run_ours(args, cfg):
             "phases_ms": phase, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
-            "sweep_ms": sweep, "batched": batched,
+            "sweep_ms": sweep, "batched": batched, "served": served,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -605,6 +615,112 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
             "per_request_ms": per_ms, "per_request_launches": 7 * len(views), "batched_graph_ms": batched_ms,
             "batched_launches": 4, "speedup": per_ms / batched_ms, "identical": identical, "config": config,
             "point_views_per_s": point_views / (batched_ms * 1e-3), "generate_s": gen_s}
+
+
+def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_batch_views: int = 32,
+               batch_config: int = 0, plain_baseline: bool = True, rate: float = 2000.0, streams: int = 1,
+               max_batch_clouds: int = 0) -> dict:
+    """16 boxes clouds (1M..300M points) registered with the server from host
+    memory, a 150 GB arena, and a Poisson stream of 2000 requests/s (random
+    cloud, resolution 512^2..3840x2160, basic or HQ, orbit camera).  Latency
+    runs from each request's scheduled arrival to its completion.  The same
+    stream is then served by plain per-request launches (one request at a
+    time, in order)."""
+    import torch
+    from paper_2104_07526_gb300 import scenes
+    sizes = scenes.SERVE_CLOUD_SIZES
+    dev_clouds = [scenes.boxes(nc, seed=100 + i, device=dev) for i, nc in enumerate(sizes)]
+    host_clouds = [c.cpu().numpy() for c in dev_clouds]
+    reqs = scenes.serve_requests(int(rate * seconds), rate, seed=7, num_clouds=len(sizes))
+    arena = torch.empty(150 << 30, dtype=torch.uint8, device=dev)
+    srv = pcr.pcr_server_create(h, arena, 3840, 2160, num_slots=64, max_batch_views=max_batch_views,
+                                max_inflight=max_inflight, streams=streams, max_batch_clouds=max_batch_clouds,
+                                batch_config=batch_config, depth_factor=1.01, background_rgba=0)
+    try:
+        for i, hc in enumerate(host_clouds):
+            pcr.pcr_server_add_cloud(srv, i, hc)
+        # warm-up: one request per cloud uploads every cloud
+        warm = [pcr.pcr_server_submit(srv, i, reqs[0][2], 512, 512, 1) for i in range(len(sizes))]
+        left = set(warm)
+        while left:
+            pcr.pcr_server_step(srv)
+            for t in pcr.pcr_server_poll_completed(srv):
+                left.discard(t)
+                pcr.pcr_server_release(srv, t)
+        stats0 = pcr.pcr_server_stats_get(srv)
+
+        def us():
+            return time.monotonic_ns() / 1e3  # same clock as the server's steady clock
+
+        t0 = us() + 1000.0
+        arrival = [t0 + r[0] * 1e6 for r in reqs]
+        lat, pts, last_done, i, done = [], 0, 0.0, 0, 0
+        owner = {}
+        while done < len(reqs):
+            now = us()
+            while i < len(reqs) and arrival[i] <= now:
+                _, c, m, W, H, flags = reqs[i]
+                owner[pcr.pcr_server_submit(srv, c, m, W, H, flags)] = i
+                i += 1
+            pcr.pcr_server_step(srv)
+            for t in pcr.pcr_server_poll_completed(srv):
+                res = pcr.pcr_server_get_result(srv, t)
+                lat.append((res.done_us - arrival[owner.pop(t)]) / 1e3)
+                pts += res.points
+                last_done = max(last_done, res.done_us)
+                pcr.pcr_server_release(srv, t)
+                done += 1
+        stats = pcr.pcr_server_stats_get(srv)
+    finally:
+        pcr.pcr_server_destroy(srv)
+    span_s = (last_done - arrival[0]) / 1e6
+    served = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+              "requests_per_s": len(reqs) / span_s, "points_per_s": pts / span_s,
+              "batches": stats["batches"] - stats0["batches"],
+              "mean_batch": (stats["views_launched"] - stats0["views_launched"]) / max(1, stats["batches"] -
+                                                                                      stats0["batches"]),
+              "uploads": stats["uploads"], "evictions": stats["evictions"], "peak_queue": stats["peak_queue"]}
+    del arena
+    torch.cuda.empty_cache()
+    if not plain_baseline:
+        return {"served": served}
+
+    # plain per-request launches on the same arrival schedule
+    W0, H0 = 3840, 2160
+    fb = pcr.alloc_framebuffer(W0, H0, dev)
+    pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+    var = pcr.PCR_VARIANT_DEDUP_EARLYZ
+
+    def render(c, m, W, H, flags):
+        pcr.pcr_upload_points(h, dev_clouds[c], dev_clouds[c].shape[0])
+        pcr.pcr_set_matrix(h, m)
+        pcr.pcr_set_viewport(h, W, H)
+        if flags & 1:
+            pcr.pcr_render_basic(h, var, True)
+            pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+        else:
+            pcr.pcr_render_hq(h, 1.01, var, True)
+            pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, fb["image"], 0)
+
+    render(*reqs[0][1:])
+    torch.cuda.synchronize()
+    t0 = us() + 1000.0
+    arrival = [t0 + r[0] * 1e6 for r in reqs]
+    lat_p, pts_p = [], 0
+    for k, (_, c, m, W, H, flags) in enumerate(reqs):
+        while us() < arrival[k]:
+            pass
+        render(c, m, W, H, flags)
+        pcr.pcr_synchronize(h)
+        lat_p.append((us() - arrival[k]) / 1e3)
+        pts_p += sizes[c]
+    span_p = (us() - arrival[0]) / 1e6
+    plain = {"p50_ms": float(np.percentile(lat_p, 50)), "p99_ms": float(np.percentile(lat_p, 99)),
+             "requests_per_s": len(reqs) / span_p, "points_per_s": pts_p / span_p}
+    return {"workload": f"{len(sizes)} boxes clouds ({sizes[0] / 1e6:.0f}M..{sizes[-1] / 1e6:.0f}M points), "
+                        f"Poisson 2000 requests/s for {seconds:g} s, 512^2..3840x2160, basic/HQ 50/50, "
+                        "150 GB arena", "requests": len(reqs), "served": served, "plain": plain,
+            "throughput_gain": served["requests_per_s"] / plain["requests_per_s"]}
 
 
 def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:

@@ -333,7 +333,11 @@ typedef struct pcr_server_config {
     uint32_t max_height;
     uint32_t num_slots;        /* frame slots: requests that can be rendering or awaiting release */
     uint32_t max_batch_views;  /* requests per batch, 1..PCR_BATCH_MAX_VIEWS */
-    uint32_t max_inflight;     /* batches on the GPU at once (one stream each), 1..8 */
+    uint32_t max_inflight;     /* batches launched and not yet retired, 1..8 */
+    uint32_t streams;          /* streams they rotate over, 1..max_inflight (0 = max_inflight):
+                                  1 queues batches back to back, more lets them run concurrently */
+    uint32_t max_batch_clouds; /* distinct clouds per batch, 0 = no limit: fewer clouds per batch
+                                  means more views share each pass over a cloud's points */
     int32_t batch_config;      /* launch configuration of pcr_batch_launch */
     float depth_factor;        /* HQ depth band, e.g. 1.01 */
     uint32_t background_rgba;
@@ -368,8 +372,8 @@ enum { PCR_REQUEST_QUEUED = 0, PCR_REQUEST_RUNNING = 1, PCR_REQUEST_DONE = 2 };
 /* Create a server on the context's device.  Frame slots (36 bytes per pixel
  * of max_width x max_height each) and one batch workspace per in-flight batch
  * are carved from the front of the arena; the rest holds resident clouds.
- * Creates one stream, one event and a pinned host staging area per in-flight
- * batch.  Errors: PCR_ERR_ARG for bad fields, PCR_ERR_WORKSPACE if the
+ * Creates `streams` streams, and one event and one pinned host staging area
+ * per in-flight batch.  Errors: PCR_ERR_ARG for bad fields, PCR_ERR_WORKSPACE if the
  * arena cannot hold the slots and workspaces, PCR_ERR_CUDA. */
 PCR_API pcr_status pcr_server_create(pcr_ctx *ctx, const pcr_server_config *cfg, pcr_server **out);
 
@@ -397,9 +401,10 @@ PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, ui
 
 /* One turn of the serving loop, never blocking on the GPU: retire batches
  * that have finished (their requests become PCR_REQUEST_DONE), then launch new
- * batches on free streams from the queued requests, in arrival order, as far
- * as frame slots and cloud memory allow (a request whose cloud cannot be
- * placed now waits while later ones go ahead).  *completed (may be NULL)
+ * batches from the queued requests, in arrival order, as far as in-flight
+ * batches, frame slots, cloud memory and max_batch_clouds allow (a request
+ * that cannot join now waits while later ones go ahead; the oldest request
+ * always joins the next batch that has room).  *completed (may be NULL)
  * counts the requests this call retired.  A batch renders each request
  * exactly as pcr_batch_launch would, so a result does not depend on which
  * other requests shared its batch. */
@@ -411,6 +416,10 @@ PCR_API pcr_status pcr_server_state(pcr_server *srv, uint64_t ticket, int *state
 /* Result of a finished request: device pointers into its frame slot (valid
  * until pcr_server_release) and its time stamps. */
 PCR_API pcr_status pcr_server_get_result(pcr_server *srv, uint64_t ticket, pcr_server_result *out);
+
+/* Report up to `capacity` tickets that finished since the previous call, in
+ * completion order; *count receives how many were written. */
+PCR_API pcr_status pcr_server_poll_completed(pcr_server *srv, uint64_t *tickets, uint32_t capacity, uint32_t *count);
 
 /* Give a finished request's frame slot back.  Reads of the slot issued on
  * other streams must have completed first: the slot may be rewritten by the

@@ -101,7 +101,7 @@ struct Request {
 };
 
 struct Inflight {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // borrowed from pcr_server::streams
   cudaEvent_t done = nullptr;
   void* staging = nullptr;  // pinned host copy of the job tables
   void* workspace = nullptr;
@@ -128,7 +128,9 @@ struct pcr_server {
   std::unordered_map<uint32_t, pcr::Cloud> clouds;
   std::unordered_map<uint64_t, pcr::Request> requests;
   std::deque<uint64_t> queue;
+  std::deque<uint64_t> finished;  // completed tickets not yet reported by pcr_server_poll_completed
   std::vector<pcr::Inflight> inflight;
+  std::vector<cudaStream_t> streams;
   uint64_t next_ticket = 1;
   uint64_t clock = 0;
   pcr_server_stats stats{};
@@ -194,6 +196,7 @@ pcr_status retire(pcr_server* s, uint32_t* completed) {
       pcr::Request& r = s->requests[tk];
       r.state = kDone;
       r.t_done = t;
+      s->finished.push_back(tk);
       ++s->stats.completed;
       s->stats.points_rendered += s->clouds[r.cloud].n;
       if (completed) ++*completed;
@@ -218,7 +221,8 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
     pcr::Request& r = s->requests[*it];
     pcr::Cloud& c = s->clouds[r.cloud];
     const bool in_batch = std::find(batch_clouds.begin(), batch_clouds.end(), r.cloud) != batch_clouds.end();
-    if (!in_batch && batch_clouds.size() >= PCR_BATCH_MAX_CLOUDS) {
+    const uint32_t cloud_cap = s->cfg.max_batch_clouds ? s->cfg.max_batch_clouds : PCR_BATCH_MAX_CLOUDS;
+    if (!in_batch && batch_clouds.size() >= std::min<uint32_t>(cloud_cap, PCR_BATCH_MAX_CLOUDS)) {
       ++it;
       continue;
     }
@@ -309,12 +313,12 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
 }
 
 void destroy(pcr_server* s) {
+  for (cudaStream_t st : s->streams) cudaStreamSynchronize(st);
   for (pcr::Inflight& f : s->inflight) {
-    if (f.stream) cudaStreamSynchronize(f.stream);
     if (f.done) cudaEventDestroy(f.done);
-    if (f.stream) cudaStreamDestroy(f.stream);
     if (f.staging) cudaFreeHost(f.staging);
   }
+  for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
   for (auto& kv : s->clouds)
     if (kv.second.ready) cudaEventDestroy(kv.second.ready);
   delete s;
@@ -331,7 +335,8 @@ pcr_status pcr_server_create(pcr_ctx* ctx, const pcr_server_config* cfg, pcr_ser
   if (cfg->max_width < 1 || cfg->max_height < 1 || cfg->max_width > 16384 || cfg->max_height > 16384)
     return PCR_ERR_ARG;
   if (cfg->num_slots < 1 || cfg->max_batch_views < 1 || cfg->max_batch_views > PCR_BATCH_MAX_VIEWS ||
-      cfg->max_inflight < 1 || cfg->max_inflight > pcr::kMaxInflight)
+      cfg->max_inflight < 1 || cfg->max_inflight > pcr::kMaxInflight || cfg->streams > cfg->max_inflight ||
+      cfg->max_batch_clouds > PCR_BATCH_MAX_CLOUDS)
     return PCR_ERR_ARG;
   if (!(cfg->depth_factor > 0.0f) || !(cfg->depth_factor < 3.0e38f)) return PCR_ERR_ARG;
   if (cfg->batch_config < 0 || cfg->batch_config >= pcr::batch_num_configs()) return PCR_ERR_ARG;
@@ -361,11 +366,17 @@ pcr_status pcr_server_create(pcr_ctx* ctx, const pcr_server_config* cfg, pcr_ser
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != s->dev.id) cudaSetDevice(s->dev.id);
+    const uint32_t nstreams = cfg->streams ? cfg->streams : cfg->max_inflight;
+    for (uint32_t i = 0; i < nstreams && st == PCR_OK; ++i) {
+      cudaStream_t sm = nullptr;
+      if (cudaStreamCreateWithFlags(&sm, cudaStreamNonBlocking) != cudaSuccess) st = PCR_ERR_CUDA;
+      else s->streams.push_back(sm);
+    }
     for (uint32_t i = 0; i < cfg->max_inflight && st == PCR_OK; ++i) {
       pcr::Inflight& f = s->inflight[i];
       f.workspace = s->arena + ws_base + i * ws_bytes;
-      if (cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) != cudaSuccess ||
+      f.stream = s->streams[i % nstreams];
+      if (cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) != cudaSuccess ||
           cudaHostAlloc(&f.staging, pcr::batch_tables_bytes(), cudaHostAllocDefault) != cudaSuccess)
         st = PCR_ERR_CUDA;
     }
@@ -478,6 +489,17 @@ pcr_status pcr_server_get_result(pcr_server* s, uint64_t ticket, pcr_server_resu
   out->launch_us = r.t_launch;
   out->done_us = r.t_done;
   out->points = s->clouds[r.cloud].n;
+  return PCR_OK;
+}
+
+pcr_status pcr_server_poll_completed(pcr_server* s, uint64_t* tickets, uint32_t capacity, uint32_t* count) {
+  if (!s || !count || (capacity > 0 && !tickets)) return PCR_ERR_ARG;
+  uint32_t k = 0;
+  while (k < capacity && !s->finished.empty()) {
+    tickets[k++] = s->finished.front();
+    s->finished.pop_front();
+  }
+  *count = k;
   return PCR_OK;
 }
 

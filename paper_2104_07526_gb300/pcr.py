@@ -61,8 +61,8 @@ class PcrServerConfig(C.Structure):
     """pcr_server_config"""
     _fields_ = [("dev_arena", C.c_void_p), ("arena_bytes", C.c_uint64), ("max_width", C.c_uint32),
                 ("max_height", C.c_uint32), ("num_slots", C.c_uint32), ("max_batch_views", C.c_uint32),
-                ("max_inflight", C.c_uint32), ("batch_config", C.c_int32), ("depth_factor", C.c_float),
-                ("background_rgba", C.c_uint32)]
+                ("max_inflight", C.c_uint32), ("streams", C.c_uint32), ("max_batch_clouds", C.c_uint32),
+                ("batch_config", C.c_int32), ("depth_factor", C.c_float), ("background_rgba", C.c_uint32)]
 
 
 class PcrRequest(C.Structure):
@@ -137,6 +137,7 @@ _SIGS = {
     "pcr_server_state": [_VP, _U64, C.POINTER(_INT)],
     "pcr_server_get_result": [_VP, _U64, C.POINTER(PcrServerResult)],
     "pcr_server_release": [_VP, _U64],
+    "pcr_server_poll_completed": [_VP, C.POINTER(_U64), _U32, C.POINTER(_U32)],
     "pcr_server_stats_get": [_VP, C.POINTER(PcrServerStats)],
 }
 
@@ -364,11 +365,12 @@ def pcr_graph_destroy(graph_exec: int):
 
 
 def pcr_server_create(ctx: int, arena, max_width: int, max_height: int, num_slots: int, max_batch_views: int = 64,
-                      max_inflight: int = 2, batch_config: int = 0, depth_factor: float = 1.01,
-                      background_rgba: int = 0) -> int:
+                      max_inflight: int = 2, streams: int = 0, max_batch_clouds: int = 0, batch_config: int = 0,
+                      depth_factor: float = 1.01, background_rgba: int = 0) -> int:
     """arena: CUDA uint8 tensor (the server's device memory)."""
     cfg = PcrServerConfig(_dptr(arena, "arena"), _nbytes(arena), max_width, max_height, num_slots, max_batch_views,
-                          max_inflight, batch_config, depth_factor, background_rgba & 0xFFFFFFFF)
+                          max_inflight, streams, max_batch_clouds, batch_config, depth_factor,
+                          background_rgba & 0xFFFFFFFF)
     out = _VP()
     _check(lib().pcr_server_create(ctx, C.byref(cfg), C.byref(out)), "pcr_server_create")
     return out.value
@@ -417,6 +419,13 @@ def pcr_server_get_result(srv: int, ticket: int) -> PcrServerResult:
     out = PcrServerResult()
     _check(lib().pcr_server_get_result(srv, ticket, C.byref(out)), "pcr_server_get_result")
     return out
+
+
+def pcr_server_poll_completed(srv: int, capacity: int = 256) -> list[int]:
+    buf = (_U64 * capacity)()
+    count = _U32()
+    _check(lib().pcr_server_poll_completed(srv, buf, capacity, C.byref(count)), "pcr_server_poll_completed")
+    return list(buf[:count.value])
 
 
 def pcr_server_release(srv: int, ticket: int):

@@ -410,3 +410,29 @@ def batch_views(num_clouds: int = 8, sizes=BATCH_VIEW_SIZES) -> list[tuple[int, 
             eye = (80.0 * math.cos(a), 80.0 * math.sin(a), 40.0 + 5.0 * (k % 3))
             out.append((c, View(f"cloud{c}/orbit{k}", camera(eye, (0, 0, 0), (0, 0, 1), size, size), size, size)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Served workload: 16 clouds (boxes recipe, 1M..300M points, log-spaced) and a
+# Poisson stream of view requests over them.
+# ---------------------------------------------------------------------------
+
+SERVE_CLOUD_SIZES = tuple(int(round(1e6 * 300.0 ** (i / 15))) for i in range(16))
+SERVE_RESOLUTIONS = ((512, 512), (1280, 720), (1920, 1080), (2560, 1440), (3840, 2160))
+
+
+def serve_requests(count: int, rate_per_s: float = 2000.0, seed: int = 0, num_clouds: int = 16):
+    """(arrival seconds, cloud, matrix, width, height, flags) tuples: Poisson
+    arrivals at the given mean rate, a uniform cloud, a uniform resolution,
+    basic or HQ with equal odds (flags 1 or 2), a random orbit camera."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_per_s, size=count))
+    out = []
+    for i in range(count):
+        c = int(rng.integers(0, num_clouds))
+        W, H = SERVE_RESOLUTIONS[int(rng.integers(0, len(SERVE_RESOLUTIONS)))]
+        flags = 1 if rng.random() < 0.5 else 2
+        a = rng.uniform(0.0, 2.0 * math.pi)
+        eye = (80.0 * math.cos(a), 80.0 * math.sin(a), 35.0 + 15.0 * rng.random())
+        out.append((float(t[i]), c, camera(eye, (0, 0, 0), (0, 0, 1), W, H), W, H, flags))
+    return out

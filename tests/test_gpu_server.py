@@ -138,6 +138,39 @@ def test_mixed_requests_match_rendering_alone(ctx, oracle):
         pcr.pcr_server_destroy(srv)
 
 
+def test_shared_stream_cloud_cap_and_completion_queue(ctx, oracle):
+    """Three in-flight batches on one stream, at most one cloud per batch;
+    finished tickets come out of the completion queue exactly once."""
+    clouds = _clouds()
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, 160, 120, num_slots=10, max_batch_views=4, max_inflight=3, streams=1,
+                                max_batch_clouds=1, background_rgba=BG)
+    try:
+        for i, c in enumerate(clouds):
+            pcr.pcr_server_add_cloud(srv, 20 + i, np.ascontiguousarray(c))
+        reqs = _requests(np.random.default_rng(7), clouds, 24, 160, 120)
+        by_ticket, pending, seen = {}, list(reqs), []
+        t0 = time.time()
+        while pending or by_ticket:
+            while pending and len(by_ticket) < 10:  # one frame slot per outstanding request
+                req = pending.pop(0)
+                by_ticket[pcr.pcr_server_submit(srv, 20 + req[0], *req[1:])] = req
+            pcr.pcr_server_step(srv)
+            for t in pcr.pcr_server_poll_completed(srv, capacity=3):
+                assert t not in seen
+                seen.append(t)
+                c, m, W, H, flags = by_ticket.pop(t)
+                _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+                pcr.pcr_server_release(srv, t)
+            assert time.time() - t0 < 60.0, "server did not finish"
+        assert len(seen) == len(reqs)
+        assert pcr.pcr_server_poll_completed(srv) == []
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["completed"] == len(reqs) and st["batches"] >= len(clouds)
+    finally:
+        pcr.pcr_server_destroy(srv)
+
+
 def test_lru_eviction_keeps_results_exact(ctx, oracle):
     """An arena that holds two of the four clouds: requests cycle through
     them, so clouds are evicted and uploaded again."""
@@ -186,3 +219,7 @@ def test_submit_rejections(ctx):
     with pytest.raises(pcr.PcrError) as e:
         pcr.pcr_server_create(ctx, torch.empty(1 << 20, dtype=torch.uint8, device="cuda"), 1024, 1024, 4)
     assert e.value.status == pcr.PCR_ERR_WORKSPACE
+    for kw in [dict(max_inflight=2, streams=3), dict(max_batch_clouds=pcr.PCR_BATCH_MAX_CLOUDS + 1)]:
+        with pytest.raises(pcr.PcrError) as e:
+            pcr.pcr_server_create(ctx, arena, 32, 32, 2, **kw)
+        assert e.value.status == pcr.PCR_ERR_ARG
