@@ -439,7 +439,8 @@ def run_ours(args, cfg):
     peak, peak_src = measured_hbm_gbs()
     achieved = n * POINT_BYTES / (render_ms * 1e-3) / 1e9
     traffic = recorded_traffic([os.path.join(ROOT, "paper_2104_07526_gb300", "csrc", f)
-                                for f in ("render.cu", "common.cuh")]) if args.config == "scan800M" else None
+                                for f in ("render.cu", "common.cuh", "geometry.cuh")]) \
+        if args.config == "scan800M" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic["bytes_per_launch"] if traffic else None,
                 "kernel": f"k_render_basic<{args.variant}>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
@@ -619,7 +620,7 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
 
 def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_batch_views: int = 32,
                batch_config: int = 0, plain_baseline: bool = True, rate: float = 2000.0, streams: int = 1,
-               max_batch_clouds: int = 0) -> dict:
+               max_batch_clouds: int = 2) -> dict:
     """16 boxes clouds (1M..300M points) registered with the server from host
     memory, a 150 GB arena, and a Poisson stream of 2000 requests/s (random
     cloud, resolution 512^2..3840x2160, basic or HQ, orbit camera).  Latency

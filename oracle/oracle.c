@@ -19,6 +19,15 @@
  *                        outside the 1% band; hand-worked averages
  *                        (tests/golden/hq_cases.txt).
  *   oracle_resolve_*     hand-worked cases.
+ *   oracle_*_rgb         constructed scenes (colour of the nearest point);
+ *                        hand-worked depth ties broken by colour
+ *                        (tests/golden/rgb_key_cases.txt); agreement with
+ *                        the index-payload render wherever the nearest
+ *                        point is unique.
+ *   oracle_morton_codes63 hand-worked codes (tests/golden/morton63_cases.txt);
+ *                        equality of the order with a 21-level depth-first
+ *                        octree traversal; its top 30 bits equal the 10-level
+ *                        code (2^21 / e is 2^11 times 1024 / e exactly).
  *   oracle_morton_codes  hand-worked codes; equality of the Morton order with
  *                        a depth-first octree traversal (Sec. 5 states the
  *                        two are the same).
@@ -173,6 +182,36 @@ void oracle_resolve_basic(const uint64_t *keys, size_t npx, const oracle_point *
     }
 }
 
+/* Sec. 3.1, Listing "basic" as printed: point = (depth << 24) | rgb, where
+ * depth is the float bits of w (positive, so its bits order like the float)
+ * and rgb the colour's 8 bits per channel in the 24 low bits.  The depth
+ * field sits above the colour, so a minimum over keys is a minimum over
+ * depth first and colour second. */
+uint64_t oracle_key_rgb(float w, uint32_t rgba) {
+    return ((uint64_t)float_to_bits(w) << 24) | (uint64_t)(rgba & 0xFFFFFFu);
+}
+
+void oracle_render_rgb(const oracle_point *pts, uint64_t n, const float m[16], int width, int height,
+                       uint64_t *keys) {
+    for (uint64_t i = 0; i < n; ++i) {
+        uint32_t p;
+        float w;
+        if (!oracle_project(m, width, height, pts[i].x, pts[i].y, pts[i].z, &p, &w)) continue;
+        uint64_t k = oracle_key_rgb(w, pts[i].rgba);
+        if (k < keys[p]) keys[p] = k;
+    }
+}
+
+/* Sec. 3.1, Listing "resolve": the colour is read from the key itself. */
+void oracle_resolve_rgb(const uint64_t *keys, size_t npx, uint32_t background, uint32_t *out) {
+    for (size_t p = 0; p < npx; ++p) {
+        if (keys[p] == UINT64_MAX)
+            out[p] = background;
+        else
+            out[p] = (uint32_t)(keys[p] & 0xFFFFFFu) | (0xFFu << 24);
+    }
+}
+
 /* Sec. 3.5, Listing "hqs_resolve": divide the colour sums by the count with
  * truncating integer division.  A channel above 255 (possible only after a
  * 32-bit sum overflowed) is clamped to 255. */
@@ -253,6 +292,44 @@ void oracle_morton_codes(const oracle_point *pts, uint64_t n, uint32_t *codes) {
     }
 }
 
+/* Quantise one coordinate to 21 bits: floor((v - lo) * scale), clamped to
+ * [0, 2^21 - 1]; NaN maps to 0. */
+static uint32_t quantise21(float v, float lo, float scale) {
+    float f = floorf((v - lo) * scale);
+    if (!(f >= 0.0f)) return 0;
+    if (f >= 2097151.0f) return 2097151u;
+    return (uint32_t)f;
+}
+
+/* Sec. 5: the paper's 21-level octree, as a 63-bit code.  Same root cube and
+ * degenerate case as oracle_morton_codes, with 2^21 cells per axis. */
+void oracle_morton_codes63(const oracle_point *pts, uint64_t n, uint64_t *codes) {
+    float lo[3], hi[3];
+    oracle_aabb(pts, n, lo, hi);
+    float ext = hi[0] - lo[0];
+    float ey = hi[1] - lo[1];
+    float ez = hi[2] - lo[2];
+    if (ey > ext) ext = ey;
+    if (ez > ext) ext = ez;
+    int degenerate = !(ext > 0.0f) || !(ext < INFINITY);
+    float scale = degenerate ? 0.0f : 2097152.0f / ext;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (degenerate) {
+            codes[i] = 0;
+            continue;
+        }
+        uint32_t q[3] = {quantise21(pts[i].x, lo[0], scale), quantise21(pts[i].y, lo[1], scale),
+                         quantise21(pts[i].z, lo[2], scale)};
+        uint64_t c = 0;
+        for (int bit = 0; bit < 21; ++bit) {
+            c |= (uint64_t)((q[0] >> bit) & 1u) << (3 * bit + 2);
+            c |= (uint64_t)((q[1] >> bit) & 1u) << (3 * bit + 1);
+            c |= (uint64_t)((q[2] >> bit) & 1u) << (3 * bit);
+        }
+        codes[i] = c;
+    }
+}
+
 /* SplitMix64 as published: state advances by the golden-ratio increment and
  * each output is the mixed state.  Output k uses state seed + (k + 1) * gamma. */
 uint64_t oracle_splitmix64(uint64_t seed, uint64_t k) {
@@ -279,14 +356,56 @@ static int keyed_cmp(const void *a, const void *b) {
     return 0;
 }
 
+typedef struct {
+    uint64_t key;
+    uint32_t index;
+} keyed64;
+
+static int keyed64_cmp(const void *a, const void *b) {
+    const keyed64 *x = (const keyed64 *)a, *y = (const keyed64 *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    if (x->index != y->index) return x->index < y->index ? -1 : 1;
+    return 0;
+}
+
+/* perm = the points in stable order of their Morton code (the 30-bit code,
+ * or the 63-bit one when wide).  Returns 0, or -1 when allocation fails. */
+static int morton_order(const oracle_point *pts, uint64_t n, int wide, uint32_t *perm) {
+    keyed64 *k = (keyed64 *)malloc(n * sizeof(keyed64));
+    uint64_t *codes = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint32_t *narrow = wide ? NULL : (uint32_t *)malloc(n * sizeof(uint32_t));
+    if (!k || !codes || (!wide && !narrow)) {
+        free(k);
+        free(codes);
+        free(narrow);
+        return -1;
+    }
+    if (wide) {
+        oracle_morton_codes63(pts, n, codes);
+    } else {
+        oracle_morton_codes(pts, n, narrow);
+        for (uint64_t i = 0; i < n; ++i) codes[i] = narrow[i];
+    }
+    for (uint64_t i = 0; i < n; ++i) {
+        k[i].key = codes[i];
+        k[i].index = (uint32_t)i;
+    }
+    qsort(k, n, sizeof(keyed64), keyed64_cmp);
+    for (uint64_t i = 0; i < n; ++i) perm[i] = k[i].index;
+    free(narrow);
+    free(codes);
+    free(k);
+    return 0;
+}
+
 int oracle_reorder(const oracle_point *pts, uint64_t n, uint64_t seed, int mode, uint32_t batch,
                    uint32_t *perm) {
-    if (n > 0xFFFFFFFFull || mode < 0 || mode > 2 || (mode == 1 && batch == 0)) return -1;
+    if (n > 0xFFFFFFFFull || mode < 0 || mode > 4 || ((mode == 1 || mode == 4) && batch == 0)) return -1;
     if (n == 0) return 0;
-    keyed *k = (keyed *)malloc(n * sizeof(keyed));
-    if (!k) return -1;
     if (mode == 2) {
         /* Sec. 5, "Shuffled": a random value per point, then sort by it. */
+        keyed *k = (keyed *)malloc(n * sizeof(keyed));
+        if (!k) return -1;
         for (uint64_t i = 0; i < n; ++i) {
             k[i].key = (uint32_t)(oracle_splitmix64(seed, i) >> 32);
             k[i].index = (uint32_t)i;
@@ -296,22 +415,13 @@ int oracle_reorder(const oracle_point *pts, uint64_t n, uint64_t seed, int mode,
         free(k);
         return 0;
     }
-    uint32_t *codes = (uint32_t *)malloc(n * sizeof(uint32_t));
-    if (!codes) {
-        free(k);
+    const int wide = mode >= 3;
+    if (mode == 0 || mode == 3) return morton_order(pts, n, wide, perm);
+    uint32_t *morton = (uint32_t *)malloc(n * sizeof(uint32_t));
+    if (!morton) return -1;
+    if (morton_order(pts, n, wide, morton) != 0) {
+        free(morton);
         return -1;
-    }
-    oracle_morton_codes(pts, n, codes);
-    for (uint64_t i = 0; i < n; ++i) {
-        k[i].key = codes[i];
-        k[i].index = (uint32_t)i;
-    }
-    free(codes);
-    qsort(k, n, sizeof(keyed), keyed_cmp);
-    if (mode == 0) {
-        for (uint64_t i = 0; i < n; ++i) perm[i] = k[i].index;
-        free(k);
-        return 0;
     }
     /* Sec. 4 and Sec. 5, "Shuffled Morton": cut the Morton order into batches
      * of `batch` points (the last one may be shorter), move whole batches to
@@ -319,7 +429,7 @@ int oracle_reorder(const oracle_point *pts, uint64_t n, uint64_t seed, int mode,
     uint64_t nb = (n + batch - 1) / batch;
     keyed *bk = (keyed *)malloc(nb * sizeof(keyed));
     if (!bk) {
-        free(k);
+        free(morton);
         return -1;
     }
     for (uint64_t b = 0; b < nb; ++b) {
@@ -332,10 +442,10 @@ int oracle_reorder(const oracle_point *pts, uint64_t n, uint64_t seed, int mode,
         uint64_t b = bk[t].index;
         uint64_t first = b * batch;
         uint64_t last = first + batch < n ? first + batch : n;
-        for (uint64_t j = first; j < last; ++j) perm[out++] = k[j].index;
+        for (uint64_t j = first; j < last; ++j) perm[out++] = morton[j];
     }
     free(bk);
-    free(k);
+    free(morton);
     return 0;
 }
 

@@ -69,6 +69,20 @@ void oracle_hq_channel_sums(const oracle_point *pts, uint64_t n, const float m[1
 void oracle_resolve_basic(const uint64_t *keys, size_t npx, const oracle_point *pts, uint64_t n,
                           uint32_t background, uint32_t *out);
 
+/* Sec. 3.1, the key as Listing "basic" prints it: depth bits shifted left
+ * by 24 over a 24-bit colour payload (the rgba word's low three bytes).  The
+ * smallest depth wins and, at equal depth, the smallest 24-bit colour. */
+uint64_t oracle_key_rgb(float w, uint32_t rgba);
+
+/* Sec. 3.1 with the colour payload: keys[p] = min(keys[p], oracle_key_rgb of
+ * every visible point landing on p).  Accumulates like oracle_render_basic. */
+void oracle_render_rgb(const oracle_point *pts, uint64_t n, const float m[16], int width, int height,
+                       uint64_t *keys);
+
+/* Sec. 3.1, resolve of colour-payload keys: background where the key is all
+ * ones, else the key's 24-bit colour with alpha 255. */
+void oracle_resolve_rgb(const uint64_t *keys, size_t npx, uint32_t background, uint32_t *out);
+
 /* Sec. 3.5, resolve: truncating integer average per channel, alpha 255;
  * background where no point contributed. */
 void oracle_resolve_hq(const uint64_t *rg, const uint64_t *ba, size_t npx, uint32_t background,
@@ -80,6 +94,11 @@ void oracle_aabb(const oracle_point *pts, uint64_t n, float lo[3], float hi[3]);
 /* 30-bit Morton code per point: 10 bits per axis over the cube spanned by the
  * largest extent of the bounds; x in bit 3i+2, y in bit 3i+1, z in bit 3i. */
 void oracle_morton_codes(const oracle_point *pts, uint64_t n, uint32_t *codes);
+
+/* 63-bit Morton code per point, the paper's 21 levels (Sec. 5 "Morton"): 21
+ * bits per axis over the same cube as oracle_morton_codes; x in bit 3i+2, y
+ * in bit 3i+1, z in bit 3i. */
+void oracle_morton_codes63(const oracle_point *pts, uint64_t n, uint64_t *codes);
 
 /* SplitMix64 (Steele, Lea, Flood 2014): the k-th output (k from 0) of the
  * generator seeded with `seed`. */
@@ -96,6 +115,8 @@ void oracle_counter_keys(uint64_t seed, uint64_t count, uint32_t *keys);
  *         each batch keeps its inner order.
  * mode 2: shuffled: points stably sorted by the high 32 bits of SplitMix64
  *         output i.
+ * mode 3: Morton order by the 63-bit code (stable sort).
+ * mode 4: shuffled Morton over the mode 3 order (batches as in mode 1).
  * Returns 0 on success, -1 on a bad argument or allocation failure. */
 int oracle_reorder(const oracle_point *pts, uint64_t n, uint64_t seed, int mode, uint32_t batch,
                    uint32_t *perm);

@@ -41,6 +41,11 @@ def lib():
                                                  VOIDP, VOIDP]
             L.oracle_resolve_basic.argtypes = [VOIDP, C.c_size_t, VOIDP, U64, U32, VOIDP]
             L.oracle_resolve_hq.argtypes = [VOIDP, VOIDP, C.c_size_t, U32, VOIDP]
+            L.oracle_key_rgb.argtypes = [FLT, U32]
+            L.oracle_key_rgb.restype = U64
+            L.oracle_render_rgb.argtypes = [VOIDP, U64, VOIDP, INT, INT, VOIDP]
+            L.oracle_resolve_rgb.argtypes = [VOIDP, C.c_size_t, U32, VOIDP]
+            L.oracle_morton_codes63.argtypes = [VOIDP, U64, VOIDP]
             L.oracle_aabb.argtypes = [VOIDP, U64, VOIDP, VOIDP]
             L.oracle_morton_codes.argtypes = [VOIDP, U64, VOIDP]
             L.oracle_splitmix64.argtypes = [U64, U64]
@@ -107,6 +112,27 @@ def render_basic(pts: np.ndarray, m, width: int, height: int, keys: np.ndarray |
     return keys
 
 
+def key_rgb(w: float, rgba: int) -> int:
+    return int(lib().oracle_key_rgb(FLT(w), rgba & 0xFFFFFFFF))
+
+
+def render_rgb(pts: np.ndarray, m, width: int, height: int, keys: np.ndarray | None = None) -> np.ndarray:
+    """Colour-payload keys (depth bits << 24 | rgb)."""
+    pts, n = _cloud(pts)
+    if keys is None:
+        keys = clear_keys(width * height)
+    assert keys.dtype == np.uint64 and keys.size == width * height
+    lib().oracle_render_rgb(_ptr(pts), n, _ptr(_mat(m)), width, height, _ptr(keys))
+    return keys
+
+
+def resolve_rgb(keys: np.ndarray, background: int = 0) -> np.ndarray:
+    keys = np.ascontiguousarray(keys, dtype=np.uint64)
+    out = np.empty(keys.size, dtype=np.uint32)
+    lib().oracle_resolve_rgb(_ptr(keys), keys.size, background, _ptr(out))
+    return out
+
+
 def clear_hq(npx: int):
     d = np.empty(npx, dtype=np.uint32)
     rg = np.empty(npx, dtype=np.uint64)
@@ -164,7 +190,14 @@ def morton_codes(pts: np.ndarray) -> np.ndarray:
     return codes
 
 
-MORTON, MORTON_SHUFFLE, SHUFFLE = 0, 1, 2
+def morton_codes63(pts: np.ndarray) -> np.ndarray:
+    pts, n = _cloud(pts)
+    codes = np.empty(n, dtype=np.uint64)
+    lib().oracle_morton_codes63(_ptr(pts), n, _ptr(codes))
+    return codes
+
+
+MORTON, MORTON_SHUFFLE, SHUFFLE, MORTON63, MORTON63_SHUFFLE = 0, 1, 2, 3, 4
 
 
 def reorder(pts: np.ndarray, seed: int, mode: int, batch: int = 128) -> np.ndarray:

@@ -219,6 +219,68 @@ def test_hq_depth_factor_one_counts_only_front(oracle):
     assert np.array_equal(ba & np.uint64(0xFFFFFFFF), counts)
 
 
+# --- Sec. 3.1 colour-payload key (Listing "basic" as printed) -------------------
+
+def test_rgb_key_hand_cases(oracle):
+    rows = read_golden("rgb_key_cases.txt")
+    assert len(rows) >= 4
+    for row in rows:
+        w, rgba, expect = row[0].split()
+        assert oracle.key_rgb(float(w), int(rgba, 16)) == int(expect, 16), row
+
+
+def test_rgb_hand_ties(oracle):
+    """An equal depth keeps the smaller 24-bit colour, whatever the index or
+    the alpha byte; the index payload would keep the first of the tie."""
+    m = _mat("1 0 0 0  0 1 0 0  0 0 1 0  0 0 1 0")  # w = z
+    xyz = np.array([[0, 0, 1.0], [0, 0, 0.5], [0, 0, 0.5], [0, 0, 2.0], [0, 0, 0.5]])
+    rgba = np.array([0xFF000010, 0xFF0000FF, 0x00000001, 0xFF000000, 0x7F000001], dtype=np.uint32)
+    cloud = cs.pack(xyz, rgba)
+    keys = oracle.render_rgb(cloud, m, 4, 4)
+    assert keys[10] == (0x3F000000 << 24) | 0x000001
+    assert np.all(np.delete(keys, 10) == np.uint64(0xFFFFFFFFFFFFFFFF))
+    out = oracle.resolve_rgb(keys, background=0x11223344)
+    assert out[10] == 0xFF000001 and np.all(np.delete(out, 10) == 0x11223344)
+    assert oracle.resolve_basic(oracle.render_basic(cloud, m, 4, 4), cloud)[10] == 0xFF0000FF
+
+
+def test_rgb_constructed_depth_scene(oracle):
+    """Points on pixel-centre rays at exact depths: per pixel the smallest
+    depth, at a tie the smallest colour."""
+    rng = np.random.default_rng(5)
+    cloud, _, recs, colour = cs.depth_scene(rng)
+    expected = np.full(cs.W * cs.H, np.uint64(0xFFFFFFFFFFFFFFFF), dtype=np.uint64)
+    for i, (p, _, _, d) in enumerate(recs):
+        rgb = int(colour[i, 0]) | (int(colour[i, 1]) << 8) | (int(colour[i, 2]) << 16)
+        key = (int(np.float32(d).view(np.uint32)) << 24) | rgb
+        expected[p] = min(int(expected[p]), key)
+    keys = oracle.render_rgb(cloud, cs.camera(), cs.W, cs.H)
+    assert np.array_equal(keys, expected)
+
+
+def test_rgb_agrees_with_index_payload(oracle):
+    """Both payloads keep the same depth everywhere; where a pixel's nearest
+    point is unique they name the same point, so the colours agree."""
+    cloud = scenes.sphere_plane(40_000, seed=9).numpy()
+    m = scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), 160, 120)
+    k_idx = oracle.render_basic(cloud, m, 160, 120)
+    k_rgb = oracle.render_rgb(cloud, m, 160, 120)
+    empty = k_idx == np.uint64(0xFFFFFFFFFFFFFFFF)
+    assert np.array_equal(empty, k_rgb == np.uint64(0xFFFFFFFFFFFFFFFF))
+    assert np.array_equal(k_idx[~empty] >> np.uint64(32), k_rgb[~empty] >> np.uint64(24))
+    depth_of = {}
+    for i in range(cloud.shape[0]):
+        hit = oracle.project(m, 160, 120, *cloud[i, :3].view(np.float32).tolist())
+        if hit is not None:
+            depth_of.setdefault(hit[0], []).append(np.float32(hit[1]).view(np.uint32))
+    unique = [p for p, ds in depth_of.items() if ds.count(min(ds)) == 1]
+    assert len(unique) > 1000
+    c_idx = oracle.resolve_basic(k_idx, cloud)
+    c_rgb = oracle.resolve_rgb(k_rgb)
+    for p in unique:
+        assert c_rgb[p] == (int(c_idx[p]) & 0xFFFFFF) | 0xFF000000
+
+
 # --- resolve -------------------------------------------------------------------
 
 def test_resolve_basic_cases(oracle):

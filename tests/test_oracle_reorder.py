@@ -81,6 +81,53 @@ def test_morton_equals_octree_dfs(oracle):
     assert list(got) == expect
 
 
+def test_morton63_hand_codes(oracle):
+    rows = read_golden("morton63_cases.txt")
+    assert len(rows) >= 10
+    top = (1 << 21) - 1
+    for row in rows:
+        x, y, z, code = (int(v) for v in row[0].split())
+        cloud = _grid_cloud(np.array([[0, 0, 0], [top, top, top], [x, y, z]]))
+        codes = oracle.morton_codes63(cloud)
+        assert codes[0] == 0
+        assert int(codes[1]) == (1 << 63) - 1
+        assert int(codes[2]) == code, (x, y, z)
+
+
+def test_morton63_equals_octree_dfs(oracle):
+    """Sec. 5's 21-level octree: sorting by the 63-bit code equals depth-first
+    traversal.  The root cube is [0, 2^21)^3 (corner points at 0 and 2^21, so
+    the scale is exactly 1) and points sit at cell centres c + 0.5, exact in
+    float32; clusters of neighbouring cells and duplicates drive the
+    traversal down to the last level."""
+    rng = np.random.default_rng(12)
+    top = 1 << 21
+    cells = rng.integers(0, top, size=(300, 3))
+    base = rng.integers(0, top - 8, size=(20, 3))
+    cluster = np.concatenate([b + rng.integers(0, 4, size=(6, 3)) for b in base])
+    cells = np.concatenate([cells, cluster, cells[:30]])
+    cells = cells[rng.permutation(cells.shape[0])]
+    xyz = np.concatenate([[[0.0, 0.0, 0.0]], [[float(top)] * 3], cells + 0.5])
+    pts = cs.pack(xyz, np.zeros(xyz.shape[0], np.uint32))
+    f = np.ascontiguousarray(pts[:, :3]).view(np.float32).astype(np.float64)
+    assert np.array_equal(f, xyz)
+    expect = _octree_dfs(f, np.zeros(3), float(top) * (1.0 + 2.0 ** -30), 21)
+    got = oracle.reorder(pts, seed=0, mode=oracle.MORTON63)
+    assert list(got) == expect
+
+
+@pytest.mark.parametrize("gen", ["random", "scan"])
+def test_morton63_top_bits_are_morton30(oracle, gen):
+    """2^21 / e is 2^11 times 1024 / e exactly in float32, so the 21-bit cell
+    of a coordinate, shifted right by 11, is its 10-bit cell (both clamp at
+    the far face): the top 30 bits of the 63-bit code are the 30-bit code."""
+    cloud = (scenes.random_cloud(5000, seed=4) if gen == "random" else scenes.scan(5000, seed=4)).numpy()
+    c63 = oracle.morton_codes63(cloud)
+    c30 = oracle.morton_codes(cloud)
+    assert np.array_equal(c63 >> np.uint64(33), c30.astype(np.uint64))
+    assert np.any(c63 & np.uint64((1 << 33) - 1))
+
+
 def test_splitmix64_published_vector(oracle):
     for row in read_golden("splitmix64.txt"):
         seed, k, out = (int(v) for v in row[0].split())
@@ -117,13 +164,24 @@ def test_reorder_properties(oracle, n):
     pr = oracle.reorder(cloud, seed, oracle.SHUFFLE)
     pkeys = [oracle.splitmix64(seed, i) >> 32 for i in range(n)]
     assert pr.tolist() == sorted(range(n), key=lambda i: (pkeys[i], i))
+    # the same two orders with the 63-bit code
+    codes63 = oracle.morton_codes63(cloud) if n else np.zeros(0, np.uint64)
+    pm63 = oracle.reorder(cloud, seed, oracle.MORTON63)
+    assert pm63.tolist() == sorted(range(n), key=lambda i: (int(codes63[i]), i))
+    ps63 = oracle.reorder(cloud, seed, oracle.MORTON63_SHUFFLE, 128)
+    expect = []
+    for b in border:
+        expect.extend(pm63[b * 128:min(n, b * 128 + 128)].tolist())
+    assert ps63.tolist() == expect
 
 
 def test_reorder_degenerate_extent(oracle):
     """All points equal: every code is 0, so Morton order keeps input order."""
     cloud = cs.pack(np.tile([[1.5, -2.0, 3.0]], (300, 1)), np.arange(300, dtype=np.uint32))
     assert np.all(oracle.morton_codes(cloud) == 0)
+    assert np.all(oracle.morton_codes63(cloud) == 0)
     assert oracle.reorder(cloud, 7, oracle.MORTON).tolist() == list(range(300))
+    assert oracle.reorder(cloud, 7, oracle.MORTON63).tolist() == list(range(300))
 
 
 def test_gather(oracle):
@@ -135,5 +193,8 @@ def test_gather(oracle):
 
 def test_reorder_rejects_bad_mode(oracle):
     cloud = scenes.random_cloud(10).numpy()
+    for mode in (5, 7, -1):
+        with pytest.raises(ValueError):
+            oracle.reorder(cloud, 0, mode)
     with pytest.raises(ValueError):
-        oracle.reorder(cloud, 0, 7)
+        oracle.reorder(cloud, 0, oracle.MORTON63_SHUFFLE, batch=0)
