@@ -264,16 +264,18 @@ def time_oracle(pts_np: np.ndarray, view, repeats: int = 1) -> float:
 def oracle_baseline(cloud_host_fn, n: int, view, target_s: float) -> dict:
     """Time the CPU oracle (single thread, as it stands) on a strided sample
     of the same cloud sized to about target_s seconds of work."""
-    pilot_n = min(n, 2_000_000)
+    pilot_n = min(n, 4_000_000)
     pilot = cloud_host_fn(pilot_n)
-    t = time_oracle(pilot, view)
+    t = time_oracle(pilot, view, repeats=2)  # the first pass pays for page faults
     rate = pilot_n / max(t, 1e-6)
     sample = int(min(n, max(pilot_n, rate * target_s)))
     pts = cloud_host_fn(sample)
     dt = time_oracle(pts, view)
+    stride = max(1, n // max(sample, 1))
+    which = (f"the first {sample} of the {n} points" if stride == 1
+             else f"every {stride}th point of the {n}-point cloud ({sample} points)")
     return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample} points (every {max(1, n // sample)}th of the {n}-point cloud), one frame "
-                      f"(render + resolve), single-threaded C oracle, {dt:.2f} s"}
+            "sample": f"{which}, one frame (render + resolve), single-threaded C oracle, {dt:.2f} s"}
 
 
 # ---------------------------------------------------------------------------
@@ -361,6 +363,7 @@ def run_ours(args, cfg):
     h = ctx.handle
     fb = pcr.alloc_framebuffer(W, H, dev)
     pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+    pcr.pcr_set_lock_buffer(h, fb["locks"], 0)
 
     # --- one-time reorders (Sec. 4); original order kept for the sweep ----
     ws = torch.empty(pcr.pcr_reorder_workspace_size(n), dtype=torch.uint8, device=dev)
@@ -378,6 +381,18 @@ def run_ours(args, cfg):
         torch.cuda.synchronize()
         reorder_ms[name] = e0.elapsed_time(e1)
         orders[name] = buf
+    if not args.no_sweep:
+        # the paper's 21-level Morton code (63 bits): timed, not kept
+        for name, mode in (("morton63", pcr.PCR_ORDER_MORTON63),
+                           ("morton63_shuffle128", pcr.PCR_ORDER_MORTON63_SHUFFLE128)):
+            buf = cloud.clone()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pcr.pcr_reorder_morton_shuffle128(h, buf, n, 0x5EED, mode, ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            reorder_ms[name] = e0.elapsed_time(e1)
+            del buf
     del ws
     if args.no_sweep:
         del orders["original"]
@@ -736,6 +751,14 @@ def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
             for var in range(7):
                 row[pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_basic(h, var, True), stream, reps=10, warm=2), 4)
+            for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ):
+                row["rgb:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
+                    lambda: pcr.pcr_render_rgb(h, var, True), stream, reps=10, warm=2), 4)
+            pcr.pcr_last_device_error(h)
+            busy = round(time_loop(lambda: pcr.pcr_render_basic(h, pcr.PCR_VARIANT_BUSY_LOOP, True), stream,
+                                   reps=5, warm=1), 4)
+            # a run whose lock waits ran out dropped points: not a valid time
+            row["busy-loop"] = busy if pcr.pcr_last_device_error(h) == 0 else "wait limit reached"
             for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ):
                 row["hq:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_hq(h, 1.01, var, True), stream, reps=5, warm=1), 4)

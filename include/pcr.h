@@ -68,14 +68,18 @@ enum {
     PCR_VARIANT_DEDUP_EARLYZ = 3,  /* Sec. 3.4 with the early test ("dedup" in Sec. 5) */
     PCR_VARIANT_REDUCE = 4,        /* Sec. 3.3: all-equal warp reduction, else pairwise */
     PCR_VARIANT_REDUCE_EARLYZ = 5, /* Sec. 3.3 with the early test */
-    PCR_VARIANT_JUST_SET = 6       /* Sec. 5 "just-set": non-atomic store, no depth test;
+    PCR_VARIANT_JUST_SET = 6,      /* Sec. 5 "just-set": non-atomic store, no depth test;
                                       a speed floor, not a correct renderer */
+    PCR_VARIANT_BUSY_LOOP = 7      /* Sec. 2 and Sec. 5 "busy-loop" (Guenther et al.): early test,
+                                      then lock the pixel (compare-and-swap), update, unlock;
+                                      pcr_render_basic only, needs pcr_set_lock_buffer */
 };
 
 enum {
     PCR_RESOLVE_BASIC = 0,  /* Sec. 3.1: key buffer -> colour of the winning point */
     PCR_RESOLVE_HQ = 1,     /* Sec. 3.5: colour sums -> truncating average */
-    PCR_RESOLVE_HQ1R = 2    /* Sec. 3.5.1: packed primary + fallback sums -> truncating average */
+    PCR_RESOLVE_HQ1R = 2,   /* Sec. 3.5.1: packed primary + fallback sums -> truncating average */
+    PCR_RESOLVE_RGB = 3     /* Sec. 3.1: colour-payload keys (pcr_render_rgb) -> their colour */
 };
 
 enum {
@@ -86,7 +90,15 @@ enum {
 enum {
     PCR_ORDER_MORTON = 0,            /* Sec. 5 "Morton" */
     PCR_ORDER_MORTON_SHUFFLE128 = 1, /* Sec. 4 and Sec. 5 "Shuffled Morton" */
-    PCR_ORDER_SHUFFLE = 2            /* Sec. 5 "Shuffled" */
+    PCR_ORDER_SHUFFLE = 2,           /* Sec. 5 "Shuffled" */
+    PCR_ORDER_MORTON63 = 3,          /* Sec. 5 "Morton" with the paper's 21 levels (63-bit code) */
+    PCR_ORDER_MORTON63_SHUFFLE128 = 4 /* Sec. 4 "Shuffled Morton" over the 63-bit Morton order */
+};
+
+/* Bits of the device-side error word (pcr_last_device_error). */
+enum {
+    PCR_DEVICE_ERROR_KEY_RANGE = 1,    /* a resolve found a key naming a point outside the cloud */
+    PCR_DEVICE_ERROR_WAIT_TIMEOUT = 2  /* a busy-loop lock wait gave up (a point was dropped) */
 };
 
 typedef struct pcr_ctx pcr_ctx;
@@ -148,8 +160,11 @@ PCR_API pcr_status pcr_clear(pcr_ctx *ctx, int what);
  * the points are merged into what the buffer holds (a minimum, so several
  * calls over parts of a cloud give the same buffer as one call over all of
  * it, provided index payloads do not collide).  Key of point i:
- * float_bits(w) << 32 | i.  Errors: PCR_ERR_ARG for an unknown variant, a
- * missing matrix, viewport or key buffer. */
+ * float_bits(w) << 32 | i.  PCR_VARIANT_BUSY_LOOP also needs the lock words
+ * of pcr_set_lock_buffer (clear != 0 zeroes them too) and leaves the same
+ * buffer as the atomic variants unless a lock wait ran out (see
+ * pcr_set_lock_buffer).  Errors: PCR_ERR_ARG for an unknown variant, a
+ * missing matrix, viewport, key buffer or (BUSY_LOOP) lock buffer. */
 PCR_API pcr_status pcr_render_basic(pcr_ctx *ctx, int variant, int clear);
 
 /* Sec. 3.5: depth pass (32-bit minimum of float_bits(w)), then colour pass:
@@ -164,6 +179,25 @@ PCR_API pcr_status pcr_render_basic(pcr_ctx *ctx, int variant, int clear);
  * for a bad variant or depth_factor (not finite or <= 0), missing matrix,
  * viewport or HQ buffers. */
 PCR_API pcr_status pcr_render_hq(pcr_ctx *ctx, float depth_factor, int variant, int clear);
+
+/* Sec. 3.1 with the key exactly as Listing "basic" prints it: each visible
+ * point offers (float_bits(w) << 24) | (rgba & 0xFFFFFF) to the key buffer,
+ * whose minimum keeps the nearest point and, at equal depth, the smallest
+ * 24-bit colour.  The key buffer of pcr_set_framebuffer is used; resolve with
+ * PCR_RESOLVE_RGB.  Variants as pcr_render_basic except BUSY_LOOP; every
+ * variant but JUST_SET leaves the same buffer.  clear != 0 first sets the
+ * keys to all ones.  Errors: PCR_ERR_ARG for a bad variant or a missing
+ * matrix, viewport or key buffer. */
+PCR_API pcr_status pcr_render_rgb(pcr_ctx *ctx, int variant, int clear);
+
+/* Attach the per-pixel lock words of PCR_VARIANT_BUSY_LOOP: uint32[width *
+ * height] device memory, caller-owned, 4-byte aligned, all zero between
+ * renders (pcr_render_basic with clear != 0 zeroes them; every lock a render
+ * takes it gives back).  NULL detaches.  wait_limit_us bounds each lock wait
+ * (0 = 100000 us): a wait that runs out sets PCR_DEVICE_ERROR_WAIT_TIMEOUT,
+ * drops that point and makes the other waits of the launch give up at once,
+ * so the launch always ends.  Errors: PCR_ERR_ARG if misaligned. */
+PCR_API pcr_status pcr_set_lock_buffer(pcr_ctx *ctx, void *dev_locks, uint32_t wait_limit_us);
 
 /* Borrow the primary buffer of the single-atomic high-quality variant
  * (Sec. 3.5.1, "HQS1R"): uint64[width*height], 8-byte aligned, holding
@@ -229,6 +263,11 @@ PCR_API pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t *bytes);
  *     key and keep their inner order.
  *   PCR_ORDER_SHUFFLE: point i gets key = high 32 bits of SplitMix64 output
  *     i; points are stably sorted by key.
+ *   PCR_ORDER_MORTON63: as PCR_ORDER_MORTON with the paper's 21 levels: a
+ *     63-bit code, 21 bits per axis, floor((v - min) * (2^21 / extent))
+ *     clamped to [0, 2^21 - 1].  Its top 30 bits are the 30-bit code.
+ *   PCR_ORDER_MORTON63_SHUFFLE128: the batches of PCR_ORDER_MORTON_SHUFFLE128
+ *     over the PCR_ORDER_MORTON63 order.
  * dev_points: n records, 16-byte aligned.  dev_workspace: at least the
  * pcr_reorder_workspace_size bytes, 256-byte aligned; its contents are
  * scratch.  dev_perm_out: NULL or uint32[n], receives perm[new] = old.
@@ -468,9 +507,10 @@ PCR_API pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx *ctx, void *dev
 PCR_API const char *pcr_status_string(pcr_status status);
 
 /* Read and clear the device-side error word of the context's device
- * (synchronises the stream).  Bit 0: a resolve found a key naming a point
- * index outside the borrowed cloud (the pixel took the background colour).
- * *code is 0 when nothing was reported.  Errors: PCR_ERR_ARG if code is NULL,
+ * (synchronises the stream): PCR_DEVICE_ERROR_KEY_RANGE when a resolve found
+ * a key naming a point index outside the borrowed cloud (the pixel took the
+ * background colour), PCR_DEVICE_ERROR_WAIT_TIMEOUT when a busy-loop lock
+ * wait gave up.  *code is 0 when nothing was reported.  Errors: PCR_ERR_ARG if code is NULL,
  * PCR_ERR_CUDA if the read fails. */
 PCR_API pcr_status pcr_last_device_error(pcr_ctx *ctx, uint32_t *code);
 

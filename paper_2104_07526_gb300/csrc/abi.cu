@@ -21,6 +21,8 @@ struct pcr_ctx {
   unsigned long long* rg = nullptr;
   unsigned long long* ba = nullptr;
   unsigned long long* primary = nullptr;  // HQS1R primary words
+  uint32_t* locks = nullptr;              // busy-loop lock words
+  uint64_t lock_wait_ns = 100000000ull;
 };
 
 namespace {
@@ -170,6 +172,25 @@ pcr_status pcr_clear(pcr_ctx* ctx, int what) {
 }
 
 pcr_status pcr_render_basic(pcr_ctx* ctx, int variant, int clear) {
+  if (!ctx || variant < PCR_VARIANT_ATOMICMIN || variant > PCR_VARIANT_BUSY_LOOP) return PCR_ERR_ARG;
+  if (!view_ready(ctx) || !ctx->keys) return PCR_ERR_ARG;
+  const bool busy = variant == PCR_VARIANT_BUSY_LOOP;
+  if (busy && !ctx->locks) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  if (clear) e = pcr::launch_fill_u64(ctx->keys, pixels(ctx), pcr::kEmptyKey, ctx->stream, ctx->dev);
+  if (e == cudaSuccess && clear && busy) e = pcr::launch_fill_u32(ctx->locks, pixels(ctx), 0u, ctx->stream, ctx->dev);
+  if (e != cudaSuccess) return PCR_ERR_CUDA;
+  const uint32_t n = static_cast<uint32_t>(ctx->n);
+  if (busy)
+    return from_cuda(pcr::launch_render_busy(ctx->points, n, view_params(ctx), ctx->keys, ctx->locks,
+                                             ctx->lock_wait_ns, ctx->stream, ctx->dev));
+  return from_cuda(pcr::launch_render_basic(variant, ctx->points, n, view_params(ctx), ctx->keys, ctx->stream,
+                                            ctx->dev));
+}
+
+pcr_status pcr_render_rgb(pcr_ctx* ctx, int variant, int clear) {
   if (!ctx || variant < PCR_VARIANT_ATOMICMIN || variant > PCR_VARIANT_JUST_SET) return PCR_ERR_ARG;
   if (!view_ready(ctx) || !ctx->keys) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
@@ -178,8 +199,15 @@ pcr_status pcr_render_basic(pcr_ctx* ctx, int variant, int clear) {
     const cudaError_t e = pcr::launch_fill_u64(ctx->keys, pixels(ctx), pcr::kEmptyKey, ctx->stream, ctx->dev);
     if (e != cudaSuccess) return PCR_ERR_CUDA;
   }
-  return from_cuda(pcr::launch_render_basic(variant, ctx->points, static_cast<uint32_t>(ctx->n), view_params(ctx),
-                                            ctx->keys, ctx->stream, ctx->dev));
+  return from_cuda(pcr::launch_render_rgb(variant, ctx->points, static_cast<uint32_t>(ctx->n), view_params(ctx),
+                                          ctx->keys, ctx->stream, ctx->dev));
+}
+
+pcr_status pcr_set_lock_buffer(pcr_ctx* ctx, void* dev_locks, uint32_t wait_limit_us) {
+  if (!ctx || (dev_locks && !aligned(dev_locks, 4))) return PCR_ERR_ARG;
+  ctx->locks = static_cast<uint32_t*>(dev_locks);
+  ctx->lock_wait_ns = 1000ull * (wait_limit_us ? wait_limit_us : 100000u);
+  return PCR_OK;
 }
 
 pcr_status pcr_render_hq(pcr_ctx* ctx, float depth_factor, int variant, int clear) {
@@ -242,6 +270,12 @@ pcr_status pcr_resolve(pcr_ctx* ctx, int mode, void* dev_rgba_out, uint32_t back
     return from_cuda(pcr::launch_resolve_hq1r(ctx->primary, ctx->rg, ctx->ba, pixels(ctx), background_rgba, out,
                                               ctx->stream, ctx->dev));
   }
+  if (mode == PCR_RESOLVE_RGB) {
+    if (!ctx->keys) return PCR_ERR_ARG;
+    DeviceScope scope(ctx->dev.id);
+    if (!scope.ok()) return PCR_ERR_CUDA;
+    return from_cuda(pcr::launch_resolve_rgb(ctx->keys, pixels(ctx), background_rgba, out, ctx->stream, ctx->dev));
+  }
   if (mode == PCR_RESOLVE_HQ) {
     if (!ctx->rg || !ctx->ba) return PCR_ERR_ARG;
     DeviceScope scope(ctx->dev.id);
@@ -278,7 +312,7 @@ pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t* bytes) {
 
 pcr_status pcr_reorder_morton_shuffle128(pcr_ctx* ctx, void* dev_points, uint64_t n, uint64_t seed, int mode,
                                          void* dev_workspace, uint64_t workspace_bytes, uint32_t* dev_perm_out) {
-  if (!ctx || n > kMaxPoints || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_SHUFFLE) return PCR_ERR_ARG;
+  if (!ctx || n > kMaxPoints || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_MORTON63_SHUFFLE128) return PCR_ERR_ARG;
   if (n == 0) return PCR_OK;
   if (!dev_points || !aligned(dev_points, 16) || (dev_perm_out && !aligned(dev_perm_out, 4))) return PCR_ERR_ARG;
   if (!dev_workspace || !aligned(dev_workspace, 256) || workspace_bytes < pcr::reorder_workspace_bytes(n))
@@ -291,7 +325,7 @@ pcr_status pcr_reorder_morton_shuffle128(pcr_ctx* ctx, void* dev_points, uint64_
 
 pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx* ctx, void* dev_points, uint64_t n, uint64_t seed,
                                                  int mode, uint32_t* dev_perm_out) {
-  if (!ctx || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_SHUFFLE) return PCR_ERR_ARG;
+  if (!ctx || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_MORTON63_SHUFFLE128) return PCR_ERR_ARG;
   if (n > PCR_REORDER_NOALLOC_MAX_POINTS) return PCR_ERR_WORKSPACE;
   if (n == 0) return PCR_OK;
   if (!dev_points || !aligned(dev_points, 16) || (dev_perm_out && !aligned(dev_perm_out, 4))) return PCR_ERR_ARG;

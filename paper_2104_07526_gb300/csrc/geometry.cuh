@@ -16,8 +16,40 @@ namespace geom {
 // warp adds directly instead of aggregating.
 constexpr int kAggregateMaxRuns = 12;
 
+// Key payloads (Sec. 3.1): the point index below the depth bits (the
+// colour is looked up in the resolve), or, as Listing "basic" prints it, the
+// 24-bit colour below depth bits shifted by 24.
+enum Payload { kPayloadIndex = 0, kPayloadRgb = 1 };
+
 __device__ __forceinline__ unsigned long long make_key(float w, uint32_t idx) {
   return (static_cast<unsigned long long>(__float_as_uint(w)) << 32) | idx;
+}
+
+template <int P>
+__device__ __forceinline__ unsigned long long make_payload_key(float w, uint32_t payload) {
+  if constexpr (P == kPayloadRgb) {
+    return (static_cast<unsigned long long>(__float_as_uint(w)) << 24) | (payload & 0xFFFFFFu);
+  } else {
+    return make_key(w, payload);
+  }
+}
+
+// The lane of `tied` (the lanes of a group whose depth equals the group's
+// minimum; `mine` says whether this lane is one of them) that holds the
+// group's smallest key.  With the index payload the index grows with the
+// lane inside a row of the chunk, so it is the lowest tied lane; with the
+// colour payload it is the lowest tied lane with the smallest colour, found
+// by the tied lanes alone (others get 32, no lane).
+template <int P>
+__device__ __forceinline__ uint32_t min_key_lane(uint32_t tied, bool mine, uint32_t payload) {
+  if constexpr (P == kPayloadRgb) {
+    if (!mine) return 32u;
+    const uint32_t c = payload & 0xFFFFFFu;
+    const uint32_t cmin = __reduce_min_sync(tied, c);
+    return static_cast<uint32_t>(__ffs(__ballot_sync(tied, c == cmin)) - 1);
+  } else {
+    return static_cast<uint32_t>(__ffs(tied) - 1);
+  }
 }
 
 // Walk the point chunks of this warp.  For each chunk, f(r, base, full)
@@ -75,12 +107,13 @@ __host__ __device__ constexpr bool reads_early() {
   return V == PCR_VARIANT_EARLYZ || V == PCR_VARIANT_DEDUP_EARLYZ || V == PCR_VARIANT_REDUCE_EARLYZ;
 }
 
-// One point slot after projection.  `seen` is this lane's earlier read of
-// its pixel (variants with the early test only).
-template <int V>
+// One point slot after projection.  `payload` is the point index or its
+// rgba word (P); `seen` is this lane's earlier read of its pixel (variants
+// with the early test only).
+template <int V, int P = kPayloadIndex>
 __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix, float w,
-                                         uint32_t idx, unsigned long long seen, uint64_t pol) {
-  const unsigned long long key = make_key(w, idx);
+                                         uint32_t payload, unsigned long long seen, uint64_t pol) {
+  const unsigned long long key = make_payload_key<P>(w, payload);
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
     // Sec. 3.1: atomicMin(framebuffer[pixelID], point)
     if (vis) red_min_u64(fb + pix, key, pol);
@@ -91,16 +124,15 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
   } else if constexpr (V == PCR_VARIANT_DEDUP) {
     // Sec. 3.4: lanes with the same pixel form a group; only the lane with
     // the group's smallest key writes.  Keys reduce on the full 64 bits
-    // (depth, then index), so each distinct pixel costs one atomic per warp
-    // even when depths tie.  Within a row of the chunk the index grows with
-    // the lane, so the smallest index among the smallest depths is the
-    // lowest such lane.
+    // (depth, then payload), so each distinct pixel costs one atomic per
+    // warp even when depths tie.
     const uint32_t tag = vis ? pix : kNoPixel;
     const uint32_t peers = __match_any_sync(kFullMask, tag);
     const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
     const uint32_t hmin = __reduce_min_sync(peers, hi);
     const uint32_t tied = __ballot_sync(kFullMask, hi == hmin) & peers;
-    if (vis && lane_id() == static_cast<uint32_t>(__ffs(tied) - 1)) red_min_u64(fb + pix, key, pol);
+    const uint32_t first = min_key_lane<P>(tied, hi == hmin, payload);
+    if (vis && lane_id() == first) red_min_u64(fb + pix, key, pol);
   } else if constexpr (V == PCR_VARIANT_DEDUP_EARLYZ) {
     // Sec. 3.4 with Sec. 3.2, tests swapped: every visible lane has read its
     // pixel already (cheap, mostly L2 hits); only lanes still closer than the
@@ -114,7 +146,13 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
       const uint32_t peers = __match_any_sync(active, pix);
       const uint32_t hi = __float_as_uint(w);
       const uint32_t hmin = __reduce_min_sync(peers, hi);
-      const uint32_t first = __reduce_min_sync(peers, hi == hmin ? lane_id() : 32u);
+      uint32_t first;
+      if constexpr (P == kPayloadRgb) {
+        const uint32_t tied = __ballot_sync(peers, hi == hmin);
+        first = min_key_lane<P>(tied, hi == hmin, payload);
+      } else {
+        first = __reduce_min_sync(peers, hi == hmin ? lane_id() : 32u);
+      }
       if (lane_id() == first) red_min_u64(fb + pix, key, pol);
     }
   } else if constexpr (V == PCR_VARIANT_REDUCE || V == PCR_VARIANT_REDUCE_EARLYZ) {
@@ -129,11 +167,14 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
       const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
       const uint32_t hmin = __reduce_min_sync(kFullMask, hi);
       const uint32_t tied = __ballot_sync(kFullMask, hi == hmin);
-      write = vis && lane_id() == static_cast<uint32_t>(__ffs(tied) - 1);
+      write = vis && lane_id() == min_key_lane<P>(tied, hi == hmin, payload);
     } else {
       const uint32_t other_tag = __shfl_xor_sync(kFullMask, tag, 1);
       const unsigned long long other_key = __shfl_xor_sync(kFullMask, key, 1);
-      if (other_tag == tag) write = vis && key < other_key;
+      if (other_tag == tag) {
+        // colour keys of two points can be equal: the even lane keeps it
+        write = vis && (key < other_key || (P == kPayloadRgb && key == other_key && (lane_id() & 1u) == 0u));
+      }
     }
     if (write && (V == PCR_VARIANT_REDUCE || key < seen)) red_min_u64(fb + pix, key, pol);
   } else {

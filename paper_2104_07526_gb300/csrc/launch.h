@@ -19,6 +19,13 @@ cudaError_t launch_fill_u64(unsigned long long* p, uint64_t count, unsigned long
                             const Device& d);
 cudaError_t launch_clear_hq(uint32_t* depth, unsigned long long* rg, unsigned long long* ba, uint64_t npx,
                             cudaStream_t s, const Device& d);
+cudaError_t launch_render_rgb(int variant, const uint4* pts, uint32_t n, const ViewParams& v,
+                              unsigned long long* keys, cudaStream_t s, const Device& d);
+cudaError_t launch_render_busy(const uint4* pts, uint32_t n, const ViewParams& v, unsigned long long* keys,
+                               uint32_t* locks, uint64_t limit_ns, cudaStream_t s, const Device& d);
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t count, uint32_t value, cudaStream_t s, const Device& d);
+cudaError_t launch_resolve_rgb(const unsigned long long* keys, uint64_t npx, uint32_t background, uint32_t* out,
+                               cudaStream_t s, const Device& d);
 cudaError_t launch_render_basic(int variant, const uint4* pts, uint32_t n, const ViewParams& v,
                                 unsigned long long* keys, cudaStream_t s, const Device& d);
 cudaError_t launch_hq_depth(int variant, const uint4* pts, uint32_t n, const ViewParams& v, uint32_t* depth,

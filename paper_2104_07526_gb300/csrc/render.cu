@@ -21,7 +21,11 @@ namespace {
 
 using namespace geom;
 
+// Device-side error word (PCR_DEVICE_ERROR_* bits), read and cleared by
+// pcr_last_device_error.
 __device__ uint32_t g_error_word;
+constexpr uint32_t kErrorKeyRange = PCR_DEVICE_ERROR_KEY_RANGE;
+constexpr uint32_t kErrorWaitTimeout = PCR_DEVICE_ERROR_WAIT_TIMEOUT;
 
 #ifndef PCR_GEOMETRY_UNROLL
 #define PCR_GEOMETRY_UNROLL 4
@@ -37,7 +41,8 @@ constexpr int kUnroll = PCR_GEOMETRY_UNROLL;
 constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
 // Each chunk runs in three phases so independent memory round trips overlap:
 // project all U points, issue all U early reads, then test and write.
-template <int V, int U>
+// P selects the key payload: the point index, or the 24-bit colour.
+template <int V, int U, int P>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                            unsigned long long* __restrict__ fb) {
   const uint64_t pol_stream = policy_evict_first();
@@ -56,7 +61,93 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_basic(const uin
 #pragma unroll
     for (int u = 0; u < U; ++u) seen[u] = (reads_early<V>() && vis[u]) ? load_relaxed_u64(fb + pix[u]) : 0ull;
 #pragma unroll
-    for (int u = 0; u < U; ++u) emit_key<V>(fb, vis[u], pix[u], w[u], base + 32u * u, seen[u], pol_fb);
+    for (int u = 0; u < U; ++u)
+      emit_key<V, P>(fb, vis[u], pix[u], w[u], P == kPayloadRgb ? r[u].w : base + 32u * u, seen[u], pol_fb);
+  });
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 2 and Sec. 5 "busy-loop" (Guenther et al.): lock the pixel with a
+// compare-and-swap, update it, unlock; with their early depth test.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t cas_acquire_u32(uint32_t* p, uint32_t expect, uint32_t value) {
+  uint32_t old;
+  asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "l"(p), "r"(expect), "r"(value)
+               : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void store_release_u32(uint32_t* p, uint32_t value) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(value) : "memory");
+}
+
+__device__ __forceinline__ void store_relaxed_u64(unsigned long long* p, unsigned long long value) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(value) : "memory");
+}
+
+// Take the pixel's lock, keep the smaller of the stored and the new key,
+// release.  Between attempts the early test is repeated: once the pixel holds
+// a key at least as small, this point has nothing left to do.  The spin is
+// bounded: it gives up when it has waited longer than limit_ns (by the global
+// nanosecond timer), after kBusyMaxAttempts attempts (at least half a second
+// of backoff), or when another thread has already given up; it then sets
+// kErrorWaitTimeout in the error word and drops this point.  Backoff doubles
+// from 32 to 1024 ns between attempts.
+constexpr uint32_t kBusyMaxAttempts = 1u << 20;
+__device__ __forceinline__ void busy_update(unsigned long long* __restrict__ fb, uint32_t* __restrict__ locks,
+                                            uint32_t pix, unsigned long long key, uint64_t limit_ns) {
+  uint32_t* lock = locks + pix;
+  uint64_t t0 = 0;
+  uint32_t backoff = 32;
+  for (uint32_t attempt = 0;; ++attempt) {
+    if (attempt > 0 && load_relaxed_u64(fb + pix) <= key) return;
+    if (cas_acquire_u32(lock, 0u, 1u) == 0u) {
+      const unsigned long long cur = load_relaxed_u64(fb + pix);
+      if (key < cur) store_relaxed_u64(fb + pix, key);
+      store_release_u32(lock, 0u);
+      return;
+    }
+    if (attempt == 0) t0 = global_ns();
+    if ((attempt & 7u) == 7u && (attempt >= kBusyMaxAttempts || global_ns() - t0 > limit_ns ||
+                                 (load_relaxed_u32(&g_error_word) & kErrorWaitTimeout) != 0u)) {
+      atomicOr(&g_error_word, kErrorWaitTimeout);
+      return;
+    }
+    __nanosleep(backoff);
+    backoff = backoff < 1024u ? backoff * 2u : 1024u;
+  }
+}
+
+template <int U>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_busy(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+                                                          unsigned long long* __restrict__ fb,
+                                                          uint32_t* __restrict__ locks, uint64_t limit_ns) {
+  const uint64_t pol_stream = policy_evict_first();
+  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+    uint32_t pix[U];
+    float w[U];
+    bool vis[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      pix[u] = 0;
+      w[u] = 0.0f;
+      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
+    }
+    unsigned long long seen[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) seen[u] = vis[u] ? load_relaxed_u64(fb + pix[u]) : 0ull;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned long long key = make_key(w[u], base + 32u * u);
+      if (vis[u] && key < seen[u]) busy_update(fb, locks, pix[u], key, limit_ns);
+    }
   });
 }
 
@@ -249,10 +340,27 @@ __global__ void k_resolve_basic(const unsigned long long* __restrict__ keys, uin
       if (idx < n)
         c = __ldg(words + 4ull * idx + 3);
       else
-        atomicOr(&g_error_word, 1u);
+        atomicOr(&g_error_word, kErrorKeyRange);
     }
     out[p] = c;
   }
+}
+
+// Sec. 3.1, Listing "resolve" for colour-payload keys: the colour is in the
+// key's low 24 bits; alpha 255.
+__global__ void k_resolve_rgb(const unsigned long long* __restrict__ keys, uint64_t npx, uint32_t background,
+                              uint32_t* __restrict__ out) {
+  for (uint64_t p = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; p < npx;
+       p += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long k = keys[p];
+    out[p] = k == kEmptyKey ? background : (static_cast<uint32_t>(k) & 0xFFFFFFu) | 0xFF000000u;
+  }
+}
+
+__global__ void k_fill_u32(uint32_t* __restrict__ p, uint64_t count, uint32_t value) {
+  for (uint64_t i = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; i < count;
+       i += static_cast<uint64_t>(gridDim.x) * blockDim.x)
+    p[i] = value;
 }
 
 // Sec. 3.5, Listing "hqs_resolve": truncating average, alpha 255.
@@ -324,12 +432,27 @@ dim3 screen_grid(uint64_t npx, const Device& d) {
   return dim3(static_cast<unsigned>(need < cap ? (need > 0 ? need : 1) : cap));
 }
 
-template <int V>
+template <int V, int P>
 cudaError_t launch_basic_v(const uint4* pts, uint32_t n, const ViewParams& v, unsigned long long* keys, cudaStream_t s,
                            const Device& d) {
-  constexpr auto k = k_render_basic<V, kUnroll>;
+  constexpr auto k = k_render_basic<V, kUnroll, P>;
   k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, keys);
   return cudaGetLastError();
+}
+
+template <int P>
+cudaError_t launch_basic_p(int variant, const uint4* pts, uint32_t n, const ViewParams& v, unsigned long long* keys,
+                           cudaStream_t s, const Device& d) {
+  switch (variant) {
+    case PCR_VARIANT_ATOMICMIN: return launch_basic_v<PCR_VARIANT_ATOMICMIN, P>(pts, n, v, keys, s, d);
+    case PCR_VARIANT_EARLYZ: return launch_basic_v<PCR_VARIANT_EARLYZ, P>(pts, n, v, keys, s, d);
+    case PCR_VARIANT_DEDUP: return launch_basic_v<PCR_VARIANT_DEDUP, P>(pts, n, v, keys, s, d);
+    case PCR_VARIANT_DEDUP_EARLYZ: return launch_basic_v<PCR_VARIANT_DEDUP_EARLYZ, P>(pts, n, v, keys, s, d);
+    case PCR_VARIANT_REDUCE: return launch_basic_v<PCR_VARIANT_REDUCE, P>(pts, n, v, keys, s, d);
+    case PCR_VARIANT_REDUCE_EARLYZ: return launch_basic_v<PCR_VARIANT_REDUCE_EARLYZ, P>(pts, n, v, keys, s, d);
+    case PCR_VARIANT_JUST_SET: return launch_basic_v<PCR_VARIANT_JUST_SET, P>(pts, n, v, keys, s, d);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int V>
@@ -359,16 +482,34 @@ cudaError_t launch_clear_hq(uint32_t* depth, unsigned long long* rg, unsigned lo
 cudaError_t launch_render_basic(int variant, const uint4* pts, uint32_t n, const ViewParams& v,
                                 unsigned long long* keys, cudaStream_t s, const Device& d) {
   if (n == 0) return cudaSuccess;
-  switch (variant) {
-    case PCR_VARIANT_ATOMICMIN: return launch_basic_v<PCR_VARIANT_ATOMICMIN>(pts, n, v, keys, s, d);
-    case PCR_VARIANT_EARLYZ: return launch_basic_v<PCR_VARIANT_EARLYZ>(pts, n, v, keys, s, d);
-    case PCR_VARIANT_DEDUP: return launch_basic_v<PCR_VARIANT_DEDUP>(pts, n, v, keys, s, d);
-    case PCR_VARIANT_DEDUP_EARLYZ: return launch_basic_v<PCR_VARIANT_DEDUP_EARLYZ>(pts, n, v, keys, s, d);
-    case PCR_VARIANT_REDUCE: return launch_basic_v<PCR_VARIANT_REDUCE>(pts, n, v, keys, s, d);
-    case PCR_VARIANT_REDUCE_EARLYZ: return launch_basic_v<PCR_VARIANT_REDUCE_EARLYZ>(pts, n, v, keys, s, d);
-    case PCR_VARIANT_JUST_SET: return launch_basic_v<PCR_VARIANT_JUST_SET>(pts, n, v, keys, s, d);
-    default: return cudaErrorInvalidValue;
-  }
+  return launch_basic_p<kPayloadIndex>(variant, pts, n, v, keys, s, d);
+}
+
+cudaError_t launch_render_rgb(int variant, const uint4* pts, uint32_t n, const ViewParams& v,
+                              unsigned long long* keys, cudaStream_t s, const Device& d) {
+  if (n == 0) return cudaSuccess;
+  return launch_basic_p<kPayloadRgb>(variant, pts, n, v, keys, s, d);
+}
+
+cudaError_t launch_render_busy(const uint4* pts, uint32_t n, const ViewParams& v, unsigned long long* keys,
+                               uint32_t* locks, uint64_t limit_ns, cudaStream_t s, const Device& d) {
+  if (n == 0) return cudaSuccess;
+  constexpr auto k = k_render_busy<kUnroll>;
+  k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, keys, locks, limit_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u32(uint32_t* p, uint64_t count, uint32_t value, cudaStream_t s, const Device& d) {
+  if (count == 0) return cudaSuccess;
+  k_fill_u32<<<screen_grid(count, d), kThreads, 0, s>>>(p, count, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resolve_rgb(const unsigned long long* keys, uint64_t npx, uint32_t background, uint32_t* out,
+                               cudaStream_t s, const Device& d) {
+  if (npx == 0) return cudaSuccess;
+  k_resolve_rgb<<<screen_grid(npx, d), kThreads, 0, s>>>(keys, npx, background, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_hq_depth(int variant, const uint4* pts, uint32_t n, const ViewParams& v, uint32_t* depth,

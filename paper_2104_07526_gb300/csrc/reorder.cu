@@ -1,6 +1,9 @@
 // Vertex-order kernels (Sec. 4, and the orderings listed in Sec. 5):
-// bounds, 30-bit Morton codes, a stable LSD radix sort of (32-bit key,
-// 32-bit index) pairs, the 128-point batch shuffle and the record gather.
+// bounds, 30-bit and 63-bit Morton codes, a stable LSD radix sort of (32-bit
+// key, 32-bit index) pairs, the 128-point batch shuffle and the record
+// gather.  A 63-bit code sorts as two 32-bit halves: the low half first, then
+// the high half (gathered through the first sort's permutation), both
+// stable, which is a stable sort by the whole code.
 //
 // Radix sort: 8-bit digits, one pass per digit, three steps per pass:
 //   1. k_sort_hist: per tile of 8192 keys, count each digit.
@@ -165,6 +168,58 @@ __global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, u
     keys[i] = code;
     vals[i] = static_cast<uint32_t>(i);
   }
+}
+
+// Spread the low 21 bits of v so bit i lands on bit 3i.
+__device__ __forceinline__ uint64_t spread3_21(uint32_t x) {
+  uint64_t v = x & 0x1FFFFFu;
+  v = (v | (v << 32)) & 0x001F00000000FFFFull;
+  v = (v | (v << 16)) & 0x001F0000FF0000FFull;
+  v = (v | (v << 8)) & 0x100F00F00F00F00Full;
+  v = (v | (v << 4)) & 0x10C30C30C30C30C3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t quantise21(float v, float lo, float scale) {
+  const float f = floorf(__fmul_rn(__fsub_rn(v, lo), scale));
+  if (!(f >= 0.0f)) return 0u;
+  if (f >= 2097151.0f) return 2097151u;
+  return static_cast<uint32_t>(f);
+}
+
+// Sec. 5 with the paper's 21 levels: the same cube, 2^21 cells per axis.
+// Writes the code's low 32 bits to keys_lo and its high 31 bits to hi.
+__global__ void __launch_bounds__(256) k_morton63(const uint4* __restrict__ pts, uint32_t n,
+                                                  const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys_lo,
+                                                  uint32_t* __restrict__ hi, uint32_t* __restrict__ vals) {
+  const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
+  const float top[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
+  float ext = __fsub_rn(top[0], lo[0]);
+  const float ey = __fsub_rn(top[1], lo[1]);
+  const float ez = __fsub_rn(top[2], lo[2]);
+  if (ey > ext) ext = ey;
+  if (ez > ext) ext = ez;
+  const bool degenerate = !(ext > 0.0f) || !(ext < __int_as_float(kInfBits));
+  const float scale = degenerate ? 0.0f : __fdiv_rn(2097152.0f, ext);
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
+    uint64_t code = 0;
+    if (!degenerate) {
+      const uint4 r = __ldcs(pts + i);
+      code = (spread3_21(quantise21(__uint_as_float(r.x), lo[0], scale)) << 2) |
+             (spread3_21(quantise21(__uint_as_float(r.y), lo[1], scale)) << 1) |
+             spread3_21(quantise21(__uint_as_float(r.z), lo[2], scale));
+    }
+    keys_lo[i] = static_cast<uint32_t>(code);
+    hi[i] = static_cast<uint32_t>(code >> 32);
+    vals[i] = static_cast<uint32_t>(i);
+  }
+}
+
+// dst[j] = src[idx[j]]
+__global__ void __launch_bounds__(256) k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx,
+                                                    uint32_t* __restrict__ dst, uint32_t n) {
+  for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < n; j += gridDim.x * 256ull) dst[j] = src[idx[j]];
 }
 
 // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output k of the generator
@@ -484,15 +539,31 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   if (mode == PCR_ORDER_SHUFFLE) {
     k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], vals[0]);
     e = radix_sort(keys, vals, n, 32, counts, partials, s, out);
-  } else {
+  } else if (mode == PCR_ORDER_MORTON || mode == PCR_ORDER_MORTON_SHUFFLE128) {
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc);
     k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], vals[0]);
     e = radix_sort(keys, vals, n, 30, counts, partials, s, out);
+  } else {
+    // 63-bit code: the high halves wait in the record-copy region, which is
+    // not needed until the final gather.
+    uint32_t* hi = reinterpret_cast<uint32_t*>(ws + l.pts_copy);
+    k_bounds_init<<<1, 32, 0, s>>>(misc);
+    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc);
+    k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi, vals[0]);
+    int a = 0;
+    e = radix_sort(keys, vals, n, 32, counts, partials, s, a);
+    if (e != cudaSuccess) return e;
+    k_gather_u32<<<grid, 256, 0, s>>>(hi, vals[a], keys[a], n);
+    uint32_t* hkeys[2] = {keys[a], keys[a ^ 1]};
+    uint32_t* hvals[2] = {vals[a], vals[a ^ 1]};
+    int b = 0;
+    e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b);
+    out = a ^ b;
   }
   if (e != cudaSuccess) return e;
   uint32_t* perm = vals[out];
-  if (mode == PCR_ORDER_MORTON_SHUFFLE128) {
+  if (mode == PCR_ORDER_MORTON_SHUFFLE128 || mode == PCR_ORDER_MORTON63_SHUFFLE128) {
     const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};

@@ -24,13 +24,15 @@ PCR_VARIANT_DEDUP_EARLYZ = 3
 PCR_VARIANT_REDUCE = 4
 PCR_VARIANT_REDUCE_EARLYZ = 5
 PCR_VARIANT_JUST_SET = 6
+PCR_VARIANT_BUSY_LOOP = 7
 EXACT_VARIANTS = (0, 1, 2, 3, 4, 5)
 VARIANT_NAMES = {0: "atomicMin", 1: "early-z", 2: "dedup", 3: "dedup+early-z", 4: "reduce",
-                 5: "reduce+early-z", 6: "just-set"}
+                 5: "reduce+early-z", 6: "just-set", 7: "busy-loop"}
 
 PCR_RESOLVE_BASIC = 0
 PCR_RESOLVE_HQ = 1
 PCR_RESOLVE_HQ1R = 2
+PCR_RESOLVE_RGB = 3
 
 PCR_CLEAR_KEYS = 1
 PCR_CLEAR_HQ = 2
@@ -43,6 +45,11 @@ PCR_BATCH_MAX_VIEWS = 256
 PCR_ORDER_MORTON = 0
 PCR_ORDER_MORTON_SHUFFLE128 = 1
 PCR_ORDER_SHUFFLE = 2
+PCR_ORDER_MORTON63 = 3
+PCR_ORDER_MORTON63_SHUFFLE128 = 4
+
+PCR_DEVICE_ERROR_KEY_RANGE = 1
+PCR_DEVICE_ERROR_WAIT_TIMEOUT = 2
 
 
 class PcrBatchCloud(C.Structure):
@@ -110,6 +117,8 @@ _SIGS = {
     "pcr_set_framebuffer": [_VP, _VP, _VP, _VP, _VP],
     "pcr_clear": [_VP, _INT],
     "pcr_render_basic": [_VP, _INT, _INT],
+    "pcr_render_rgb": [_VP, _INT, _INT],
+    "pcr_set_lock_buffer": [_VP, _VP, _U32],
     "pcr_render_hq": [_VP, _FLT, _INT, _INT],
     "pcr_resolve": [_VP, _INT, _VP, _U32],
     "pcr_set_hq1r_buffer": [_VP, _VP],
@@ -255,6 +264,14 @@ def pcr_render_basic(ctx: int, variant: int = PCR_VARIANT_DEDUP_EARLYZ, clear: b
 
 def pcr_render_hq(ctx: int, depth_factor: float = 1.01, variant: int = PCR_VARIANT_DEDUP_EARLYZ, clear: bool = True):
     _check(lib().pcr_render_hq(ctx, depth_factor, variant, int(bool(clear))), "pcr_render_hq")
+
+
+def pcr_render_rgb(ctx: int, variant: int = PCR_VARIANT_DEDUP_EARLYZ, clear: bool = True):
+    _check(lib().pcr_render_rgb(ctx, variant, int(bool(clear))), "pcr_render_rgb")
+
+
+def pcr_set_lock_buffer(ctx: int, locks=None, wait_limit_us: int = 0):
+    _check(lib().pcr_set_lock_buffer(ctx, _dptr(locks, "locks"), wait_limit_us), "pcr_set_lock_buffer")
 
 
 def pcr_set_hq1r_buffer(ctx: int, primary=None):
@@ -450,7 +467,8 @@ def pcr_last_device_error(ctx: int) -> int:
 
 def alloc_framebuffer(width: int, height: int, device="cuda", hq: bool = True) -> dict:
     """Device tensors for one viewport: keys (int64 storage of uint64),
-    hq_depth (int32 storage of uint32), hq_rg, hq_ba and the rgba image."""
+    hq_depth (int32 storage of uint32), hq_rg, hq_ba, the HQS1R primary
+    words, the busy-loop lock words (zeroed) and the rgba image."""
     import torch
     npx = width * height
     fb = {"keys": torch.empty(npx, dtype=torch.int64, device=device),
@@ -460,6 +478,7 @@ def alloc_framebuffer(width: int, height: int, device="cuda", hq: bool = True) -
         fb["hq_rg"] = torch.empty(npx, dtype=torch.int64, device=device)
         fb["hq_ba"] = torch.empty(npx, dtype=torch.int64, device=device)
         fb["hq1r_primary"] = torch.empty(npx, dtype=torch.int64, device=device)
+    fb["locks"] = torch.zeros(npx, dtype=torch.int32, device=device)
     return fb
 
 

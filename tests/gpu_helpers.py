@@ -45,9 +45,14 @@ class Renderer:
             self.size = (width, height)
             pcr.pcr_set_framebuffer(self.h, self.fb["keys"], self.fb["hq_depth"], self.fb["hq_rg"], self.fb["hq_ba"])
             pcr.pcr_set_hq1r_buffer(self.h, self.fb["hq1r_primary"])
+            pcr.pcr_set_lock_buffer(self.h, self.fb["locks"], 0)
 
     def render_basic(self, variant: int, clear: bool = True) -> np.ndarray:
         pcr.pcr_render_basic(self.h, variant, clear)
+        return self.keys()
+
+    def render_rgb(self, variant: int, clear: bool = True) -> np.ndarray:
+        pcr.pcr_render_rgb(self.h, variant, clear)
         return self.keys()
 
     def keys(self) -> np.ndarray:

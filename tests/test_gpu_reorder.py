@@ -11,7 +11,8 @@ from paper_2104_07526_gb300 import pcr, scenes
 
 pytestmark = pytest.mark.gpu
 
-MODES = (pcr.PCR_ORDER_MORTON, pcr.PCR_ORDER_MORTON_SHUFFLE128, pcr.PCR_ORDER_SHUFFLE)
+MODES = (pcr.PCR_ORDER_MORTON, pcr.PCR_ORDER_MORTON_SHUFFLE128, pcr.PCR_ORDER_SHUFFLE, pcr.PCR_ORDER_MORTON63,
+         pcr.PCR_ORDER_MORTON63_SHUFFLE128)
 
 
 @pytest.fixture(scope="module")
@@ -102,7 +103,7 @@ def test_reorder_errors(r):
     assert e.value.status == pcr.PCR_ERR_WORKSPACE
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     with pytest.raises(pcr.PcrError) as e:
-        pcr.pcr_reorder_morton_shuffle128(r.h, dev, n, 0, 3, ws)
+        pcr.pcr_reorder_morton_shuffle128(r.h, dev, n, 0, 5, ws)
     assert e.value.status == pcr.PCR_ERR_ARG
     with pytest.raises(pcr.PcrError) as e:
         pcr.pcr_reorder_morton_shuffle128(r.h, dev.data_ptr() + 4, n, 0, 0, ws)
