@@ -41,9 +41,17 @@ constexpr int kUnroll = PCR_GEOMETRY_UNROLL;
 constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
 // Each chunk runs in three phases so independent memory round trips overlap:
 // project all U points, issue all U early reads, then test and write.
-// P selects the key payload: the point index, or the 24-bit colour.
+// P selects the key payload: the point index, or the 24-bit colour.  The
+// kernels are held to 48 registers (5 resident blocks of 256 threads per SM):
+// the frame is latency-bound, and one resident block fewer costs more than
+// the few instructions the register cap adds.
+template <int V, int P>
+constexpr int render_min_blocks() {
+  return kMinBlocks < 5 ? 5 : kMinBlocks;
+}
+
 template <int V, int U, int P>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, render_min_blocks<V, P>()) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                            unsigned long long* __restrict__ fb) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();

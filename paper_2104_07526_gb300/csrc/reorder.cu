@@ -9,9 +9,14 @@
 //   1. k_sort_hist: per tile of 8192 keys, count each digit.
 //   2. exclusive scan of the counts in digit-major order, which gives every
 //      (digit, tile) its first output slot;
-//   3. k_sort_scatter: per tile, rank each key among the earlier keys of its
-//      tile with the same digit (rounds of 256 keys in index order; inside a
-//      warp by match/popc, across warps by a shared prefix) and write it.
+//   3. k_sort_scatter: each warp of a tile takes 1024 consecutive keys and
+//      counts their digits (per 32 keys, one match.any when their digits
+//      form few runs, else eight ballots, one per digit bit);
+//      one prefix over (digit, warp) then gives every warp its first slot
+//      per digit, and the warp ranks its keys again in index order into the
+//      tile's digit-sorted order in shared memory.  The tile is then written
+//      out run by run, so each digit's keys leave as one contiguous,
+//      coalesced run.
 // Ranks follow index order, so each pass, and the sort, is stable.
 #include <cstdint>
 #include <mutex>
@@ -242,74 +247,162 @@ __global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t se
 
 // --- radix sort ---------------------------------------------------------------
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
-                                                            uint32_t* __restrict__ counts, uint32_t tiles) {
-  __shared__ uint32_t hist[kRadix];
-  hist[threadIdx.x] = 0;
-  __syncthreads();
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile + threadIdx.x;
-  const uint32_t lane = lane_id();
-#pragma unroll 4
-  for (int r = 0; r < kSortRounds; ++r) {
-    const uint64_t i = base + static_cast<uint64_t>(r) * kSortThreads;
-    const bool ok = i < n;
-    const uint32_t d = ok ? (keys[i] >> shift) & (kRadix - 1) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(kFullMask, d);
-    if (ok && lane == static_cast<uint32_t>(__ffs(peers) - 1)) atomicAdd(&hist[d], __popc(peers));
+// Lanes of the warp whose 8-bit digit equals this lane's, among the lanes
+// in `valid`.  When the warp's digits form few runs (coherent keys: a
+// Morton order's high digits), one match.any finds them cheaply; otherwise
+// one ballot per digit bit does, at a cost that does not depend on how many
+// distinct digits the warp holds (match.any grows with that number).
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid) {
+  const uint32_t prev = __shfl_up_sync(kFullMask, d, 1);
+  const uint32_t runs = __popc(__ballot_sync(kFullMask, lane_id() == 0 || prev != d));
+  if (runs <= 6) return __match_any_sync(kFullMask, d) & valid;
+  uint32_t peers = valid;
+#pragma unroll
+  for (int b = 0; b < kDigitBits; ++b) {
+    const uint32_t bit = (d >> b) & 1u;
+    const uint32_t set = __ballot_sync(kFullMask, bit);
+    peers &= bit ? set : ~set;
   }
-  __syncthreads();
-  counts[static_cast<uint64_t>(threadIdx.x) * tiles + blockIdx.x] = hist[threadIdx.x];
+  return peers;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint32_t* __restrict__ kin,
-                                                               const uint32_t* __restrict__ vin,
-                                                               uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                               uint32_t n, int shift,
-                                                               const uint32_t* __restrict__ offsets, uint32_t tiles) {
-  __shared__ uint32_t next[kRadix];                      // next free output slot per digit
-  __shared__ uint32_t slot[2][kSortWarps][kRadix];       // per-warp digit counts, then offsets
+// Per tile, the count of each digit.  Each warp counts into its own 256
+// counters with shared-memory atomics (one per key: no ranking is needed to
+// count), and the eight warps' counters are summed at the end.
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
+                                                            uint32_t* __restrict__ counts, uint32_t tiles) {
+  __shared__ uint32_t hist[kSortWarps][kRadix];
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) hist[w][threadIdx.x] = 0;
+  __syncthreads();
+  uint32_t* mine = hist[threadIdx.x >> 5];
+  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile + threadIdx.x;
+#pragma unroll 8
+  for (int r = 0; r < kSortRounds; ++r) {
+    const uint64_t i = base + static_cast<uint64_t>(r) * kSortThreads;
+    if (i < n) atomicAdd(&mine[(__ldcs(keys + i) >> shift) & (kRadix - 1)], 1u);
+  }
+  __syncthreads();
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) c += hist[w][threadIdx.x];
+  counts[static_cast<uint64_t>(threadIdx.x) * tiles + blockIdx.x] = c;
+}
+
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total);
+
+constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 1024 = kSortRounds x 32
+
+// Dynamic shared memory of k_sort_scatter: the tile's values as loaded, its
+// keys in digit-sorted order with their input slots, the per-warp first slot
+// of each digit, and per-digit starts (tile-local and global).
+constexpr size_t kScatterSmem = 2 * sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile +
+                                sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
+
+// 16-byte asynchronous copy global -> shared (cp.async, completes on
+// cp.async.wait_all); `bytes` < 16 reads only that many and zero-fills.
+__device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_src, uint32_t bytes) {
+  const uint32_t dst = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gmem_src), "r"(bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort_scatter(const uint32_t* __restrict__ kin,
+                                                                  const uint32_t* __restrict__ vin,
+                                                                  uint32_t* __restrict__ kout,
+                                                                  uint32_t* __restrict__ vout, uint32_t n, int shift,
+                                                                  const uint32_t* __restrict__ offsets,
+                                                                  uint32_t tiles) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* s_vin = smem;                                           // [kTile] the tile's values
+  uint32_t* s_keys = s_vin + kTile;                                 // [kTile]
+  uint32_t* wbase = s_keys + kTile;                                 // [kSortWarps][kRadix]
+  uint32_t* local_start = wbase + kSortWarps * kRadix;              // [kRadix]
+  uint32_t* global_start = local_start + kRadix;                    // [kRadix]
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(global_start + kRadix);  // [kTile]
   const uint32_t t = threadIdx.x;
   const uint32_t lane = lane_id();
   const uint32_t warp = t >> 5;
-  next[t] = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
+  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
+  // the tile's values go straight to shared memory while the keys are ranked
+  {
+    const uint64_t valid = n - tile_base < kTile ? n - tile_base : kTile;
+    for (uint32_t c = t; c * 4 < valid; c += kSortThreads) {
+      const uint64_t left = valid - 4ull * c;
+      copy16_async(s_vin + 4 * c, vin + tile_base + 4ull * c, left >= 4 ? 16u : static_cast<uint32_t>(4 * left));
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
 #pragma unroll
-  for (int w = 0; w < kSortWarps; ++w) {
-    slot[0][w][t] = 0;
-    slot[1][w][t] = 0;
+  for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] = 0;
+  global_start[t] = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
+  // this warp's 1024 keys, loaded up front (32 per lane)
+  const uint64_t wfirst = tile_base + warp * kKeysPerWarp;
+  uint32_t rk[kSortRounds];
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const uint64_t i = wfirst + static_cast<uint64_t>(r) * 32 + lane;
+    rk[r] = i < n ? __ldcs(kin + i) : 0u;
   }
   __syncthreads();
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile + t;
+  uint32_t* mine = wbase + warp * kRadix;
+  // pass 1: this warp's digit counts; each key keeps its rank among the
+  // round's lanes with its digit, that group's size and the digit
+  // (rank | size << 8 | digit << 16, bit 31 set for a key inside the cloud)
   const uint32_t below = (1u << lane) - 1u;
-  for (int r = 0; r < kSortRounds; ++r) {
-    const int p = r & 1;
-    const uint64_t i = base + static_cast<uint64_t>(r) * kSortThreads;
-    const bool ok = i < n;
-    uint32_t key = 0, val = 0, d = 0xFFFFFFFFu;
-    if (ok) {
-      key = kin[i];
-      val = vin[i];
-      d = (key >> shift) & (kRadix - 1);
-    }
-    const uint32_t peers = __match_any_sync(kFullMask, d);
-    const uint32_t rank = __popc(peers & below);
-    if (ok && rank == 0) slot[p][warp][d] = __popc(peers);
-    __syncthreads();
-    // digit t: turn this round's per-warp counts into output slots
-    uint32_t run = next[t];
+  uint32_t info[kSortRounds];
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = slot[p][w][t];
-      slot[p][w][t] = run;
-      run += c;
-      slot[p ^ 1][w][t] = 0;
-    }
-    next[t] = run;
-    __syncthreads();
+  for (int r = 0; r < kSortRounds; ++r) {
+    const bool ok = wfirst + static_cast<uint64_t>(r) * 32 + lane < n;
+    const uint32_t d = (rk[r] >> shift) & (kRadix - 1);
+    const uint32_t peers = digit_peers(d, __ballot_sync(kFullMask, ok));
+    const uint32_t rank = __popc(peers & below);
+    info[r] = ok ? (rank | (static_cast<uint32_t>(__popc(peers)) << 8) | (d << 16) | 0x80000000u) : 0u;
+    if (ok && rank == 0) mine[d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // digit t: first slot of each warp's keys within the digit, then the
+  // digit's first slot within the tile
+  uint32_t run = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) {
+    const uint32_t c = wbase[w * kRadix + t];
+    wbase[w * kRadix + t] = run;
+    run += c;
+  }
+  uint32_t total;
+  const uint32_t start = block_exclusive_scan<kSortThreads>(run, total);
+  local_start[t] = start;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] += start;
+  __syncthreads();
+  // pass 2: place each key, in index order
+#pragma unroll
+  for (int r = 0; r < kSortRounds; ++r) {
+    const uint32_t v = info[r];
+    const bool ok = (v >> 31) != 0u;
+    const uint32_t d = (v >> 16) & (kRadix - 1);
+    const uint32_t rank = v & 0xFFu;
+    const uint32_t at = ok ? mine[d] : 0u;
+    __syncwarp();
     if (ok) {
-      const uint32_t pos = slot[p][warp][d] + rank;
-      kout[pos] = key;
-      vout[pos] = val;
+      s_keys[at + rank] = rk[r];
+      s_src[at + rank] = static_cast<uint16_t>(warp * kKeysPerWarp + r * 32 + lane);
+      if (rank == 0) mine[d] = at + ((v >> 8) & 0xFFu);
     }
+    __syncwarp();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  // the tile in digit order: consecutive slots of a digit go to consecutive
+  // output positions
+  for (uint32_t l = t; l < total; l += kSortThreads) {
+    const uint32_t key = s_keys[l];
+    const uint32_t d = (key >> shift) & (kRadix - 1);
+    const uint32_t g = global_start[d] + (l - local_start[d]);
+    kout[g] = key;
+    vout[g] = s_vin[s_src[l]];
   }
 }
 
@@ -428,12 +521,15 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
   out = 0;
   if (count == 0) return cudaSuccess;
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
+  cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(kScatterSmem));
+  if (e != cudaSuccess) return e;
   for (int shift = 0; shift < key_bits; shift += kDigitBits) {
     k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
-    cudaError_t e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
+    e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
-    k_sort_scatter<<<tiles, kSortThreads, 0, s>>>(keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count, shift,
-                                                  counts, tiles);
+    k_sort_scatter<<<tiles, kSortThreads, kScatterSmem, s>>>(keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count,
+                                                             shift, counts, tiles);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     out ^= 1;
