@@ -294,11 +294,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
 
 constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 1024 = kSortRounds x 32
 
-// Dynamic shared memory of k_sort_scatter: the tile's values as loaded, its
-// keys in digit-sorted order with their input slots, the per-warp first slot
-// of each digit, and per-digit starts (tile-local and global).
-constexpr size_t kScatterSmem = 2 * sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile +
-                                sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
+// Dynamic shared memory of k_sort_scatter: the tile's keys as loaded, each
+// output slot's input slot, the per-warp first slot of each digit, and
+// per-digit starts (tile-local and global).  58 KB: three blocks per SM.
+constexpr size_t kScatterSmem =
+    sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile + sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
 
 // 16-byte asynchronous copy global -> shared (cp.async, completes on
 // cp.async.wait_all); `bytes` < 16 reads only that many and zero-fills.
@@ -307,16 +307,15 @@ __device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_sr
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gmem_src), "r"(bytes) : "memory");
 }
 
-__global__ void __launch_bounds__(kSortThreads, 2) k_sort_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
                                                                   uint32_t* __restrict__ kout,
                                                                   uint32_t* __restrict__ vout, uint32_t n, int shift,
                                                                   const uint32_t* __restrict__ offsets,
                                                                   uint32_t tiles) {
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* s_vin = smem;                                           // [kTile] the tile's values
-  uint32_t* s_keys = s_vin + kTile;                                 // [kTile]
-  uint32_t* wbase = s_keys + kTile;                                 // [kSortWarps][kRadix]
+  uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
+  uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
   uint32_t* local_start = wbase + kSortWarps * kRadix;              // [kRadix]
   uint32_t* global_start = local_start + kRadix;                    // [kRadix]
   uint16_t* s_src = reinterpret_cast<uint16_t*>(global_start + kRadix);  // [kTile]
@@ -324,37 +323,30 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_scatter(const uint32_t
   const uint32_t lane = lane_id();
   const uint32_t warp = t >> 5;
   const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
-  // the tile's values go straight to shared memory while the keys are ranked
-  {
-    const uint64_t valid = n - tile_base < kTile ? n - tile_base : kTile;
-    for (uint32_t c = t; c * 4 < valid; c += kSortThreads) {
-      const uint64_t left = valid - 4ull * c;
-      copy16_async(s_vin + 4 * c, vin + tile_base + 4ull * c, left >= 4 ? 16u : static_cast<uint32_t>(4 * left));
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+  const uint32_t valid = static_cast<uint32_t>(n - tile_base < kTile ? n - tile_base : kTile);
+  for (uint32_t c = t; c * 4 < valid; c += kSortThreads) {
+    const uint32_t left = valid - 4 * c;
+    copy16_async(s_kin + 4 * c, kin + tile_base + 4ull * c, left >= 4 ? 16u : 4 * left);
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] = 0;
   global_start[t] = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
-  // this warp's 1024 keys, loaded up front (32 per lane)
-  const uint64_t wfirst = tile_base + warp * kKeysPerWarp;
-  uint32_t rk[kSortRounds];
-#pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const uint64_t i = wfirst + static_cast<uint64_t>(r) * 32 + lane;
-    rk[r] = i < n ? __ldcs(kin + i) : 0u;
-  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
+  // this warp's 1024 consecutive keys; pass 1 counts their digits, and each
+  // key keeps its rank among the round's lanes with its digit, that group's
+  // size and the digit (rank | size << 8 | digit << 16, bit 31 set for a key
+  // inside the cloud)
+  const uint32_t wfirst = warp * kKeysPerWarp;
   uint32_t* mine = wbase + warp * kRadix;
-  // pass 1: this warp's digit counts; each key keeps its rank among the
-  // round's lanes with its digit, that group's size and the digit
-  // (rank | size << 8 | digit << 16, bit 31 set for a key inside the cloud)
   const uint32_t below = (1u << lane) - 1u;
   uint32_t info[kSortRounds];
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
-    const bool ok = wfirst + static_cast<uint64_t>(r) * 32 + lane < n;
-    const uint32_t d = (rk[r] >> shift) & (kRadix - 1);
+    const uint32_t j = wfirst + r * 32 + lane;
+    const bool ok = j < valid;
+    const uint32_t d = ok ? (s_kin[j] >> shift) & (kRadix - 1) : 0u;
     const uint32_t peers = digit_peers(d, __ballot_sync(kFullMask, ok));
     const uint32_t rank = __popc(peers & below);
     info[r] = ok ? (rank | (static_cast<uint32_t>(__popc(peers)) << 8) | (d << 16) | 0x80000000u) : 0u;
@@ -377,7 +369,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_scatter(const uint32_t
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] += start;
   __syncthreads();
-  // pass 2: place each key, in index order
+  // pass 2: each key's slot in the tile's digit order, in index order
 #pragma unroll
   for (int r = 0; r < kSortRounds; ++r) {
     const uint32_t v = info[r];
@@ -387,22 +379,22 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_scatter(const uint32_t
     const uint32_t at = ok ? mine[d] : 0u;
     __syncwarp();
     if (ok) {
-      s_keys[at + rank] = rk[r];
-      s_src[at + rank] = static_cast<uint16_t>(warp * kKeysPerWarp + r * 32 + lane);
+      s_src[at + rank] = static_cast<uint16_t>(wfirst + r * 32 + lane);
       if (rank == 0) mine[d] = at + ((v >> 8) & 0xFFu);
     }
     __syncwarp();
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
-  // output positions
+  // output positions; values are gathered from the tile's 32 KB window
+#pragma unroll 8
   for (uint32_t l = t; l < total; l += kSortThreads) {
-    const uint32_t key = s_keys[l];
+    const uint32_t src = s_src[l];
+    const uint32_t key = s_kin[src];
     const uint32_t d = (key >> shift) & (kRadix - 1);
     const uint32_t g = global_start[d] + (l - local_start[d]);
     kout[g] = key;
-    vout[g] = s_vin[s_src[l]];
+    vout[g] = __ldg(vin + tile_base + src);
   }
 }
 
