@@ -581,14 +581,17 @@ def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, step
     torch.cuda.synchronize()
     barrier(dist)
     t0 = time.perf_counter()
+    marks = []
     for _ in range(steps):
-        step()
+        step()  # ends in a synchronous download of the image
+        marks.append(time.perf_counter())
     torch.cuda.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
     del host
+    per = [(b - a) * 1e3 for a, b in zip([t0] + marks[:-1], marks)]
     return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
             "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
-            "ms_per_step": dt / steps * 1e3}
+            "ms_per_step": dt / steps * 1e3, "step_ms_min": min(per), "step_ms_median": statistics.median(per)}
 
 
 def run_batched(h, pcr, stream, dev, reps: int) -> dict:
