@@ -255,37 +255,61 @@ def describe_sample(n: int, sample: int) -> str:
     return f"every {stride}th point of the {n}-point cloud ({sample} points)"
 
 
-def time_oracle(pts_np: np.ndarray, view, repeats: int = 1) -> float:
-    """Seconds per oracle frame (render + resolve) on this sample."""
+def time_oracle(pts_np: np.ndarray, view, repeats: int = 1, threads: int = 1) -> float:
+    """Seconds per oracle frame (render + resolve) on this sample: the
+    single-threaded functions for threads == 1, else their host-parallel
+    forms on `threads` threads (0 = every host core)."""
     from oracle import pyoracle
     best = None
     for _ in range(repeats):
         t0 = time.perf_counter()
-        keys = pyoracle.render_basic(pts_np, view.matrix, view.width, view.height)
-        pyoracle.resolve_basic(keys, pts_np, 0)
+        if threads == 1:
+            keys = pyoracle.render_basic(pts_np, view.matrix, view.width, view.height)
+            pyoracle.resolve_basic(keys, pts_np, 0)
+        else:
+            keys, _ = pyoracle.render_basic_threads(pts_np, view.matrix, view.width, view.height, threads)
+            pyoracle.resolve_basic_threads(keys, pts_np, 0, threads)
         dt = time.perf_counter() - t0
         best = dt if best is None else min(best, dt)
     return best
 
 
+def oracle_threads() -> int:
+    """Host threads the parallel oracle uses."""
+    from oracle import pyoracle
+    _, used = pyoracle.render_basic_threads(np.zeros((0, 4), np.int32), np.eye(4, dtype=np.float32), 1, 1, 0)
+    return used
+
+
 def oracle_baseline(cloud_host_fn, n: int, view, target_s: float) -> dict:
-    """Time the CPU oracle (single thread, as it stands) on a strided sample
-    of the same cloud sized to about target_s seconds of work."""
-    pilot_n = min(n, 4_000_000)
-    pilot = cloud_host_fn(pilot_n)
-    t = time_oracle(pilot, view, repeats=2)  # the first pass pays for page faults
-    rate = pilot_n / max(t, 1e-6)
-    sample = int(min(n, max(pilot_n, rate * target_s)))
-    pts = cloud_host_fn(sample)
-    # whole frames until the target time is spent (the sample is capped at the
-    # cloud, which a fast host renders in less than the target)
-    frames, total = 0, 0.0
-    while total < target_s and frames < 10:
-        total += time_oracle(pts, view)
-        frames += 1
-    which = describe_sample(n, sample)
-    return {"value": sample * frames / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{which}, {frames} frame(s) (render + resolve), single-threaded C oracle, {total:.2f} s"}
+    """Time the CPU oracle as it stands on the host cores: its host-parallel
+    render and resolve on every core, on a sample of the same cloud sized to
+    about target_s seconds of work, plus the single-threaded functions on
+    the same sample for about a third of that."""
+
+    def timed(threads: int, seconds: float):
+        pilot_n = min(n, 4_000_000)
+        pilot = cloud_host_fn(pilot_n)
+        t = time_oracle(pilot, view, repeats=2, threads=threads)  # the first pass pays for page faults
+        rate = pilot_n / max(t, 1e-6)
+        sample = int(min(n, max(pilot_n, rate * seconds)))
+        pts = cloud_host_fn(sample)
+        # whole frames until the time is spent (the sample is capped at the
+        # cloud, which a fast host renders in less than the target)
+        frames, total = 0, 0.0
+        while total < seconds and frames < 10:
+            total += time_oracle(pts, view, threads=threads)
+            frames += 1
+        return sample * frames / total, sample, frames, total
+
+    cores = oracle_threads()
+    value, sample, frames, total = timed(0, target_s)
+    one, one_sample, one_frames, one_total = timed(1, target_s / 3)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{describe_sample(n, sample)}, {frames} frame(s) (render + resolve), C oracle on "
+                      f"{cores} threads, {total:.2f} s",
+            "single_thread": {"value": one, "unit": UNIT, "cores": 1,
+                              "sample": f"{describe_sample(n, one_sample)}, {one_frames} frame(s), {one_total:.2f} s"}}
 
 
 # ---------------------------------------------------------------------------
@@ -321,13 +345,13 @@ def run_reference(args, cfg):
     budget = 120.0
     pilot_n = min(n, 1_000_000)
     pilot = host_sample(pilot_n)
-    rate = pilot_n / max(time_oracle(pilot, view), 1e-6)
+    rate = pilot_n / max(time_oracle(pilot, view, threads=0), 1e-6)
     per_step = budget / max(1, args.steps + args.warmup)
     sample = int(min(n, max(100_000, rate * per_step)))
     pts = host_sample(sample)
     for _ in range(args.warmup):
-        time_oracle(pts, view)
-    times = [time_oracle(pts, view) for _ in range(args.steps)]
+        time_oracle(pts, view, threads=0)
+    times = [time_oracle(pts, view, threads=0) for _ in range(args.steps)]
     step_s = sum(times) / len(times)
     value = sample / step_s
     line = {
@@ -335,9 +359,9 @@ def run_reference(args, cfg):
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/u64", "data": "synthetic",
         "config": workload_config(cfg, view),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                          "sample": f"per step {describe_sample(n, sample)}, put in shuffled-Morton order, "
-                                   f"render + resolve, single-threaded C oracle"},
+                                   f"render + resolve, C oracle on every host core"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

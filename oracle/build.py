@@ -25,10 +25,13 @@ def stale() -> bool:
 
 
 def build(force: bool = False) -> str:
+    """Builds with OpenMP (the *_threads functions then use several host
+    threads); without it if the compiler lacks OpenMP."""
     if force or stale():
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", *CFLAGS, "-o", tmp, *SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        cmd = ["gcc", *CFLAGS, "-fopenmp", "-o", tmp, *SRC, "-lm"]
+        if subprocess.run(cmd, capture_output=True).returncode != 0:
+            subprocess.run(["gcc", *CFLAGS, "-o", tmp, *SRC, "-lm"], check=True)
         os.replace(tmp, LIB)
     return LIB
 

@@ -19,6 +19,8 @@
  *                        outside the 1% band; hand-worked averages
  *                        (tests/golden/hq_cases.txt).
  *   oracle_resolve_*     hand-worked cases.
+ *   oracle_*_threads     equal to the single-threaded functions on scenes
+ *                        with heavy per-pixel contention.
  *   oracle_*_rgb         constructed scenes (colour of the nearest point);
  *                        hand-worked depth ties broken by colour
  *                        (tests/golden/rgb_key_cases.txt); agreement with
@@ -40,6 +42,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static float bits_to_float(uint32_t u) {
     float f;
@@ -210,6 +215,52 @@ void oracle_resolve_rgb(const uint64_t *keys, size_t npx, uint32_t background, u
         else
             out[p] = (uint32_t)(keys[p] & 0xFFFFFFu) | (0xFFu << 24);
     }
+}
+
+static int thread_count(int threads) {
+#ifdef _OPENMP
+    return threads > 0 ? threads : omp_get_max_threads();
+#else
+    (void)threads;
+    return 1;
+#endif
+}
+
+/* Sec. 3.1 on several threads: the same per-point minimum as
+ * oracle_render_basic, each update a compare-and-swap loop that retries
+ * while the point's key is still smaller than the pixel's. */
+int oracle_render_basic_threads(const oracle_point *pts, uint64_t n, const float m[16], int width, int height,
+                                uint64_t *keys, int threads) {
+    int used = thread_count(threads);
+    int64_t count = (int64_t)n;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(used) schedule(static)
+#endif
+    for (int64_t i = 0; i < count; ++i) {
+        uint32_t p;
+        float w;
+        if (!oracle_project(m, width, height, pts[i].x, pts[i].y, pts[i].z, &p, &w)) continue;
+        uint64_t k = oracle_key(w, (uint32_t)i);
+        uint64_t cur = __atomic_load_n(&keys[p], __ATOMIC_RELAXED);
+        while (k < cur && !__atomic_compare_exchange_n(&keys[p], &cur, k, 1, __ATOMIC_RELAXED, __ATOMIC_RELAXED)) {
+        }
+    }
+    return used;
+}
+
+int oracle_resolve_basic_threads(const uint64_t *keys, size_t npx, const oracle_point *pts, uint64_t n,
+                                 uint32_t background, uint32_t *out, int threads) {
+    int used = thread_count(threads);
+    int64_t count = (int64_t)npx;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(used) schedule(static)
+#endif
+    for (int64_t p = 0; p < count; ++p) {
+        uint64_t k = keys[p];
+        uint64_t idx = k & 0xFFFFFFFFu;
+        out[p] = (k == UINT64_MAX || idx >= n) ? background : pts[idx].rgba;
+    }
+    return used;
 }
 
 /* Sec. 3.5, Listing "hqs_resolve": divide the colour sums by the count with

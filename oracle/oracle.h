@@ -83,6 +83,17 @@ void oracle_render_rgb(const oracle_point *pts, uint64_t n, const float m[16], i
  * ones, else the key's 24-bit colour with alpha 255. */
 void oracle_resolve_rgb(const uint64_t *keys, size_t npx, uint32_t background, uint32_t *out);
 
+/* oracle_render_basic and oracle_resolve_basic on `threads` host threads
+ * (every available one when threads <= 0; one when the oracle was built
+ * without OpenMP).  Each point takes its pixel's minimum with a
+ * compare-and-swap loop; a minimum does not depend on order, so the keys
+ * equal oracle_render_basic's.  Used to time the oracle on all host cores.
+ * Return the number of threads used. */
+int oracle_render_basic_threads(const oracle_point *pts, uint64_t n, const float m[16], int width, int height,
+                                uint64_t *keys, int threads);
+int oracle_resolve_basic_threads(const uint64_t *keys, size_t npx, const oracle_point *pts, uint64_t n,
+                                 uint32_t background, uint32_t *out, int threads);
+
 /* Sec. 3.5, resolve: truncating integer average per channel, alpha 255;
  * background where no point contributed. */
 void oracle_resolve_hq(const uint64_t *rg, const uint64_t *ba, size_t npx, uint32_t background,

@@ -41,6 +41,10 @@ def lib():
                                                  VOIDP, VOIDP]
             L.oracle_resolve_basic.argtypes = [VOIDP, C.c_size_t, VOIDP, U64, U32, VOIDP]
             L.oracle_resolve_hq.argtypes = [VOIDP, VOIDP, C.c_size_t, U32, VOIDP]
+            L.oracle_render_basic_threads.argtypes = [VOIDP, U64, VOIDP, INT, INT, VOIDP, INT]
+            L.oracle_render_basic_threads.restype = INT
+            L.oracle_resolve_basic_threads.argtypes = [VOIDP, C.c_size_t, VOIDP, U64, U32, VOIDP, INT]
+            L.oracle_resolve_basic_threads.restype = INT
             L.oracle_key_rgb.argtypes = [FLT, U32]
             L.oracle_key_rgb.restype = U64
             L.oracle_render_rgb.argtypes = [VOIDP, U64, VOIDP, INT, INT, VOIDP]
@@ -131,6 +135,23 @@ def resolve_rgb(keys: np.ndarray, background: int = 0) -> np.ndarray:
     out = np.empty(keys.size, dtype=np.uint32)
     lib().oracle_resolve_rgb(_ptr(keys), keys.size, background, _ptr(out))
     return out
+
+
+def render_basic_threads(pts: np.ndarray, m, width: int, height: int, threads: int = 0,
+                         keys: np.ndarray | None = None):
+    """render_basic on several host threads; returns (keys, threads used)."""
+    pts, n = _cloud(pts)
+    if keys is None:
+        keys = clear_keys(width * height)
+    used = lib().oracle_render_basic_threads(_ptr(pts), n, _ptr(_mat(m)), width, height, _ptr(keys), threads)
+    return keys, used
+
+
+def resolve_basic_threads(keys: np.ndarray, pts: np.ndarray, background: int = 0, threads: int = 0):
+    pts, n = _cloud(pts)
+    out = np.empty(keys.size, dtype=np.uint32)
+    used = lib().oracle_resolve_basic_threads(_ptr(keys), keys.size, _ptr(pts), n, background, _ptr(out), threads)
+    return out, used
 
 
 def clear_hq(npx: int):

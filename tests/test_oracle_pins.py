@@ -281,6 +281,28 @@ def test_rgb_agrees_with_index_payload(oracle):
         assert c_rgb[p] == (int(c_idx[p]) & 0xFFFFFF) | 0xFF000000
 
 
+# --- multi-threaded timing variant ------------------------------------------------
+
+@pytest.mark.parametrize("threads", [1, 3, 0])
+def test_threads_variant_equals_single_thread(oracle, threads):
+    """The host-parallel render and resolve (used only to time the oracle on
+    all host cores) give exactly the single-threaded results, also when all
+    points fight over one pixel."""
+    sphere = scenes.sphere_plane(60_000, seed=3).numpy()
+    n = 40_000
+    one_px = cs.pack(np.tile([[0.0, 0.0, 1.5]], (n, 1)), np.arange(n, dtype=np.uint32))
+    d = np.random.default_rng(4).integers(4, 4000, size=n) / 256.0
+    one_px_depths = cs.pack(np.stack([np.zeros(n), np.zeros(n), cs.EYE_Z - d], 1), np.arange(n, dtype=np.uint32))
+    for cloud in (sphere, one_px, one_px_depths):
+        m = cs.camera()
+        want = oracle.render_basic(cloud, m, cs.W, cs.H)
+        got, used = oracle.render_basic_threads(cloud, m, cs.W, cs.H, threads)
+        assert used >= 1
+        assert np.array_equal(got, want)
+        img, _ = oracle.resolve_basic_threads(got, cloud, 0x01020304, threads)
+        assert np.array_equal(img, oracle.resolve_basic(want, cloud, 0x01020304))
+
+
 # --- resolve -------------------------------------------------------------------
 
 def test_resolve_basic_cases(oracle):
