@@ -274,6 +274,31 @@ def time_oracle(pts_np: np.ndarray, view, repeats: int = 1, threads: int = 1) ->
     return best
 
 
+# Algorithmic DRAM bytes per point of each one-time reorder (Sec. 4, Sec. 5),
+# counted from what the kernels must read and write at least once:
+#   bounds 16 (read the records); 30-bit codes 16 read + 8 written (key,
+#   index); 63-bit codes 16 read + 12 written (low key, high word, index);
+#   each sort pass 4 (histogram read) + 8 read + 8 written (key, index);
+#   high-word gather 4 + 4 read + 4 written; random keys 8 written; batch
+#   sort and permutation about 1; record copy 16 + 16; record gather 4 (index)
+#   + 16 read + 16 written.
+REORDER_BYTES_PER_POINT = {
+    "morton": 16 + 24 + 4 * 20 + 32 + 36,
+    "morton_shuffle128": 16 + 24 + 4 * 20 + 1 + 32 + 36,
+    "shuffle": 8 + 4 * 20 + 32 + 36,
+    "morton63": 16 + 28 + 4 * 20 + 12 + 4 * 20 + 32 + 36,
+    "morton63_shuffle128": 16 + 28 + 4 * 20 + 12 + 4 * 20 + 1 + 32 + 36,
+}
+
+
+def reorder_roofline(reorder_ms: dict, n: int, peak: float) -> dict:
+    out = {}
+    for name, ms in reorder_ms.items():
+        gb = REORDER_BYTES_PER_POINT[name] * n / 1e9
+        out[name] = {"ms": ms, "algorithmic_gb": gb, "achieved_gbs": gb / (ms * 1e-3), "frac": gb / (ms * 1e-3) / peak}
+    return out
+
+
 def oracle_threads() -> int:
     """Host threads the parallel oracle uses."""
     from oracle import pyoracle
@@ -560,6 +585,11 @@ def run_ours(args, cfg):
             "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view),
             "frame_gbs": n * POINT_BYTES / (ms_per_step * 1e-3) / 1e9,
             "phases_ms": phase, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
+            "hq_roofline": None if hq_ms is None else {
+                "bound": "hbm", "algorithmic_bytes": 2 * n * POINT_BYTES,
+                "achieved_gbs": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9,
+                "frac": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9 / peak, "note": "two passes over the points"},
+            "reorder_roofline": reorder_roofline(reorder_ms, n, peak),
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
             "sweep_ms": sweep, "batched": batched, "served": served,
