@@ -45,13 +45,10 @@ constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
 // kernels are held to 48 registers (5 resident blocks of 256 threads per SM):
 // the frame is latency-bound, and one resident block fewer costs more than
 // the few instructions the register cap adds.
-template <int V, int P>
-constexpr int render_min_blocks() {
-  return kMinBlocks < 5 ? 5 : kMinBlocks;
-}
+constexpr int kRenderMinBlocks = kMinBlocks < 5 ? 5 : kMinBlocks;
 
 template <int V, int U, int P>
-__global__ void __launch_bounds__(kThreads, render_min_blocks<V, P>()) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, kRenderMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                            unsigned long long* __restrict__ fb) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();

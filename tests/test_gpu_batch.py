@@ -158,3 +158,27 @@ def test_batch_rejects_bad_descriptions(ctx):
     assert e.value.status == pcr.PCR_ERR_WORKSPACE
     with pytest.raises(pcr.PcrError):
         pcr.pcr_batch_launch(ctx, ws, pcr.pcr_batch_num_configs())
+
+
+def test_batch_table_limits(ctx, oracle):
+    """The largest batches the tables hold: one cloud seen by 256 views, and
+    256 clouds (some empty) with one view each; sizes, flags and cameras
+    vary from view to view."""
+    rng = np.random.default_rng(77)
+    one = [scenes.random_cloud(5003, seed=8).numpy()]
+    views = []
+    for i in range(pcr.PCR_BATCH_MAX_VIEWS):
+        W, H = int(rng.integers(1, 41)), int(rng.integers(1, 31))
+        a = rng.uniform(0, 2 * np.pi)
+        m = scenes.camera((3 * np.cos(a), 3 * np.sin(a), 1.0), (0, 0, 0), (0, 0, 1), W, H)
+        views.append((0, m, W, H, int(rng.choice([BASIC, HQ, BASIC | HQ]))))
+    many = [scenes.random_cloud(int(rng.integers(1, 300)), seed=100 + i).numpy() if i % 17 else
+            np.zeros((0, 4), np.int32) for i in range(pcr.PCR_BATCH_MAX_CLOUDS)]
+    views_many = [(i, views[i][1], views[i][2], views[i][3], views[i][4]) for i in range(pcr.PCR_BATCH_MAX_CLOUDS)]
+    for clouds, vs in ((one, views), (many, views_many)):
+        expected = _expected(oracle, clouds, vs)
+        dev, bufs, ws = _prepare(ctx, clouds, vs)
+        for config in range(pcr.pcr_batch_num_configs()):
+            _poison(bufs)
+            pcr.pcr_batch_launch(ctx, ws, config)
+            _check(bufs, expected, f"limits config {config}")

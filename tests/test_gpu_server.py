@@ -223,3 +223,32 @@ def test_submit_rejections(ctx):
         with pytest.raises(pcr.PcrError) as e:
             pcr.pcr_server_create(ctx, arena, 32, 32, 2, **kw)
         assert e.value.status == pcr.PCR_ERR_ARG
+
+
+def test_full_batches_of_small_requests(ctx, oracle):
+    """Many small requests, batches of up to 256 views over three clouds; every
+    result exact."""
+    clouds = [scenes.random_cloud(3001 + 1000 * i, seed=60 + i).numpy() for i in range(3)]
+    arena = torch.empty(128 << 20, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, 24, 16, num_slots=300, max_batch_views=pcr.PCR_BATCH_MAX_VIEWS,
+                                max_inflight=2, background_rgba=BG)
+    try:
+        for i, c in enumerate(clouds):
+            pcr.pcr_server_add_cloud(srv, i, np.ascontiguousarray(c))
+        rng = np.random.default_rng(61)
+        reqs = []
+        for _ in range(300):
+            c = int(rng.integers(0, 3))
+            W, H = int(rng.integers(1, 25)), int(rng.integers(1, 17))
+            a = rng.uniform(0, 2 * np.pi)
+            m = scenes.camera((3 * np.cos(a), 3 * np.sin(a), 1.0), (0, 0, 0), (0, 0, 1), W, H)
+            reqs.append((c, m, W, H, int(rng.choice([BASIC, HQ, BASIC | HQ]))))
+        tickets = [pcr.pcr_server_submit(srv, *r) for r in reqs]
+        _drain(srv, tickets)
+        for t, (c, m, W, H, flags) in zip(tickets, reqs):
+            _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+            pcr.pcr_server_release(srv, t)
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["completed"] == 300 and st["batches"] <= 20
+    finally:
+        pcr.pcr_server_destroy(srv)
