@@ -188,11 +188,12 @@ __global__ void __launch_bounds__(kThreads) k_batch_phase2(const Tables* __restr
       uint32_t d[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(bv.depth + pix[u]) : 0u;
+      bool contrib[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const bool contrib = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
-        emit_color<true>(bv.rg, bv.ba, contrib, pix[u], r[u].w, pol_fb);
-      }
+      for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
+      const bool agg = aggregate_chunk(contrib[0], pix[0]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) emit_color(bv.rg, bv.ba, contrib[u], pix[u], r[u].w, pol_fb, agg);
     }
   });
 }

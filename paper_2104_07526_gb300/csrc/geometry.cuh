@@ -212,36 +212,38 @@ __device__ __forceinline__ void emit_depth(uint32_t* __restrict__ depth, bool vi
   }
 }
 
-// Colour pass (Listing "hqs_render"): a visible point contributes when
-// w <= depth * factor.  With AGG, lanes that contribute to the same pixel
-// first sum their colours inside the warp (at most 32 * 255 per channel,
-// so r | g << 16 and b | count << 16 cannot carry), then one lane adds.
-template <bool AGG>
+// Colour pass (Listing "hqs_render"): whether the warp sums its colours
+// before adding, decided once per chunk from its first row of points: the
+// runs of equal pixels among neighbouring contributing lanes.  With at most
+// kAggregateMaxRuns runs (coherent orders: neighbours share pixels) the warp
+// aggregates; otherwise (shuffled orders) matching would cost more than it
+// saves.  The rows of a chunk are 32 points apart in the same order, so the
+// first row speaks for the others.  Warp-uniform.
+__device__ __forceinline__ bool aggregate_chunk(bool contrib0, uint32_t pix0) {
+  const uint32_t tag = contrib0 ? pix0 : kNoPixel;
+  const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
+  const uint32_t starts = __ballot_sync(kFullMask, contrib0 && (lane_id() == 0 || prev != tag));
+  return __popc(starts) <= kAggregateMaxRuns;
+}
+
+// A visible point contributes when w <= depth * factor, adding (r << 32 | g)
+// and (b << 32 | 1).  With `agg` (warp-uniform), lanes that contribute to
+// the same pixel first sum their colours inside the warp (at most 32 * 255
+// per channel, so r | g << 16 and b | count << 16 cannot carry), then one
+// lane adds.
 __device__ __forceinline__ void emit_color(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
-                                           bool contrib, uint32_t pix, uint32_t rgba, uint64_t pol) {
+                                           bool contrib, uint32_t pix, uint32_t rgba, uint64_t pol, bool agg) {
   const uint32_t cr = rgba & 0xFFu;
   const uint32_t cg = (rgba >> 8) & 0xFFu;
   const uint32_t cb = (rgba >> 16) & 0xFFu;
-  if constexpr (!AGG) {
+  if (!agg) {
     if (contrib) {
       red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
       red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
     }
   } else {
-    // Aggregate only when the contributing lanes share pixels: count the
-    // runs of equal pixels among neighbouring lanes (cheap), and fall back
-    // to plain adds when the warp's pixels are mostly distinct (shuffled
-    // orders), where matching would cost more than it saves.
-    const uint32_t tag = contrib ? pix : kNoPixel;
     const uint32_t active = __ballot_sync(kFullMask, contrib);
-    const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
-    const uint32_t starts = __ballot_sync(kFullMask, contrib && (lane_id() == 0 || prev != tag));
-    if (__popc(starts) > kAggregateMaxRuns) {
-      if (contrib) {
-        red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
-        red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
-      }
-    } else if (contrib) {
+    if (contrib) {
       const uint32_t peers = __match_any_sync(active, pix);
       const uint32_t s_rg = __reduce_add_sync(peers, cr | (cg << 16));
       const uint32_t s_bc = __reduce_add_sync(peers, cb | (1u << 16));

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_depth(const uint4* 
   });
 }
 
-// Colour pass (Listing "hqs_render"): see emit_color.
+// Colour pass (Listing "hqs_render"): see aggregate_chunk and emit_color.
 template <bool AGG, int U>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        float factor, const uint32_t* __restrict__ depth,
@@ -205,11 +205,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_color(const uint4* 
     uint32_t d[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(depth + pix[u]) : 0u;
+    bool contrib[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool contrib = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
-      emit_color<AGG>(rg, ba, contrib, pix[u], r[u].w, pol_fb);
-    }
+    for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
+    const bool agg = AGG && aggregate_chunk(contrib[0], pix[0]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) emit_color(rg, ba, contrib[u], pix[u], r[u].w, pol_fb, agg);
   });
 }
 
@@ -256,20 +257,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks)
     for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(depth + pix[u]) : 0u;
     bool mine[U];
     uint32_t sr[U], sg[U], sb[U], k[U];
+    bool contrib[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
+    const bool agg = AGG && aggregate_chunk(contrib[0], pix[0]);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const bool contrib = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
       sr[u] = r[u].w & 0xFFu;
       sg[u] = (r[u].w >> 8) & 0xFFu;
       sb[u] = (r[u].w >> 16) & 0xFFu;
       k[u] = 1;
-      mine[u] = contrib;
-      if constexpr (AGG) {
-        const uint32_t tag = contrib ? pix[u] : kNoPixel;
-        const uint32_t active = __ballot_sync(kFullMask, contrib);
-        const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
-        const uint32_t starts = __ballot_sync(kFullMask, contrib && (lane_id() == 0 || prev != tag));
-        if (__popc(starts) <= kAggregateMaxRuns && contrib) {
+      mine[u] = contrib[u];
+      if (agg) {
+        const uint32_t active = __ballot_sync(kFullMask, contrib[u]);
+        if (contrib[u]) {
           const uint32_t peers = __match_any_sync(active, pix[u]);
           const uint32_t s_rg = __reduce_add_sync(peers, sr[u] | (sg[u] << 16));
           const uint32_t s_bc = __reduce_add_sync(peers, sb[u] | (1u << 16));
