@@ -233,25 +233,22 @@ __device__ __forceinline__ bool aggregate_chunk(bool contrib0, uint32_t pix0) {
 // lane adds.
 __device__ __forceinline__ void emit_color(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
                                            bool contrib, uint32_t pix, uint32_t rgba, uint64_t pol, bool agg) {
-  const uint32_t cr = rgba & 0xFFu;
-  const uint32_t cg = (rgba >> 8) & 0xFFu;
-  const uint32_t cb = (rgba >> 16) & 0xFFu;
-  if (!agg) {
-    if (contrib) {
-      red_add_u64(rg + pix, (static_cast<unsigned long long>(cr) << 32) | cg, pol);
-      red_add_u64(ba + pix, (static_cast<unsigned long long>(cb) << 32) | 1ull, pol);
-    }
-  } else {
+  // r | g << 16 and b | 1 << 16, each one byte permute of the rgba word
+  uint32_t s_rg = __byte_perm(rgba, 0u, 0x4140u);
+  uint32_t s_bc = __byte_perm(rgba, 0x100u, 0x4542u);
+  bool add = contrib;
+  if (agg) {
     const uint32_t active = __ballot_sync(kFullMask, contrib);
     if (contrib) {
       const uint32_t peers = __match_any_sync(active, pix);
-      const uint32_t s_rg = __reduce_add_sync(peers, cr | (cg << 16));
-      const uint32_t s_bc = __reduce_add_sync(peers, cb | (1u << 16));
-      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
-        red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol);
-        red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol);
-      }
+      s_rg = __reduce_add_sync(peers, s_rg);
+      s_bc = __reduce_add_sync(peers, s_bc);
+      add = lane_id() == static_cast<uint32_t>(__ffs(peers) - 1);
     }
+  }
+  if (add) {
+    red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol);
+    red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol);
   }
 }
 
