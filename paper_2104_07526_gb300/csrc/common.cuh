@@ -47,7 +47,8 @@ __device__ __forceinline__ bool project(const ViewParams& v, float x, float y, f
   const float sx = to_screen(cx, w, v.fw);
   const float sy = to_screen(cy, w, v.fh);
   if (!(sx >= 0.0f) || !(sx < v.fw) || !(sy >= 0.0f) || !(sy < v.fh)) return false;
-  pixel = static_cast<uint32_t>(floorf(sx)) + static_cast<uint32_t>(floorf(sy)) * v.width;
+  // 0 <= s < size here, so converting with round-toward-minus-infinity is floor
+  pixel = __float2uint_rd(sx) + __float2uint_rd(sy) * v.width;
   return true;
 }
 
