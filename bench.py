@@ -43,21 +43,28 @@ METRIC = "points/s and HBM GB/s vs roofline per frame"
 UNIT = "points/s"
 POINT_BYTES = 16
 FALLBACK_HBM_GBS = 6800.0
+# The timed frame's variant.  Every exact variant leaves the same buffer; on
+# GB300 the early depth test alone is the fastest of them on the scan scene
+# (the sweep in the JSON line times all of them).
+HEADLINE_VARIANT = "early-z"
+# The HQ frames' depth-pass variant: with the deduplicating variants the
+# colour pass also sums colours inside the warp, its fastest form.
+HQ_VARIANT = "dedup+early-z"
 
 CONFIGS = {
     # name: (points, generator, views, headline view)
     "scan800M": dict(points=800_000_000, gen="scan", view="overview",
                      desc="800M-point scan scene (facades + terrain), shuffled-Morton order, overview camera, "
-                          "1920x1080, basic frame with dedup+early-z"),
+                          f"1920x1080, basic frame with {HEADLINE_VARIANT}"),
     "scan100M": dict(points=100_000_000, gen="scan", view="overview",
                      desc="100M-point scan scene (the 800M recipe at 1/8 size, for profiling), shuffled-Morton "
                           "order, overview camera, 1920x1080, basic frame"),
     "boxes50M": dict(points=50_000_000, gen="boxes", view="overview",
                      desc="50M points on 200 boxes over a ground plane, shuffled-Morton order, overview camera, "
-                          "1920x1080, basic frame with dedup+early-z"),
+                          f"1920x1080, basic frame with {HEADLINE_VARIANT}"),
     "sphere1M": dict(points=1_000_000, gen="sphere_plane", view="front",
                      desc="1M points on a sphere plus a plane, shuffled-Morton order, 640x480, basic frame with "
-                          "dedup+early-z"),
+                          f"{HEADLINE_VARIANT}"),
 }
 
 
@@ -72,7 +79,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--variant", default="dedup+early-z", help="render variant of the timed frame")
+    ap.add_argument("--variant", default=HEADLINE_VARIANT, help="render variant of the timed frame")
     ap.add_argument("--no-hq", action="store_true", help="skip the high-quality frame")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (8 clouds x 8 views) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson request stream) measurement")
@@ -209,9 +216,10 @@ def measured_hbm_gbs() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(kernel_sources: list[str]) -> dict | None:
+def recorded_traffic(kernel_sources: list[str], variant: str) -> dict | None:
     """DRAM bytes per render launch from an ncu capture, if it was taken on
-    the current kernel sources (profiles/traffic_render_scan800M.txt)."""
+    the current kernel sources and the timed variant
+    (profiles/traffic_render_scan800M.txt)."""
     path = os.path.join(ROOT, "profiles", "traffic_render_scan800M.txt")
     try:
         with open(path) as f:
@@ -222,7 +230,7 @@ def recorded_traffic(kernel_sources: list[str]) -> dict | None:
     for p in kernel_sources:
         with open(p, "rb") as f:
             h.update(f.read())
-    if kv.get("sources_sha256", "").strip() != h.hexdigest():
+    if kv.get("sources_sha256", "").strip() != h.hexdigest() or kv.get("variant", "").strip() != variant:
         return None
     return {"bytes_per_launch": float(kv["bytes_per_launch"]), "note": kv.get("note", "").strip()}
 
@@ -383,7 +391,7 @@ def run_reference(args, cfg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/u64", "data": "synthetic",
-        "config": workload_config(cfg, view),
+        "config": workload_config(cfg, view, args.variant),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                          "sample": f"per step {describe_sample(n, sample)}, put in shuffled-Morton order, "
                                    f"render + resolve, C oracle on every host core"},
@@ -393,9 +401,10 @@ def run_reference(args, cfg):
     return 0
 
 
-def workload_config(cfg: dict, view) -> dict:
-    return {"workload": cfg["desc"], "points": cfg["points"], "width": view.width, "height": view.height,
-            "order": "morton_shuffle128", "camera": view.name, "variant": "dedup+early-z",
+def workload_config(cfg: dict, view, variant: str) -> dict:
+    desc = cfg["desc"].replace(f"basic frame with {HEADLINE_VARIANT}", f"basic frame with {variant}")
+    return {"workload": desc, "points": cfg["points"], "width": view.width, "height": view.height,
+            "order": "morton_shuffle128", "camera": view.name, "variant": variant,
             "l2": "inputs larger than L2 (no flush needed)" if cfg["points"] * POINT_BYTES > 129e6
             else "inputs fit in L2 (L2-resident case)", "parallelism": "replicas"}
 
@@ -519,7 +528,7 @@ def run_ours(args, cfg):
     peak, peak_src = measured_hbm_gbs()
     achieved = n * POINT_BYTES / (render_ms * 1e-3) / 1e9
     traffic = recorded_traffic([os.path.join(ROOT, "paper_2104_07526_gb300", "csrc", f)
-                                for f in ("render.cu", "common.cuh", "geometry.cuh")]) \
+                                for f in ("render.cu", "common.cuh", "geometry.cuh")], args.variant) \
         if args.config == "scan800M" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic["bytes_per_launch"] if traffic else None,
@@ -528,12 +537,14 @@ def run_ours(args, cfg):
                 "algorithmic_bytes_per_launch": n * POINT_BYTES}
 
     # --- HQ frame (Sec. 3.5) ------------------------------------------------------
+    hq_variant = names[HQ_VARIANT]
+
     def hq_frame():
-        pcr.pcr_render_hq(h, 1.01, variant, True)
+        pcr.pcr_render_hq(h, 1.01, hq_variant, True)
         pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, fb["image"], 0)
 
     def hq1r_frame():
-        pcr.pcr_render_hq1r(h, 1.01, variant, True)
+        pcr.pcr_render_hq1r(h, 1.01, hq_variant, True)
         pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ1R, fb["image"], 0)
 
     pcr.pcr_set_hq1r_buffer(h, fb["hq1r_primary"])
@@ -582,7 +593,7 @@ def run_ours(args, cfg):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view),
+            "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view, args.variant),
             "frame_gbs": n * POINT_BYTES / (ms_per_step * 1e-3) / 1e9,
             "phases_ms": phase, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
             "hq_roofline": None if hq_ms is None else {
@@ -645,7 +656,8 @@ def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, step
     per = [(b - a) * 1e3 for a, b in zip([t0] + marks[:-1], marks)]
     return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
             "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
-            "ms_per_step": dt / steps * 1e3, "step_ms_min": min(per), "step_ms_median": statistics.median(per)}
+            "ms_per_step": dt / steps * 1e3, "step_ms_min": min(per), "step_ms_median": statistics.median(per),
+            "step_ms_max": max(per)}
 
 
 def run_batched(h, pcr, stream, dev, reps: int) -> dict:
