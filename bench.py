@@ -657,7 +657,7 @@ def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, step
     return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
             "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
             "ms_per_step": dt / steps * 1e3, "step_ms_min": min(per), "step_ms_median": statistics.median(per),
-            "step_ms_max": max(per)}
+            "step_ms_max": max(per), "step_ms": [round(x, 2) for x in per]}
 
 
 def run_batched(h, pcr, stream, dev, reps: int) -> dict:
