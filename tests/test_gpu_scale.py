@@ -1,7 +1,8 @@
 """Full-size GPU parity: the 50M-point boxes scene on all variants and
 cameras, and the 800M-point scan scene in the launch configuration the
 benchmark times (shuffled-Morton order, overview camera, 1920x1080,
-dedup+early-z), compared with the oracle over whole buffers."""
+early-z), compared with the oracle over whole buffers, with every exact
+variant, the busy-loop, the colour payload and the HQ passes."""
 import numpy as np
 import pytest
 import torch
@@ -103,13 +104,18 @@ def test_scan800M_bench_configuration(r, oracle):
     assert np.array_equal(r.resolve(pcr.PCR_RESOLVE_BASIC, 0), oracle.resolve_basic(expect, host, 0))
     for v in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_REDUCE_EARLYZ):
         assert np.array_equal(r.render_basic(v), expect), pcr.VARIANT_NAMES[v]
+    # the busy-loop comparison kernel and the colour-payload keys, full size
+    assert np.array_equal(r.render_basic(pcr.PCR_VARIANT_BUSY_LOOP), expect)
+    assert pcr.pcr_last_device_error(h) == 0
+    assert np.array_equal(r.render_rgb(pcr.PCR_VARIANT_EARLYZ), oracle.render_rgb(host, view.matrix, W, H))
     e = oracle.render_hq(host, view.matrix, W, H, 1.01)
     got = r.render_hq(pcr.PCR_VARIANT_DEDUP_EARLYZ, 1.01)
     for a, b in zip(got, e):
         assert np.array_equal(a, b)
-    # the other two cameras with the benchmark's variant
+    # the other two cameras with the benchmark's variant and dedup+early-z
     for name in ("closeup", "empty"):
         vv = views[name]
         r.view(vv.matrix, vv.width, vv.height)
-        assert np.array_equal(r.render_basic(pcr.PCR_VARIANT_DEDUP_EARLYZ),
-                              oracle.render_basic(host, vv.matrix, vv.width, vv.height)), name
+        want = oracle.render_basic(host, vv.matrix, vv.width, vv.height)
+        for v in (pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_DEDUP_EARLYZ):
+            assert np.array_equal(r.render_basic(v), want), (name, pcr.VARIANT_NAMES[v])
