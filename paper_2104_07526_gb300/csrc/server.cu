@@ -7,11 +7,12 @@
 // rest on demand and evicted least-recently-used when room is needed (never
 // while a batch in flight reads them).  pcr_server_step is the loop body:
 // it retires batches whose completion event has fired, then forms new
-// batches from the queued requests, in arrival order, as long as a batch
-// stream, frame slots and cloud memory are free.  Each batch runs on its own
-// stream, so batches overlap on the GPU; requests that arrive while others
-// render join the next batch.  A request's result stays in its frame slot
-// until the caller releases the ticket.
+// batches from the queued requests, in arrival order, as long as an
+// in-flight batch, frame slots and cloud memory are free.  Batches rotate over
+// the server's streams (one per in-flight batch unless fewer are asked for),
+// so with several streams they overlap on the GPU; requests that arrive
+// while others render join the next batch.  A request's result stays in its
+// frame slot until the caller releases the ticket.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -295,7 +296,18 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
     e = cudaMemcpyAsync(f.workspace, f.staging, pcr::batch_tables_bytes(), cudaMemcpyHostToDevice, f.stream);
   if (e == cudaSuccess) e = pcr::batch_launch(f.workspace, s->cfg.batch_config, f.stream, s->dev);
   if (e == cudaSuccess) e = cudaEventRecord(f.done, f.stream);
-  if (e != cudaSuccess) return PCR_ERR_CUDA;
+  if (e != cudaSuccess) {
+    // nothing of this batch is known to have run: its requests go back to the
+    // front of the queue, in order, with their slots and cloud pins released
+    for (auto it = take.rbegin(); it != take.rend(); ++it) {
+      pcr::Request& r = s->requests[*it];
+      s->free_slots.push_back(r.slot);
+      r.slot = -1;
+      s->queue.push_front(*it);
+    }
+    for (uint32_t id : batch_clouds) --s->clouds[id].pins;
+    return PCR_ERR_CUDA;
+  }
 
   const double t = pcr::now_us();
   for (uint64_t tk : take) {
