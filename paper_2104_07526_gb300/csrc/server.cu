@@ -306,6 +306,11 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
       s->queue.push_front(*it);
     }
     for (uint32_t id : batch_clouds) --s->clouds[id].pins;
+    for (uint32_t id : uploads) {  // their uploads may not have run
+      pcr::Cloud& c = s->clouds[id];
+      s->mem.release(c.offset, pcr::align_up(c.bytes));
+      c.resident = false;
+    }
     return PCR_ERR_CUDA;
   }
 
