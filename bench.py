@@ -47,9 +47,9 @@ FALLBACK_HBM_GBS = 6800.0
 # GB300 the early depth test alone is the fastest of them on the scan scene
 # (the sweep in the JSON line times all of them).
 HEADLINE_VARIANT = "early-z"
-# The HQ frames' depth-pass variant: with the deduplicating variants the
-# colour pass also sums colours inside the warp, its fastest form.
-HQ_VARIANT = "dedup+early-z"
+# The HQ frames' depth-pass variant (the colour pass sums colours inside the
+# warp for every variant but atomicMin).
+HQ_VARIANT = "early-z"
 
 CONFIGS = {
     # name: (points, generator, views, headline view)
@@ -684,7 +684,7 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
 
     per = [buffers(v.width, v.height) for _, v in views]
     bat = [buffers(v.width, v.height) for _, v in views]
-    var = pcr.PCR_VARIANT_DEDUP_EARLYZ
+    var = pcr.PCR_VARIANT_EARLYZ  # the per-view forms the batch kernels use
 
     def per_request():
         for (c, v), b in zip(views, per):
@@ -790,7 +790,7 @@ def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_b
     W0, H0 = 3840, 2160
     fb = pcr.alloc_framebuffer(W0, H0, dev)
     pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
-    var = pcr.PCR_VARIANT_DEDUP_EARLYZ
+    var = pcr.PCR_VARIANT_EARLYZ  # the per-view forms the batch kernels use
 
     def render(c, m, W, H, flags):
         pcr.pcr_upload_points(h, dev_clouds[c], dev_clouds[c].shape[0])

@@ -172,9 +172,9 @@ PCR_API pcr_status pcr_render_basic(pcr_ctx *ctx, int variant, int clear);
  * product; the paper uses 1.01) adds (r << 32 | g) to rg[p] and
  * (b << 32 | 1) to ba[p] with 64-bit integer adds.  clear != 0 first sets
  * depth to +inf and the sums to 0.  `variant` selects the form of the depth
- * pass (ATOMICMIN, EARLYZ, DEDUP, DEDUP_EARLYZ); the DEDUP forms also sum the
- * colours of same-pixel points within a warp before the adds.  Results do
- * not depend on the variant.  Channel sums are exact while each stays below
+ * pass (ATOMICMIN, EARLYZ, DEDUP, DEDUP_EARLYZ); with every variant but
+ * ATOMICMIN the colour pass also sums the colours of same-pixel points
+ * within a warp before the adds.  Results do not depend on the variant.  Channel sums are exact while each stays below
  * 2^32 (about 16.8M points per pixel at full intensity).  Errors: PCR_ERR_ARG
  * for a bad variant or depth_factor (not finite or <= 0), missing matrix,
  * viewport or HQ buffers. */
@@ -209,7 +209,7 @@ PCR_API pcr_status pcr_set_hq1r_buffer(pcr_ctx *ctx, void *dev_primary);
 
 /* Sec. 3.5.1, "HQS1R": the depth pass of pcr_render_hq, then a colour pass
  * with one 64-bit atomic add per contributing point (or per group of
- * same-pixel points of a warp, with the DEDUP variants) into the primary
+ * same-pixel points of a warp, with every variant but ATOMICMIN) into the primary
  * word.  The paper's 16-16-16-16 pattern leaves 2^16 - 256 counts of margin
  * for adds that land on a full word before it is reset; a GB300 can have
  * more adds than that in flight on one pixel, so, as the paper allows, the
@@ -324,9 +324,9 @@ PCR_API pcr_status pcr_batch_num_configs(int *count);
  * bytes) on the context's stream, and wait for the copy.  The arrays are
  * read during the call only; the buffers they point to are borrowed by every
  * later launch of this workspace.  Each view gets the frames its flags name,
- * with the results of pcr_render_basic(PCR_VARIANT_DEDUP_EARLYZ, clear) +
- * pcr_resolve(BASIC) and of pcr_render_hq(depth_factor, DEDUP_EARLYZ, clear) +
- * pcr_resolve(HQ), bit for bit.  Errors: PCR_ERR_ARG for counts of 0 or
+ * with the results of pcr_render_basic(clear) + pcr_resolve(BASIC) and of
+ * pcr_render_hq(depth_factor, clear) + pcr_resolve(HQ), bit for bit (the
+ * same for every exact variant; the passes use the early depth test).  Errors: PCR_ERR_ARG for counts of 0 or
  * above the maxima, a bad cloud index, size, flags, pointer or alignment, or
  * a bad depth_factor; PCR_ERR_WORKSPACE for a missing or small workspace. */
 PCR_API pcr_status pcr_batch_prepare(pcr_ctx *ctx, const pcr_batch_cloud *clouds, uint32_t num_clouds,

@@ -3,10 +3,10 @@
 // as one CUDA graph.
 //
 // Each pass over a cloud's points projects every point for a group of that
-// cloud's views.  Phase 1 writes the basic key (Sec. 3.1-3.4, warp
-// deduplication plus early depth test) and the high-quality depth (Sec. 3.5)
-// from one projection; phase 2, after all depth buffers are complete, adds
-// the high-quality colours.  A group holds as many views as fit an L2 budget
+// cloud's views.  Phase 1 writes the basic key (Sec. 3.1-3.2, with the
+// early depth test) and the high-quality depth (Sec. 3.5) from one
+// projection; phase 2, after all depth buffers are complete, adds the
+// high-quality colours (summed inside the warp first).  A group holds as many views as fit an L2 budget
 // (framebuffer bytes the pass touches), packed first-fit by decreasing size,
 // so the atomics and early depth reads of a pass stay in L2 while the point
 // stream passes through.  The passes of a phase are laid out as one sequence
@@ -128,8 +128,10 @@ __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&
   }
 }
 
-// Phase 1: per view of the pass, basic key (dedup + early-z) and HQ depth
-// (dedup + early-z), both from one projection.
+// Phase 1: per view of the pass, basic key and HQ depth, each with the
+// early depth test (on GB300 the fastest exact form once the buffer is
+// filling: warp deduplication saves no atomics after the early test), both
+// from one projection.
 template <int U>
 __global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restrict__ tables) {
   __shared__ Shared sh;
@@ -157,12 +159,12 @@ __global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restr
       if (basic) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          emit_key<PCR_VARIANT_DEDUP_EARLYZ>(bv.keys, vis[u], pix[u], w[u], base + 32u * u, seen_key[u], pol_fb);
+          emit_key<PCR_VARIANT_EARLYZ>(bv.keys, vis[u], pix[u], w[u], base + 32u * u, seen_key[u], pol_fb);
       }
       if (hq) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          emit_depth<PCR_VARIANT_DEDUP_EARLYZ>(bv.depth, vis[u], pix[u], __float_as_uint(w[u]), seen_depth[u],
+          emit_depth<PCR_VARIANT_EARLYZ>(bv.depth, vis[u], pix[u], __float_as_uint(w[u]), seen_depth[u],
                                                pol_fb);
       }
     }

@@ -534,7 +534,7 @@ cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const Vie
                             const uint32_t* depth, unsigned long long* rg, unsigned long long* ba, cudaStream_t s,
                             const Device& d) {
   if (n == 0) return cudaSuccess;
-  if (variant == PCR_VARIANT_DEDUP || variant == PCR_VARIANT_DEDUP_EARLYZ) {
+  if (variant != PCR_VARIANT_ATOMICMIN) {  // every variant but the basic one aggregates colours
     constexpr auto k = k_hq_color<true, kUnroll>;
     k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, rg, ba);
   } else {
@@ -548,7 +548,7 @@ cudaError_t launch_hq1r_color(int variant, const uint4* pts, uint32_t n, const V
                               const uint32_t* depth, unsigned long long* primary, unsigned long long* rg,
                               unsigned long long* ba, cudaStream_t s, const Device& d) {
   if (n == 0) return cudaSuccess;
-  if (variant == PCR_VARIANT_DEDUP || variant == PCR_VARIANT_DEDUP_EARLYZ) {
+  if (variant != PCR_VARIANT_ATOMICMIN) {  // every variant but the basic one aggregates colours
     constexpr auto k = k_hq1r_color<true, kUnroll>;
     k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, primary, rg, ba);
   } else {
