@@ -836,7 +836,7 @@ def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
             for var in range(7):
                 row[pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_basic(h, var, True), stream, reps=10, warm=2), 4)
-            for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ):
+            for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_DEDUP_EARLYZ):
                 row["rgb:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_rgb(h, var, True), stream, reps=10, warm=2), 4)
             pcr.pcr_last_device_error(h)
@@ -844,7 +844,7 @@ def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
                                    reps=5, warm=1), 4)
             # a run whose lock waits ran out dropped points: not a valid time
             row["busy-loop"] = busy if pcr.pcr_last_device_error(h) == 0 else "wait limit reached"
-            for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_DEDUP_EARLYZ):
+            for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_DEDUP_EARLYZ):
                 row["hq:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_hq(h, 1.01, var, True), stream, reps=5, warm=1), 4)
                 row["hq1r:" + pcr.VARIANT_NAMES[var]] = round(time_loop(

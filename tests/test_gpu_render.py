@@ -280,3 +280,23 @@ def test_hq1r_overflow_protocol(r, oracle):
     d0, *_ = oracle.render_hq(cloud, cs.camera(), cs.W, cs.H, 1.01)
     counts = oracle.hq_channel_sums(cloud, cs.camera(), cs.W, cs.H, d0, 1.01)[3]
     assert sorted(counts[counts > 0].tolist())[-1] > 100_000  # heavy pixels really were exercised
+
+
+def test_host_upload_and_download(r, oracle, sphere):
+    """The e2e path: points copied from pinned host memory by the library,
+    the frame rendered, the image read back into host memory."""
+    view = scenes.sphere_plane_views()[0]
+    W, H = view.width, view.height
+    host = torch.from_numpy(np.ascontiguousarray(sphere)).pin_memory()
+    dev = torch.zeros_like(host, device="cuda")
+    r.view(view.matrix, W, H)
+    pcr.pcr_upload_points_from_host(r.h, dev, host, host.shape[0])
+    r.points, r.n = dev, host.shape[0]
+    pcr.pcr_clear(r.h, pcr.PCR_CLEAR_KEYS)
+    pcr.pcr_render_basic(r.h, pcr.PCR_VARIANT_EARLYZ, False)
+    pcr.pcr_resolve(r.h, pcr.PCR_RESOLVE_BASIC, r.fb["image"], 0x0F0F0F0F)
+    img = np.empty(W * H, dtype=np.uint32)
+    pcr.pcr_download(r.h, img, r.fb["image"])
+    expect = oracle.render_basic(sphere, view.matrix, W, H)
+    assert np.array_equal(img, oracle.resolve_basic(expect, sphere, 0x0F0F0F0F))
+    assert torch.equal(dev.cpu(), host)
