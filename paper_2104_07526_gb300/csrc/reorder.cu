@@ -99,12 +99,15 @@ __global__ void k_bounds_init(uint32_t* misc) {
 }
 
 // Per axis min and max over non-NaN coordinates.  -0 is folded into +0 (the
-// codes do not depend on the sign of a zero bound).
-__global__ void __launch_bounds__(256) k_bounds(const uint4* __restrict__ pts, uint32_t n, uint32_t* misc) {
+// codes do not depend on the sign of a zero bound).  With `copy`, the records
+// are also copied there (the source of the final gather), saving a pass.
+__global__ void __launch_bounds__(256) k_bounds(const uint4* __restrict__ pts, uint32_t n, uint32_t* misc,
+                                                uint4* __restrict__ copy) {
   uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
   uint32_t hi[3] = {0u, 0u, 0u};
   for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
     const uint4 r = __ldcs(pts + i);
+    if (copy) __stcs(copy + i, r);
     const float v[3] = {__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z)};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -236,12 +239,16 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-// Keys for the random orders: the high half of SplitMix64 output i.
+// Keys for the random orders: the high half of SplitMix64 output i.  With
+// `copy`, record i of `pts` is also copied there (the source of the final
+// gather), saving a pass.
 __global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t seed, uint32_t* __restrict__ keys,
-                                                     uint32_t* __restrict__ vals) {
+                                                     uint32_t* __restrict__ vals, const uint4* __restrict__ pts,
+                                                     uint4* __restrict__ copy) {
   for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < count; i += gridDim.x * 256ull) {
     keys[i] = static_cast<uint32_t>(splitmix64(seed, i) >> 32);
     vals[i] = static_cast<uint32_t>(i);
+    if (copy) __stcs(copy + i, __ldcs(pts + i));
   }
 }
 
@@ -624,12 +631,15 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   const unsigned grid = stream_grid(n, d);
   cudaError_t e = cudaSuccess;
   int out = 0;
+  // the record copy the final gather reads is made by the first pass over
+  // the records, except for the 63-bit code, whose sort uses its region
+  const bool wide = mode == PCR_ORDER_MORTON63 || mode == PCR_ORDER_MORTON63_SHUFFLE128;
   if (mode == PCR_ORDER_SHUFFLE) {
-    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], vals[0]);
+    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], vals[0], pts, copy);
     e = radix_sort(keys, vals, n, 32, counts, partials, s, out);
-  } else if (mode == PCR_ORDER_MORTON || mode == PCR_ORDER_MORTON_SHUFFLE128) {
+  } else if (!wide) {
     k_bounds_init<<<1, 32, 0, s>>>(misc);
-    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc);
+    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
     k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], vals[0]);
     e = radix_sort(keys, vals, n, 30, counts, partials, s, out);
   } else {
@@ -637,7 +647,7 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     // not needed until the final gather.
     uint32_t* hi = reinterpret_cast<uint32_t*>(ws + l.pts_copy);
     k_bounds_init<<<1, 32, 0, s>>>(misc);
-    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc);
+    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
     k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi, vals[0]);
     int a = 0;
     e = radix_sort(keys, vals, n, 32, counts, partials, s, a);
@@ -655,7 +665,7 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
-    k_random_keys<<<stream_grid(nb, d), 256, 0, s>>>(nb, seed, bkeys[0], bvals[0]);
+    k_random_keys<<<stream_grid(nb, d), 256, 0, s>>>(nb, seed, bkeys[0], bvals[0], nullptr, nullptr);
     int bout = 0;
     e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout);
     if (e != cudaSuccess) return e;
@@ -665,7 +675,7 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
                                                                                  shuffled);
     perm = shuffled;
   }
-  k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
+  if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
   k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
   return cudaGetLastError();
 }
