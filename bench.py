@@ -381,7 +381,9 @@ def run_reference(args, cfg):
     pilot = host_sample(pilot_n)
     rate = pilot_n / max(time_oracle(pilot, view, threads=0), 1e-6)
     per_step = budget / max(1, args.steps + args.warmup)
-    sample = int(min(n, max(100_000, rate * per_step)))
+    # at most 100M points: the oracle puts the sample in shuffled-Morton order
+    # (a single-threaded sort) before timing, which must stay a few minutes
+    sample = int(min(n, 100_000_000, max(100_000, rate * per_step)))
     pts = host_sample(sample)
     for _ in range(args.warmup):
         time_oracle(pts, view, threads=0)
