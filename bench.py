@@ -287,16 +287,17 @@ def time_oracle(pts_np: np.ndarray, view, repeats: int = 1, threads: int = 1) ->
 #   bounds 16 read (plus 16 written: the record copy, for the 30-bit orders);
 #   30-bit codes 16 read + 8 written (key, index); 63-bit codes 16 read + 12
 #   written (low key, high word, index); each sort pass 4 (histogram read) +
-#   8 read + 8 written (key, index); high-word gather 4 + 4 read + 4 written;
-#   random keys 8 written, plus the record copy 16 + 16; batch sort and
+#   8 read + 8 written (key, index), and 4 + 4 more for the high word the
+#   63-bit orders carry through their first four passes; random keys 8
+#   written, plus the record copy 16 + 16; batch sort and
 #   permutation about 1; separate record copy (63-bit orders) 16 + 16;
 #   record gather 4 (index) + 16 read + 16 written.
 REORDER_BYTES_PER_POINT = {
     "morton": 32 + 24 + 4 * 20 + 36,
     "morton_shuffle128": 32 + 24 + 4 * 20 + 1 + 36,
     "shuffle": 8 + 32 + 4 * 20 + 36,
-    "morton63": 16 + 28 + 4 * 20 + 12 + 4 * 20 + 32 + 36,
-    "morton63_shuffle128": 16 + 28 + 4 * 20 + 12 + 4 * 20 + 1 + 32 + 36,
+    "morton63": 16 + 28 + 4 * 28 + 4 * 20 + 32 + 36,
+    "morton63_shuffle128": 16 + 28 + 4 * 28 + 4 * 20 + 1 + 32 + 36,
 }
 
 

@@ -1,9 +1,9 @@
 // Vertex-order kernels (Sec. 4, and the orderings listed in Sec. 5):
 // bounds, 30-bit and 63-bit Morton codes, a stable LSD radix sort of (32-bit
 // key, 32-bit index) pairs, the 128-point batch shuffle and the record
-// gather.  A 63-bit code sorts as two 32-bit halves: the low half first, then
-// the high half (gathered through the first sort's permutation), both
-// stable, which is a stable sort by the whole code.
+// gather.  A 63-bit code sorts as two 32-bit halves: the low half first
+// (the high half carried along), then the high half, both stable, which is a
+// stable sort by the whole code.
 //
 // Radix sort: 8-bit digits, one pass per digit, three steps per pass:
 //   1. k_sort_hist: per tile of 8192 keys, count each digit.
@@ -224,12 +224,6 @@ __global__ void __launch_bounds__(256) k_morton63(const uint4* __restrict__ pts,
   }
 }
 
-// dst[j] = src[idx[j]]
-__global__ void __launch_bounds__(256) k_gather_u32(const uint32_t* __restrict__ src, const uint32_t* __restrict__ idx,
-                                                    uint32_t* __restrict__ dst, uint32_t n) {
-  for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < n; j += gridDim.x * 256ull) dst[j] = src[idx[j]];
-}
-
 // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output k of the generator
 // seeded with `seed` mixes the state seed + (k + 1) * 0x9E3779B97F4A7C15.
 __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
@@ -314,12 +308,15 @@ __device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_sr
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gmem_src), "r"(bytes) : "memory");
 }
 
+// `cin`/`cout` (may be null): a second 32-bit value carried with each key
+// (the high words of 63-bit codes while their low words are sorted).
 __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
                                                                   uint32_t* __restrict__ kout,
                                                                   uint32_t* __restrict__ vout, uint32_t n, int shift,
                                                                   const uint32_t* __restrict__ offsets,
-                                                                  uint32_t tiles) {
+                                                                  uint32_t tiles, const uint32_t* __restrict__ cin,
+                                                                  uint32_t* __restrict__ cout) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
   uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
@@ -402,6 +399,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t
     const uint32_t g = global_start[d] + (l - local_start[d]);
     kout[g] = key;
     vout[g] = __ldg(vin + tile_base + src);
+    if (cout) cout[g] = __ldg(cin + tile_base + src);
   }
 }
 
@@ -514,9 +512,10 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 }
 
 // Stable sort of count (key, value) pairs on the low key_bits bits.  The
-// result ends in buffer index `out` (0 or 1).
+// result ends in buffer index `out` (0 or 1).  With `carry` (may be null),
+// a second value per key moves with it through its own two buffers.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
-                       uint32_t* partials, cudaStream_t s, int& out) {
+                       uint32_t* partials, cudaStream_t s, int& out, uint32_t* const* carry = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
@@ -528,7 +527,8 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
     e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
     k_sort_scatter<<<tiles, kSortThreads, kScatterSmem, s>>>(keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count,
-                                                             shift, counts, tiles);
+                                                             shift, counts, tiles, carry ? carry[out] : nullptr,
+                                                             carry ? carry[out ^ 1] : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     out ^= 1;
@@ -643,20 +643,22 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], vals[0]);
     e = radix_sort(keys, vals, n, 30, counts, partials, s, out);
   } else {
-    // 63-bit code: the high halves wait in the record-copy region, which is
-    // not needed until the final gather.
-    uint32_t* hi = reinterpret_cast<uint32_t*>(ws + l.pts_copy);
+    // 63-bit code: the high halves ride along with their keys while the low
+    // halves are sorted, in two buffers in the record-copy region (not
+    // needed until the final gather); then they are the keys.
+    uint32_t* hi[2] = {reinterpret_cast<uint32_t*>(ws + l.pts_copy),
+                       reinterpret_cast<uint32_t*>(ws + l.pts_copy) + align_up(4ull * n) / 4};
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
-    k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi, vals[0]);
+    k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi[0], vals[0]);
     int a = 0;
-    e = radix_sort(keys, vals, n, 32, counts, partials, s, a);
+    e = radix_sort(keys, vals, n, 32, counts, partials, s, a, hi);
     if (e != cudaSuccess) return e;
-    k_gather_u32<<<grid, 256, 0, s>>>(hi, vals[a], keys[a], n);
-    uint32_t* hkeys[2] = {keys[a], keys[a ^ 1]};
+    uint32_t* hkeys[2] = {hi[a], hi[a ^ 1]};
     uint32_t* hvals[2] = {vals[a], vals[a ^ 1]};
     int b = 0;
     e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b);
+    // the sorted values end in vals[a ^ b]
     out = a ^ b;
   }
   if (e != cudaSuccess) return e;
