@@ -13,8 +13,14 @@
  *  - Sec. 3.5: the high-quality variant: a depth pass, then a colour pass
  *    that sums the colours of all points within a depth band of the nearest
  *    one, then a resolve that averages.
- *  - Sec. 4: Morton order and shuffled Morton order (batches of 128 points)
- *    as a one-time reordering of the point buffer.
+ *  - Sec. 3.5.1: the single-atomic high-quality form (HQS1R); Sec. 3.1 with
+ *    the colour-payload key as its listing prints it; Sec. 2 and 5: the
+ *    just-set and busy-loop comparison kernels.
+ *  - Sec. 4 and 5: Morton order (30-bit, or the paper's 63-bit), shuffled
+ *    Morton order (batches of 128 points) and a random shuffle, as a
+ *    one-time reordering of the point buffer.
+ *  - Many clouds and views rendered together (pcr_batch_*), and a serving
+ *    loop over resident clouds with continuous batching (pcr_server_*).
  *
  * Conventions, for every entry point:
  *  - Every call returns a pcr_status.  No C++ exception crosses this
@@ -55,7 +61,9 @@ enum {
     PCR_ERR_ARG = -1,          /* bad argument; nothing was launched */
     PCR_ERR_CUDA = -2,         /* a CUDA call failed (no device, launch error, ...) */
     PCR_ERR_WORKSPACE = -3,    /* workspace missing or too small; nothing was launched */
-    PCR_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
+    PCR_ERR_TIMEOUT = -4,      /* reserved: bounded device-side waits report through
+                                  pcr_last_device_error (PCR_DEVICE_ERROR_WAIT_TIMEOUT),
+                                  since launches return before the kernel runs */
     PCR_ERR_UNSUPPORTED = -5   /* valid request this build does not provide */
 };
 
