@@ -632,36 +632,57 @@ def time_loop(fn, stream, reps: int, warm: int) -> float:
 
 def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, steps: int, warm: int) -> dict:
     """Points from pinned host memory -> frame -> image back to host, every
-    step, all through the C ABI."""
+    step, all through the C ABI.  Two ways in: the render kernels read the
+    pinned buffer over the host link (pcr_upload_points_mapped, the reported
+    value), or the library copies it into a device buffer first
+    (pcr_upload_points_from_host, reported as `copy_path`).  Both move every
+    point record host -> device once per step."""
     import torch
     host = torch.empty(points.shape, dtype=points.dtype, pin_memory=True)
     host.copy_(points)
     img_host = torch.empty(W * H, dtype=torch.int32).pin_memory()
 
-    def step():
-        pcr.pcr_upload_points_from_host(h, points, host, n)
+    def frame_and_download():
         pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
         pcr.pcr_render_basic(h, variant, False)
         pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
-        pcr.pcr_download(h, img_host, fb["image"])
+        pcr.pcr_download(h, img_host, fb["image"])  # synchronous
 
-    for _ in range(warm):
-        step()
-    torch.cuda.synchronize()
-    barrier(dist)
-    t0 = time.perf_counter()
-    marks = []
-    for _ in range(steps):
-        step()  # ends in a synchronous download of the image
-        marks.append(time.perf_counter())
-    torch.cuda.synchronize()
-    dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    def step_mapped():
+        pcr.pcr_upload_points_mapped(h, host, n)
+        frame_and_download()
+
+    def step_copy():
+        pcr.pcr_upload_points_from_host(h, points, host, n)
+        frame_and_download()
+
+    def measure(step) -> dict:
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        marks = []
+        for _ in range(steps):
+            step()
+            marks.append(time.perf_counter())
+        torch.cuda.synchronize()
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        per = [(b - a) * 1e3 for a, b in zip([t0] + marks[:-1], marks)]
+        return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
+                "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
+                "ms_per_step": dt / steps * 1e3, "step_ms_min": min(per), "step_ms_median": statistics.median(per),
+                "step_ms_max": max(per), "step_ms": [round(x, 2) for x in per]}
+
+    mapped = measure(step_mapped)
+    mapped_image = img_host.clone()
+    copied = measure(step_copy)
+    identical = bool(torch.equal(mapped_image, img_host))
     del host
-    per = [(b - a) * 1e3 for a, b in zip([t0] + marks[:-1], marks)]
-    return {"value": aggregate_throughput(n, world, dt / steps), "unit": UNIT,
-            "h2d_bytes_per_step": n * POINT_BYTES, "d2h_bytes_per_step": W * H * 4,
-            "ms_per_step": dt / steps * 1e3, "step_ms_min": min(per), "step_ms_median": statistics.median(per),
-            "step_ms_max": max(per), "step_ms": [round(x, 2) for x in per]}
+    return {**mapped, "path": "render kernels read the pinned host buffer over the host link "
+                              "(pcr_upload_points_mapped)", "images_identical": identical,
+            "copy_path": {**copied, "path": "cudaMemcpyAsync into a device buffer, then render "
+                                            "(pcr_upload_points_from_host)"}}
 
 
 def run_batched(h, pcr, stream, dev, reps: int) -> dict:

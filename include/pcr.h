@@ -137,6 +137,21 @@ PCR_API pcr_status pcr_upload_points(pcr_ctx *ctx, const void *dev_points, uint6
  * errors as pcr_upload_points, plus PCR_ERR_CUDA if the copy fails. */
 PCR_API pcr_status pcr_upload_points_from_host(pcr_ctx *ctx, void *dev_points, const void *host_points, uint64_t n);
 
+/* Borrow n records that stay in pinned host memory (allocated by
+ * cudaHostAlloc / cudaMallocHost, or registered by cudaHostRegister, and
+ * mapped into the device's address space): the following renders read them
+ * over the host link, each render once, with no device copy.  On a Grace
+ * host the link (NVLink-C2C) is about as fast as a cudaMemcpyAsync of the
+ * same bytes, so a basic frame rendered this way costs the transfer alone,
+ * while copy-then-render costs the transfer plus the render.  HQ frames read
+ * the points twice; copy those first.  The buffer must stay pinned and
+ * unchanged until the work that reads it has finished.  Errors: PCR_ERR_ARG
+ * on a NULL or misaligned pointer with n > 0, on n >= 2^32, or when the first
+ * or the last record is not in pinned, mapped host memory (plain pageable
+ * memory and device memory are refused); PCR_ERR_CUDA if the device cannot be
+ * selected. */
+PCR_API pcr_status pcr_upload_points_mapped(pcr_ctx *ctx, const void *host_points, uint64_t n);
+
 /* Sec. 3.1 "worldViewProj": a row-major 4x4 float matrix with
  * clip = M (x, y, z, 1)^T.  Only rows 0, 1 and 3 are used: clip.w is the
  * linear depth and there is no near or far plane test.  The matrix is copied.

@@ -132,6 +132,38 @@ pcr_status pcr_upload_points_from_host(pcr_ctx* ctx, void* dev_points, const voi
   return pcr_upload_points(ctx, dev_points, n);
 }
 
+namespace {
+// Device address of a byte of pinned, mapped host memory, or nullptr.
+void* mapped_address(const void* host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost) return nullptr;
+  void* dev = nullptr;
+  if (cudaHostGetDevicePointer(&dev, const_cast<void*>(host), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return dev;
+}
+}  // namespace
+
+pcr_status pcr_upload_points_mapped(pcr_ctx* ctx, const void* host_points, uint64_t n) {
+  if (!ctx || n > kMaxPoints) return PCR_ERR_ARG;
+  if (n == 0) return pcr_upload_points(ctx, nullptr, 0);
+  if (!host_points || !aligned(host_points, 16)) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  // Both ends must be pinned and mapped, and map to one contiguous range.
+  const uint64_t last = n * 16 - 1;
+  char* first_dev = static_cast<char*>(mapped_address(host_points));
+  char* last_dev = static_cast<char*>(mapped_address(static_cast<const char*>(host_points) + last));
+  if (!first_dev || !last_dev || last_dev != first_dev + last) return PCR_ERR_ARG;
+  return pcr_upload_points(ctx, first_dev, n);
+}
+
 pcr_status pcr_set_matrix(pcr_ctx* ctx, const float m[16]) {
   if (!ctx || !m) return PCR_ERR_ARG;
   std::memcpy(ctx->m, m, sizeof(ctx->m));

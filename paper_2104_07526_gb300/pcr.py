@@ -112,6 +112,7 @@ _SIGS = {
     "pcr_set_stream": [_VP, _VP],
     "pcr_upload_points": [_VP, _VP, _U64],
     "pcr_upload_points_from_host": [_VP, _VP, _VP, _U64],
+    "pcr_upload_points_mapped": [_VP, _VP, _U64],
     "pcr_set_matrix": [_VP, C.POINTER(_FLT)],
     "pcr_set_viewport": [_VP, _INT, _INT],
     "pcr_set_framebuffer": [_VP, _VP, _VP, _VP, _VP],
@@ -235,6 +236,13 @@ def pcr_upload_points_from_host(ctx: int, dev_points, host_points, n: int | None
         n = _nbytes(host_points) // 16
     _check(lib().pcr_upload_points_from_host(ctx, _dptr(dev_points, "dev_points"),
                                              _hptr(host_points, "host_points"), n), "pcr_upload_points_from_host")
+
+
+def pcr_upload_points_mapped(ctx: int, host_points, n: int | None = None):
+    """host_points: a pinned CPU tensor (e.g. torch.empty(..., pin_memory=True))."""
+    if n is None:
+        n = _nbytes(host_points) // 16
+    _check(lib().pcr_upload_points_mapped(ctx, _hptr(host_points, "host_points"), n), "pcr_upload_points_mapped")
 
 
 def pcr_set_matrix(ctx: int, m):

@@ -300,3 +300,39 @@ def test_host_upload_and_download(r, oracle, sphere):
     expect = oracle.render_basic(sphere, view.matrix, W, H)
     assert np.array_equal(img, oracle.resolve_basic(expect, sphere, 0x0F0F0F0F))
     assert torch.equal(dev.cpu(), host)
+
+
+def test_render_from_mapped_host_memory(r, oracle, sphere):
+    """Points left in pinned host memory and read by the render kernels over
+    the host link: every exact variant and the resolve's colour gather match
+    the oracle."""
+    view = scenes.sphere_plane_views()[0]
+    W, H = view.width, view.height
+    host = torch.from_numpy(np.ascontiguousarray(sphere)).pin_memory()
+    n = host.shape[0]
+    r.view(view.matrix, W, H)
+    pcr.pcr_upload_points_mapped(r.h, host, n)
+    expect = oracle.render_basic(sphere, view.matrix, W, H)
+    for v in pcr.EXACT_VARIANTS:
+        pcr.pcr_render_basic(r.h, v, True)
+        assert np.array_equal(r.fb["keys"].cpu().numpy().view(np.uint64), expect), pcr.VARIANT_NAMES[v]
+    pcr.pcr_resolve(r.h, pcr.PCR_RESOLVE_BASIC, r.fb["image"], 0)
+    assert np.array_equal(r.fb["image"].cpu().numpy().view(np.uint32), oracle.resolve_basic(expect, sphere, 0))
+    torch.cuda.synchronize()
+    pcr.pcr_upload_points_mapped(r.h, host[:0], 0)  # n = 0 is allowed
+
+
+def test_mapped_upload_refusals(r):
+    """Pageable host memory, device memory, a misaligned start and a range
+    running past the pinned block are refused before anything is launched."""
+    host = torch.zeros((1024, 4), dtype=torch.int32).pin_memory()
+    pageable = torch.zeros((1024, 4), dtype=torch.int32)
+    dev = torch.zeros((1024, 4), dtype=torch.int32, device="cuda")
+    lib = pcr.lib()
+    assert lib.pcr_upload_points_mapped(r.h, pageable.data_ptr(), 1024) == pcr.PCR_ERR_ARG
+    assert lib.pcr_upload_points_mapped(r.h, dev.data_ptr(), 1024) == pcr.PCR_ERR_ARG
+    assert lib.pcr_upload_points_mapped(r.h, host.data_ptr() + 4, 1000) == pcr.PCR_ERR_ARG
+    assert lib.pcr_upload_points_mapped(r.h, host.data_ptr(), 1 << 31) == pcr.PCR_ERR_ARG
+    assert lib.pcr_upload_points_mapped(r.h, None, 1) == pcr.PCR_ERR_ARG
+    assert lib.pcr_upload_points_mapped(r.h, host.data_ptr(), 1024) == pcr.PCR_OK
+    r.upload(np.zeros((0, 4), np.int32))
