@@ -267,9 +267,15 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid) {
   return peers;
 }
 
-// Per tile, the count of each digit.  Each warp counts into its own 256
-// counters with shared-memory atomics (one per key: no ranking is needed to
-// count), and the eight warps' counters are summed at the end.
+constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 1024 = kSortRounds x 32
+
+// Per tile, the count of each digit.  Lane l of each warp counts keys
+// [32l, 32l + 32) of the warp's 1024 (eight 16-byte loads) and adds a run of
+// equal digits to its warp's counters once, when the digit changes.
+// Coherent orders (and the passes after the first, whose input is sorted on
+// the lower digits) have long runs, which one add per key would turn into
+// many same-address shared-memory atomics.  The eight warps' counters are
+// summed at the end.
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
                                                             uint32_t* __restrict__ counts, uint32_t tiles) {
   __shared__ uint32_t hist[kSortWarps][kRadix];
@@ -277,12 +283,35 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   for (int w = 0; w < kSortWarps; ++w) hist[w][threadIdx.x] = 0;
   __syncthreads();
   uint32_t* mine = hist[threadIdx.x >> 5];
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kTile + threadIdx.x;
-#pragma unroll 8
-  for (int r = 0; r < kSortRounds; ++r) {
-    const uint64_t i = base + static_cast<uint64_t>(r) * kSortThreads;
-    if (i < n) atomicAdd(&mine[(__ldcs(keys + i) >> shift) & (kRadix - 1)], 1u);
+  const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kTile + (threadIdx.x >> 5) * kKeysPerWarp +
+                         lane_id() * kSortRounds;
+  uint32_t cur = 0, run = 0;
+  auto count = [&](uint32_t key) {
+    const uint32_t d = (key >> shift) & (kRadix - 1);
+    if (d == cur) {
+      ++run;
+    } else {
+      if (run) atomicAdd(&mine[cur], run);
+      cur = d;
+      run = 1;
+    }
+  };
+  if (first + kSortRounds <= n) {
+    const uint4* q = reinterpret_cast<const uint4*>(keys + first);  // 128-byte aligned
+    uint4 v[kSortRounds / 4];
+#pragma unroll
+    for (int k = 0; k < kSortRounds / 4; ++k) v[k] = __ldg(q + k);
+#pragma unroll
+    for (int k = 0; k < kSortRounds / 4; ++k) {
+      count(v[k].x);
+      count(v[k].y);
+      count(v[k].z);
+      count(v[k].w);
+    }
+  } else {
+    for (uint64_t i = first; i < n && i < first + kSortRounds; ++i) count(__ldg(keys + i));
   }
+  if (run) atomicAdd(&mine[cur], run);
   __syncthreads();
   uint32_t c = 0;
 #pragma unroll
@@ -293,7 +322,6 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
 template <int NT>
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total);
 
-constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 1024 = kSortRounds x 32
 
 // Dynamic shared memory of k_sort_scatter: the tile's keys as loaded, each
 // output slot's input slot, the per-warp first slot of each digit, and

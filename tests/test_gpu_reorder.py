@@ -35,15 +35,19 @@ def test_reorder_matches_oracle(r, oracle, n):
         assert np.array_equal(dev.cpu().numpy(), oracle.gather(cloud, expect) if n else cloud), (n, mode)
 
 
-def test_reorder_scene_with_duplicates(r, oracle):
-    """Scanline scene (many equal Morton codes: stability decides) at a size
-    spanning many sort tiles with a ragged tail."""
-    cloud = scenes.scan(300_017, seed=1).numpy()
+@pytest.mark.parametrize("n", [300_017, 5_000_017])
+def test_reorder_scene_with_duplicates(r, oracle, n):
+    """Scanline scene (many equal Morton codes: stability decides) at sizes
+    spanning many sort tiles with a ragged tail; 5M points is 611 tiles, more
+    than the sort kernel keeps resident at once, so later tiles start only as
+    earlier ones finish and each tile's look-back meets every state."""
+    cloud = scenes.scan(n, seed=1).numpy()
     for mode in MODES:
         expect = oracle.reorder(cloud, 42, mode)
         dev = torch.from_numpy(cloud.copy()).cuda()
         perm = reorder_gpu(r.h, dev, 42, mode)
         assert np.array_equal(perm, expect), mode
+    assert pcr.pcr_last_device_error(r.h) == 0
 
 
 def test_reorder_degenerate_and_nonfinite(r, oracle):
