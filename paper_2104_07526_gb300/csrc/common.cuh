@@ -6,6 +6,17 @@
 // an FMA), the division is IEEE (__fdiv_rn).  The point is culled unless
 // w > 0 and finite, and unless 0 <= s < size on both axes with
 // s = (clip / w * 0.5 + 0.5) * size.  pixel = floor(sx) + floor(sy) * width.
+//
+// Two forms here compute the same results with fewer instructions:
+// - ndc * 0.5 + 0.5 is one fused multiply-add.  ndc * 0.5 is exact unless
+//   |ndc| < 2^-125, and then both forms round to 0.5.
+// - The tests are integer compares of bit patterns.  w lies in (0, inf)
+//   exactly when bits(w) - 1 < 0x7F7FFFFF: -0, negatives and NaNs fail.  For
+//   s, 0 <= s < size exactly when bits(s) < bits(size): s is never -0, and
+//   negatives and NaNs have larger patterns.
+// The projection has no branch: every slot of a chunk is projected, and
+// culled slots drop out at the one visibility test.  The compiler can then
+// interleave the divisions of a lane's slots.
 #pragma once
 
 #include <cstdint>
@@ -34,19 +45,20 @@ __device__ __forceinline__ float row_dot(const float r[4], float x, float y, flo
 }
 
 __device__ __forceinline__ float to_screen(float c, float w, float size) {
-  return __fmul_rn(__fadd_rn(__fmul_rn(__fdiv_rn(c, w), 0.5f), 0.5f), size);
+  return __fmul_rn(__fmaf_rn(__fdiv_rn(c, w), 0.5f, 0.5f), size);
 }
 
 // Returns true and the pixel/depth when the point is visible.
 __device__ __forceinline__ bool project(const ViewParams& v, float x, float y, float z, uint32_t& pixel,
                                         float& w) {
   w = row_dot(v.r3, x, y, z);
-  if (!(w > 0.0f) || !(w < __int_as_float(kInfBits))) return false;
+  const bool w_ok = __float_as_uint(w) - 1u < 0x7F7FFFFFu;
   const float cx = row_dot(v.r0, x, y, z);
   const float cy = row_dot(v.r1, x, y, z);
   const float sx = to_screen(cx, w, v.fw);
   const float sy = to_screen(cy, w, v.fh);
-  if (!(sx >= 0.0f) || !(sx < v.fw) || !(sy >= 0.0f) || !(sy < v.fh)) return false;
+  if (!(w_ok && __float_as_uint(sx) < __float_as_uint(v.fw) && __float_as_uint(sy) < __float_as_uint(v.fh)))
+    return false;
   // 0 <= s < size here, so converting with round-toward-minus-infinity is floor
   pixel = __float2uint_rd(sx) + __float2uint_rd(sy) * v.width;
   return true;

@@ -42,10 +42,10 @@ constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
 // Each chunk runs in three phases so independent memory round trips overlap:
 // project all U points, issue all U early reads, then test and write.
 // P selects the key payload: the point index, or the 24-bit colour.  The
-// kernels are held to 48 registers (5 resident blocks of 256 threads per SM):
+// kernels are held to 40 registers (6 resident blocks of 256 threads per SM):
 // the frame is latency-bound, and one resident block fewer costs more than
 // the few instructions the register cap adds.
-constexpr int kRenderMinBlocks = kMinBlocks < 5 ? 5 : kMinBlocks;
+constexpr int kRenderMinBlocks = kMinBlocks < 6 ? 6 : kMinBlocks;
 
 template <int V, int U, int P>
 __global__ void __launch_bounds__(kThreads, kRenderMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
