@@ -46,6 +46,8 @@ constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
 // the frame is latency-bound, and one resident block fewer costs more than
 // the few instructions the register cap adds.
 constexpr int kRenderMinBlocks = kMinBlocks < 6 ? 6 : kMinBlocks;
+// The HQ depth and colour passes take the same cap (40 registers each).
+constexpr int kHqMinBlocks = kMinBlocks < 6 ? 6 : kMinBlocks;
 
 template <int V, int U, int P>
 __global__ void __launch_bounds__(kThreads, kRenderMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_busy(const uint
 // ---------------------------------------------------------------------------
 
 template <int V, int U>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_depth(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_depth(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        uint32_t* __restrict__ depth) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_depth(const uint4* 
 
 // Colour pass (Listing "hqs_render"): see aggregate_chunk and emit_color.
 template <bool AGG, int U>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
+__global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        float factor, const uint32_t* __restrict__ depth,
                                                        unsigned long long* __restrict__ rg,
                                                        unsigned long long* __restrict__ ba) {
