@@ -48,8 +48,10 @@ FALLBACK_HBM_GBS = 6800.0
 # (the sweep in the JSON line times all of them).
 HEADLINE_VARIANT = "early-z"
 # The HQ frames' depth-pass variant (the colour pass sums colours inside the
-# warp for every variant but atomicMin).
-HQ_VARIANT = "early-z"
+# warp for every variant but atomicMin): with the early test the depth pass
+# is the same for early-z and dedup+early-z up to the deduplication, which
+# is about 1.5% faster on the scan scene's HQ frames.
+HQ_VARIANT = "dedup+early-z"
 
 CONFIGS = {
     # name: (points, generator, views, headline view)

@@ -123,8 +123,10 @@ __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&
   for (int u = 0; u < U; ++u) {
     pix[u] = 0;
     w[u] = 0.0f;
-    vis[u] = ok[u] && project(vp, __uint_as_float(r[u].x), __uint_as_float(r[u].y), __uint_as_float(r[u].z), pix[u],
-                              w[u]);
+    // project every slot (a slot past the cloud holds zeros), then mask: no
+    // branch per slot, so the slots' divisions interleave
+    vis[u] = project(vp, __uint_as_float(r[u].x), __uint_as_float(r[u].y), __uint_as_float(r[u].z), pix[u], w[u]) &&
+             ok[u];
   }
 }
 
