@@ -6,10 +6,10 @@
 // stable sort by the whole code.
 //
 // Radix sort: 8-bit digits, one pass per digit, three steps per pass:
-//   1. k_sort_hist: per tile of 8192 keys, count each digit.
+//   1. k_sort_hist: per tile of 6144 keys, count each digit.
 //   2. exclusive scan of the counts in digit-major order, which gives every
 //      (digit, tile) its first output slot;
-//   3. k_sort_scatter: each warp of a tile takes 1024 consecutive keys and
+//   3. k_sort_scatter: each warp of a tile takes 768 consecutive keys and
 //      counts their digits (per 32 keys, one match.any when their digits
 //      form few runs, else eight ballots, one per digit bit);
 //      one prefix over (digit, warp) then gives every warp its first slot
@@ -31,7 +31,7 @@ namespace {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 32;
+constexpr int kSortRounds = 24;  // keys per lane in a tile
 constexpr uint32_t kTile = kSortThreads * kSortRounds;
 constexpr int kDigitBits = 8;
 constexpr int kRadix = 1 << kDigitBits;
@@ -267,10 +267,10 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid) {
   return peers;
 }
 
-constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 1024 = kSortRounds x 32
+constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 768 = kSortRounds x 32
 
 // Per tile, the count of each digit.  Lane l of each warp counts keys
-// [32l, 32l + 32) of the warp's 1024 (eight 16-byte loads) and adds a run of
+// [24l, 24l + 24) of the warp's 768 (six 16-byte loads) and adds a run of
 // equal digits to its warp's counters once, when the digit changes.
 // Coherent orders (and the passes after the first, whose input is sorted on
 // the lower digits) have long runs, which one add per key would turn into
@@ -325,7 +325,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
 
 // Dynamic shared memory of k_sort_scatter: the tile's keys as loaded, each
 // output slot's input slot, the per-warp first slot of each digit, and
-// per-digit starts (tile-local and global).  58 KB: three blocks per SM.
+// per-digit starts (tile-local and global).  46 KB: four blocks per SM.
 constexpr size_t kScatterSmem =
     sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile + sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
 
@@ -338,7 +338,7 @@ __device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_sr
 
 // `cin`/`cout` (may be null): a second 32-bit value carried with each key
 // (the high words of 63-bit codes while their low words are sorted).
-__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
                                                                   uint32_t* __restrict__ kout,
                                                                   uint32_t* __restrict__ vout, uint32_t n, int shift,
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t
   global_start[t] = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  // this warp's 1024 consecutive keys; pass 1 counts their digits, and each
+  // this warp's 768 consecutive keys; pass 1 counts their digits, and each
   // key keeps its rank among the round's lanes with its digit, that group's
   // size and the digit (rank | size << 8 | digit << 16, bit 31 set for a key
   // inside the cloud)
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const uint32_t
   }
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
-  // output positions; values are gathered from the tile's 32 KB window
+  // output positions; values are gathered from the tile's 24 KB window
 #pragma unroll 8
   for (uint32_t l = t; l < total; l += kSortThreads) {
     const uint32_t src = s_src[l];

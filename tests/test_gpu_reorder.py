@@ -23,7 +23,7 @@ def r():
     rend.close()
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 127, 128, 129, 1000, 8191, 8192, 8193, 100_003])
+@pytest.mark.parametrize("n", [0, 1, 2, 127, 128, 129, 1000, 6143, 6144, 6145, 8191, 8192, 8193, 12289, 100_003])
 def test_reorder_matches_oracle(r, oracle, n):
     cloud = scenes.random_cloud(n, seed=n + 7).numpy() if n else np.zeros((0, 4), np.int32)
     for mode in MODES:
@@ -38,7 +38,7 @@ def test_reorder_matches_oracle(r, oracle, n):
 @pytest.mark.parametrize("n", [300_017, 5_000_017])
 def test_reorder_scene_with_duplicates(r, oracle, n):
     """Scanline scene (many equal Morton codes: stability decides) at sizes
-    spanning many sort tiles with a ragged tail; 5M points is 611 tiles, more
+    spanning many sort tiles with a ragged tail; 5M points is 814 tiles, more
     than the sort kernel keeps resident at once, so later tiles start only as
     earlier ones finish and each tile's look-back meets every state."""
     cloud = scenes.scan(n, seed=1).numpy()
