@@ -98,6 +98,8 @@ __global__ void k_bounds_init(uint32_t* misc) {
   }
 }
 
+constexpr int kStreamUnroll = 4;
+
 // Per axis min and max over non-NaN coordinates.  -0 is folded into +0 (the
 // codes do not depend on the sign of a zero bound).  With `copy`, the records
 // are also copied there (the source of the final gather), saving a pass.
@@ -105,16 +107,28 @@ __global__ void __launch_bounds__(256) k_bounds(const uint4* __restrict__ pts, u
                                                 uint4* __restrict__ copy) {
   uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
   uint32_t hi[3] = {0u, 0u, 0u};
-  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
-    const uint4 r = __ldcs(pts + i);
-    if (copy) __stcs(copy + i, r);
-    const float v[3] = {__uint_as_float(r.x), __uint_as_float(r.y), __uint_as_float(r.z)};
+  // kStreamUnroll records per thread per step, all loads issued first
+  const uint64_t step = gridDim.x * 256ull * kStreamUnroll;
+  for (uint64_t i0 = blockIdx.x * 256ull * kStreamUnroll + threadIdx.x; i0 < n; i0 += step) {
+    uint4 r[kStreamUnroll];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      if (v[a] == v[a]) {
-        const uint32_t o = float_order(__fadd_rn(v[a], 0.0f));
-        lo[a] = min(lo[a], o);
-        hi[a] = max(hi[a], o);
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      const uint64_t i = i0 + 256ull * u;
+      r[u] = i < n ? __ldcs(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      const uint64_t i = i0 + 256ull * u;
+      if (i >= n) break;
+      if (copy) __stcs(copy + i, r[u]);
+      const float v[3] = {__uint_as_float(r[u].x), __uint_as_float(r[u].y), __uint_as_float(r[u].z)};
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (v[a] == v[a]) {
+          const uint32_t o = float_order(__fadd_rn(v[a], 0.0f));
+          lo[a] = min(lo[a], o);
+          hi[a] = max(hi[a], o);
+        }
       }
     }
   }
@@ -165,16 +179,27 @@ __global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, u
   if (ez > ext) ext = ez;
   const bool degenerate = !(ext > 0.0f) || !(ext < __int_as_float(kInfBits));
   const float scale = degenerate ? 0.0f : __fdiv_rn(1024.0f, ext);
-  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
-    uint32_t code = 0;
-    if (!degenerate) {
-      const uint4 r = __ldcs(pts + i);
-      code = (spread3(quantise(__uint_as_float(r.x), lo[0], scale)) << 2) |
-             (spread3(quantise(__uint_as_float(r.y), lo[1], scale)) << 1) |
-             spread3(quantise(__uint_as_float(r.z), lo[2], scale));
+  const uint64_t step = gridDim.x * 256ull * kStreamUnroll;
+  for (uint64_t i0 = blockIdx.x * 256ull * kStreamUnroll + threadIdx.x; i0 < n; i0 += step) {
+    uint4 r[kStreamUnroll];
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      const uint64_t i = i0 + 256ull * u;
+      r[u] = (!degenerate && i < n) ? __ldcs(pts + i) : make_uint4(0u, 0u, 0u, 0u);
     }
-    keys[i] = code;
-    vals[i] = static_cast<uint32_t>(i);
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      const uint64_t i = i0 + 256ull * u;
+      if (i >= n) break;
+      uint32_t code = 0;
+      if (!degenerate) {
+        code = (spread3(quantise(__uint_as_float(r[u].x), lo[0], scale)) << 2) |
+               (spread3(quantise(__uint_as_float(r[u].y), lo[1], scale)) << 1) |
+               spread3(quantise(__uint_as_float(r[u].z), lo[2], scale));
+      }
+      keys[i] = code;
+      vals[i] = static_cast<uint32_t>(i);
+    }
   }
 }
 
