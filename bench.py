@@ -528,6 +528,10 @@ def run_ours(args, cfg):
     ms_per_step = max_total_ms / K
     phase = {p: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, p in
              enumerate(("clear", "render", "resolve"))}
+    frame_times = [e[0].elapsed_time(e[3]) for e in ev]
+    render_times = [e[1].elapsed_time(e[2]) for e in ev]
+    frame_stats = {"frame_ms_median": statistics.median(frame_times), "frame_ms_min": min(frame_times),
+                   "frame_ms_max": max(frame_times), "render_ms_median": statistics.median(render_times)}
     render_ms = phase["render"]
     value = aggregate_throughput(n, world, max_total_ms / K / 1e3)
 
@@ -601,7 +605,7 @@ def run_ours(args, cfg):
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view, args.variant),
             "frame_gbs": n * POINT_BYTES / (ms_per_step * 1e-3) / 1e9,
-            "phases_ms": phase, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
+            "phases_ms": phase, "frame_stats": frame_stats, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
             "hq_roofline": None if hq_ms is None else {
                 "bound": "hbm", "algorithmic_bytes": 2 * n * POINT_BYTES,
                 "achieved_gbs": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9,
