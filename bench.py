@@ -592,12 +592,12 @@ def run_ours(args, cfg):
                               args.cpu_seconds)
 
     # --- served: Poisson request stream, continuous batching vs plain launches --
-    served = None
+    served = served_sat = None
     if not args.no_served:
         orders.clear()
         points = cloud = None
         torch.cuda.empty_cache()
-        served = run_served(h, pcr, stream, dev, args.served_seconds)
+        served, served_sat = run_served(h, pcr, stream, dev, args.served_seconds, rates=(2000.0, 8000.0))
 
     if rank == 0:
         line = {
@@ -613,7 +613,7 @@ def run_ours(args, cfg):
             "reorder_roofline": reorder_roofline(reorder_ms, n, peak),
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
-            "sweep_ms": sweep, "batched": batched, "served": served,
+            "sweep_ms": sweep, "batched": batched, "served": served, "served_saturated": served_sat,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -691,6 +691,20 @@ def run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world, step
                                             "(pcr_upload_points_from_host)"}}
 
 
+def vertex_order(h, pcr, clouds, dev) -> None:
+    """Put every cloud in shuffled-Morton order (Sec. 4), in place: the
+    one-time preprocessing the paper prescribes before rendering."""
+    import torch
+    if not clouds:
+        return
+    ws = torch.empty(pcr.pcr_reorder_workspace_size(max(c.shape[0] for c in clouds)), dtype=torch.uint8, device=dev)
+    for c in clouds:
+        pcr.pcr_reorder_morton_shuffle128(h, c, c.shape[0], 0x5EED, pcr.PCR_ORDER_MORTON_SHUFFLE128, ws)
+    torch.cuda.synchronize()
+    del ws
+    torch.cuda.empty_cache()
+
+
 def run_batched(h, pcr, stream, dev, reps: int) -> dict:
     """8 boxes clouds (1M..200M points) x 8 orbit views (256^2..2048^2), basic
     and HQ frames: every view through the single-view calls (7 launches per
@@ -700,6 +714,7 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
     from paper_2104_07526_gb300 import scenes
     t0 = time.perf_counter()
     clouds = [scenes.boxes(nc, seed=i, device=dev) for i, nc in enumerate(scenes.BATCH_CLOUD_SIZES)]
+    vertex_order(h, pcr, clouds, dev)
     views = scenes.batch_views(len(clouds))
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
@@ -743,26 +758,40 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
     torch.cuda.synchronize()
     identical = all(torch.equal(p_[k], b_[k]) for p_, b_ in zip(per, bat) for k in p_)
     point_views = sum(clouds[c].shape[0] for c, _ in views)
-    return {"workload": "8 boxes clouds (1M..200M points, 388M total) x 8 orbit views (256^2..2048^2), basic + HQ",
+    return {"workload": "8 boxes clouds (1M..200M points, 388M total, shuffled-Morton order) x 8 orbit views "
+                        "(256^2..2048^2), basic + HQ",
             "per_request_ms": per_ms, "per_request_launches": 7 * len(views), "batched_graph_ms": batched_ms,
             "batched_launches": 4, "speedup": per_ms / batched_ms, "identical": identical, "config": config,
             "point_views_per_s": point_views / (batched_ms * 1e-3), "generate_s": gen_s}
 
 
 def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_batch_views: int = 32,
-               batch_config: int = 0, plain_baseline: bool = True, rate: float = 2000.0, streams: int = 1,
-               max_batch_clouds: int = 2) -> dict:
-    """16 boxes clouds (1M..300M points) registered with the server from host
-    memory, a 150 GB arena, and a Poisson stream of 2000 requests/s (random
-    cloud, resolution 512^2..3840x2160, basic or HQ, orbit camera).  Latency
-    runs from each request's scheduled arrival to its completion.  The same
-    stream is then served by plain per-request launches (one request at a
-    time, in order)."""
+               batch_config: int = 0, plain_baseline: bool = True, rates=(2000.0,), streams: int = 2,
+               max_batch_clouds: int = 2) -> list:
+    """16 boxes clouds (1M..300M points, shuffled-Morton order) registered
+    with the server from host memory, a 150 GB arena, and for each rate a
+    Poisson stream of requests (random cloud, resolution 512^2..3840x2160,
+    basic or HQ, orbit camera).  Latency runs from each request's scheduled
+    arrival to its completion.  The same stream is then served by plain
+    per-request launches (one request at a time, in order).  One result per
+    rate."""
     import torch
     from paper_2104_07526_gb300 import scenes
     sizes = scenes.SERVE_CLOUD_SIZES
     dev_clouds = [scenes.boxes(nc, seed=100 + i, device=dev) for i, nc in enumerate(sizes)]
+    vertex_order(h, pcr, dev_clouds, dev)
     host_clouds = [c.cpu().numpy() for c in dev_clouds]
+    out = []
+    for rate in rates:
+        out.append(served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, max_inflight,
+                                  max_batch_views, batch_config, plain_baseline, streams, max_batch_clouds))
+    return out
+
+
+def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, max_inflight, max_batch_views,
+                   batch_config, plain_baseline, streams, max_batch_clouds) -> dict:
+    import torch
+    from paper_2104_07526_gb300 import scenes
     reqs = scenes.serve_requests(int(rate * seconds), rate, seed=7, num_clouds=len(sizes))
     arena = torch.empty(150 << 30, dtype=torch.uint8, device=dev)
     srv = pcr.pcr_server_create(h, arena, 3840, 2160, num_slots=64, max_batch_views=max_batch_views,
@@ -849,8 +878,9 @@ def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_b
     span_p = (us() - arrival[0]) / 1e6
     plain = {"p50_ms": float(np.percentile(lat_p, 50)), "p99_ms": float(np.percentile(lat_p, 99)),
              "requests_per_s": len(reqs) / span_p, "points_per_s": pts_p / span_p}
-    return {"workload": f"{len(sizes)} boxes clouds ({sizes[0] / 1e6:.0f}M..{sizes[-1] / 1e6:.0f}M points), "
-                        f"Poisson 2000 requests/s for {seconds:g} s, 512^2..3840x2160, basic/HQ 50/50, "
+    return {"workload": f"{len(sizes)} boxes clouds ({sizes[0] / 1e6:.0f}M..{sizes[-1] / 1e6:.0f}M points, "
+                        "shuffled-Morton order), "
+                        f"Poisson {rate:g} requests/s for {seconds:g} s, 512^2..3840x2160, basic/HQ 50/50, "
                         "150 GB arena", "requests": len(reqs), "served": served, "plain": plain,
             "throughput_gain": served["requests_per_s"] / plain["requests_per_s"]}
 
