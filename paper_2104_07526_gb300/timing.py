@@ -65,6 +65,7 @@ def time_batch(launches: int = 4) -> dict:
             pcr.pcr_reorder_morton_shuffle128(h, c, c.shape[0], 0x5EED, pcr.PCR_ORDER_MORTON_SHUFFLE128, rws)
         torch.cuda.synchronize()
         del rws
+        torch.cuda.empty_cache()
         ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device="cuda")
         pcr.pcr_batch_prepare(h, [pcr.batch_cloud(c) for c in clouds],
                               [pcr.batch_view(v.matrix, v.width, v.height, c, flags, **b) for (c, v), b in
