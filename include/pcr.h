@@ -467,9 +467,13 @@ PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, ui
  * batches, frame slots, cloud memory and max_batch_clouds allow (a request
  * that cannot join now waits while later ones go ahead; the oldest request
  * always joins the next batch that has room).  *completed (may be NULL)
- * counts the requests this call retired.  A batch renders each request
- * exactly as pcr_batch_launch would, so a result does not depend on which
- * other requests shared its batch. */
+ * counts the requests this call retired.  A batch in which some cloud has
+ * two views or more runs through pcr_batch_launch; a batch whose views all
+ * have different clouds runs each view through the single-view kernels
+ * (pcr_render_basic with early-z, pcr_render_hq with dedup+early-z, and the
+ * resolves).  Both give every request exactly the buffers of the request
+ * rendered alone, so a result does not depend on which other requests
+ * shared its batch. */
 PCR_API pcr_status pcr_server_step(pcr_server *srv, uint32_t *completed);
 
 /* PCR_REQUEST_QUEUED, _RUNNING or _DONE for a ticket not yet released. */

@@ -210,6 +210,48 @@ pcr_status retire(pcr_server* s, uint32_t* completed) {
   return PCR_OK;
 }
 
+// A batch in which no two views share a cloud shares no point loads.  Its
+// views then run through the single-view kernels instead of the batch
+// kernels (early-z keys, dedup+early-z HQ depth, warp-aggregated colours):
+// the same buffers bit for bit, with the kernels tuned for one view.
+cudaError_t launch_single_views(pcr_server* s, const std::vector<uint64_t>& take, cudaStream_t st) {
+  for (uint64_t tk : take) {
+    const pcr::Request& r = s->requests[tk];
+    const pcr::Cloud& c = s->clouds[r.cloud];
+    const uint4* pts = static_cast<const uint4*>(cloud_points(s, c));
+    const uint32_t n = static_cast<uint32_t>(c.n);
+    pcr::ViewParams v{};
+    for (int k = 0; k < 4; ++k) {
+      v.r0[k] = r.matrix[k];
+      v.r1[k] = r.matrix[4 + k];
+      v.r3[k] = r.matrix[12 + k];
+    }
+    v.fw = static_cast<float>(r.width);
+    v.fh = static_cast<float>(r.height);
+    v.width = static_cast<uint32_t>(r.width);
+    v.height = static_cast<uint32_t>(r.height);
+    const uint64_t npx = static_cast<uint64_t>(r.width) * static_cast<uint64_t>(r.height);
+    const SlotPtrs p = slot_ptrs(s, r.slot);
+    cudaError_t e = cudaSuccess;
+    if (r.flags & PCR_BATCH_BASIC) {
+      e = pcr::launch_fill_u64(p.keys, npx, pcr::kEmptyKey, st, s->dev);
+      if (e == cudaSuccess) e = pcr::launch_render_basic(PCR_VARIANT_EARLYZ, pts, n, v, p.keys, st, s->dev);
+      if (e == cudaSuccess)
+        e = pcr::launch_resolve_basic(p.keys, npx, pts, n, s->cfg.background_rgba, p.image, st, s->dev);
+    }
+    if (e == cudaSuccess && (r.flags & PCR_BATCH_HQ)) {
+      e = pcr::launch_clear_hq(p.depth, p.rg, p.ba, npx, st, s->dev);
+      if (e == cudaSuccess) e = pcr::launch_hq_depth(PCR_VARIANT_DEDUP_EARLYZ, pts, n, v, p.depth, st, s->dev);
+      if (e == cudaSuccess)
+        e = pcr::launch_hq_color(PCR_VARIANT_DEDUP_EARLYZ, pts, n, v, s->cfg.depth_factor, p.depth, p.rg, p.ba, st,
+                                 s->dev);
+      if (e == cudaSuccess) e = pcr::launch_resolve_hq(p.rg, p.ba, npx, s->cfg.background_rgba, p.hq_image, st, s->dev);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 // Form and launch one batch on the free in-flight slot `f`.  Returns
 // PCR_OK with nothing launched when no queued request can run now.
 pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
@@ -273,8 +315,10 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
     v.hq_ba = (r.flags & PCR_BATCH_HQ) ? p.ba : nullptr;
     v.hq_image = (r.flags & PCR_BATCH_HQ) ? p.hq_image : nullptr;
   }
-  pcr::batch_build_tables(bc.data(), static_cast<uint32_t>(bc.size()), bv.data(), static_cast<uint32_t>(bv.size()),
-                          s->cfg.depth_factor, s->cfg.background_rgba, f.staging);
+  const bool shared_cloud = batch_clouds.size() < take.size();  // some cloud has two views or more
+  if (shared_cloud)
+    pcr::batch_build_tables(bc.data(), static_cast<uint32_t>(bc.size()), bv.data(), static_cast<uint32_t>(bv.size()),
+                            s->cfg.depth_factor, s->cfg.background_rgba, f.staging);
 
   cudaError_t e = cudaSuccess;
   for (uint32_t id : uploads) {
@@ -292,9 +336,11 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
         std::find(uploads.begin(), uploads.end(), id) == uploads.end())
       e = cudaStreamWaitEvent(f.stream, c.ready, 0);
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && shared_cloud)
     e = cudaMemcpyAsync(f.workspace, f.staging, pcr::batch_tables_bytes(), cudaMemcpyHostToDevice, f.stream);
-  if (e == cudaSuccess) e = pcr::batch_launch(f.workspace, s->cfg.batch_config, f.stream, s->dev);
+  if (e == cudaSuccess)
+    e = shared_cloud ? pcr::batch_launch(f.workspace, s->cfg.batch_config, f.stream, s->dev)
+                     : launch_single_views(s, take, f.stream);
   if (e == cudaSuccess) e = cudaEventRecord(f.done, f.stream);
   if (e != cudaSuccess) {
     // nothing of this batch is known to have run: its requests go back to the

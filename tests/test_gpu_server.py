@@ -138,6 +138,45 @@ def test_mixed_requests_match_rendering_alone(ctx, oracle):
         pcr.pcr_server_destroy(srv)
 
 
+def test_both_launch_paths_match_rendering_alone(ctx, oracle):
+    """A batch in which no two views share a cloud runs its views through the
+    single-view kernels; one with a shared cloud runs the batch kernels.
+    One view per batch forces the first path; submitting views of one cloud
+    together with room for them all forces the second.  Both give the
+    oracle's buffers."""
+    clouds = _clouds()
+    dev = [torch.from_numpy(c.copy()).cuda() for c in clouds]
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(43)
+    for views_per_batch, same_cloud in ((1, False), (6, True)):
+        srv = pcr.pcr_server_create(ctx, arena, 200, 150, num_slots=8, max_batch_views=views_per_batch,
+                                    max_inflight=2, background_rgba=BG)
+        try:
+            for i, d in enumerate(dev):
+                pcr.pcr_server_add_device_cloud(srv, i, d)
+            reqs = _requests(rng, clouds, 12, 200, 150)
+            if same_cloud:
+                reqs = [(3, scenes.camera((0, -300, 200), (0, 0, 0), (0, 0, 1), W, H), W, H, f)
+                        for _, _, W, H, f in reqs]
+            by_ticket = {pcr.pcr_server_submit(srv, *r): r for r in reqs}
+
+            def finish(t):
+                c, m, W, H, flags = by_ticket.pop(t)
+                _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+                pcr.pcr_server_release(srv, t)
+
+            _drain(srv, list(by_ticket), finish)
+            assert not by_ticket
+            st = pcr.pcr_server_stats_get(srv)
+            assert st["completed"] == len(reqs)
+            if same_cloud:
+                assert st["batches"] < len(reqs)  # views shared batches
+            else:
+                assert st["batches"] == len(reqs)
+        finally:
+            pcr.pcr_server_destroy(srv)
+
+
 def test_shared_stream_cloud_cap_and_completion_queue(ctx, oracle):
     """Three in-flight batches on one stream, at most one cloud per batch;
     finished tickets come out of the completion queue exactly once."""
