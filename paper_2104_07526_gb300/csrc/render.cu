@@ -46,7 +46,8 @@ constexpr int kMinBlocks = PCR_GEOMETRY_MIN_BLOCKS;
 // the frame is latency-bound, and one resident block fewer costs more than
 // the few instructions the register cap adds.
 constexpr int kRenderMinBlocks = kMinBlocks < 6 ? 6 : kMinBlocks;
-// The HQ depth and colour passes take the same cap (40 registers each).
+// The HQ depth and colour passes, HQS1R's included, take the same cap (40
+// registers each).
 constexpr int kHqMinBlocks = kMinBlocks < 6 ? 6 : kMinBlocks;
 
 template <int V, int U, int P>
@@ -238,7 +239,7 @@ constexpr unsigned long long kHq1rChannelMask = 0x3FFFull;
 constexpr unsigned long long kHq1rCountMask = 0x3FFFFFull;
 
 template <bool AGG, int U>
-__global__ void __launch_bounds__(kThreads, kMinBlocks)
+__global__ void __launch_bounds__(kThreads, kHqMinBlocks)
     k_hq1r_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v, float factor,
                  const uint32_t* __restrict__ depth, unsigned long long* __restrict__ primary,
                  unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba) {
