@@ -78,6 +78,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="scan800M")
     ap.add_argument("--no-sweep", action="store_true", help="skip the variant x order x camera sweep")
+    ap.add_argument("--no-small", action="store_true", help="skip the 1M and 50M-point workloads")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffers) measurement")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -349,6 +350,50 @@ def oracle_baseline(cloud_host_fn, n: int, view, target_s: float) -> dict:
                               "sample": f"{describe_sample(n, one_sample)}, {one_frames} frame(s), {one_total:.2f} s"}}
 
 
+def run_small_configs(h, pcr, stream, dev, with_cpu: bool) -> dict:
+    """The two smaller workloads beside the headline one: the 1M-point
+    sphere-and-plane scene (640x480, L2-resident points: launch- and
+    L2-bound) and the 50M-point boxes scene (overview camera, 1920x1080),
+    both in shuffled-Morton order.  Per workload: the GPU frame (clear,
+    early-z render, resolve) with CUDA events, and, as CPU baselines, the
+    oracle's host-parallel and single-threaded frames on the whole cloud."""
+    import torch
+    out = {}
+    for name in ("sphere1M", "boxes50M"):
+        cfg = CONFIGS[name]
+        cloud, views = make_cloud(cfg, dev)
+        vertex_order(h, pcr, [cloud], dev)
+        view = next(v for v in views if v.name == cfg["view"])
+        n = cloud.shape[0]
+        fb = pcr.alloc_framebuffer(view.width, view.height, dev)
+        pcr.pcr_upload_points(h, cloud, n)
+        pcr.pcr_set_matrix(h, view.matrix)
+        pcr.pcr_set_viewport(h, view.width, view.height)
+        pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+
+        def frame():
+            pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
+            pcr.pcr_render_basic(h, pcr.PCR_VARIANT_EARLYZ, False)
+            pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+
+        reps = 200 if n <= 10_000_000 else 50
+        ms = time_loop(frame, stream, reps=reps, warm=5)
+        row = {"points": n, "width": view.width, "height": view.height, "gpu_frame_ms": ms,
+               "gpu_points_per_s": n / (ms * 1e-3), "frames": reps}
+        if with_cpu:
+            host = cloud.cpu().numpy()
+            t_all = time_oracle(host, view, repeats=2, threads=0)
+            t_one = time_oracle(host, view, repeats=1, threads=1)
+            row["cpu_baseline"] = {"kind": "oracle", "cores": oracle_threads(), "frame_ms": t_all * 1e3,
+                                   "points_per_s": n / t_all, "single_thread_frame_ms": t_one * 1e3,
+                                   "single_thread_points_per_s": n / t_one,
+                                   "sample": "the whole cloud, best of 2 frames (1 single-threaded)"}
+        out[name] = row
+        del cloud, fb
+        torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -591,6 +636,14 @@ def run_ours(args, cfg):
         cpu = oracle_baseline(lambda k: points[cpu_sample_indices(n, k).to(dev)].cpu().numpy(), n, view,
                               args.cpu_seconds)
 
+    # --- the smaller workloads (1M and 50M points), GPU frame and CPU oracle --
+    small = None
+    if not args.no_small:
+        small = run_small_configs(h, pcr, stream, dev, with_cpu=(rank == 0 and world == 1 and not args.no_cpu))
+        pcr.pcr_upload_points(h, points, n)
+        set_view(view)
+        pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+
     # --- served: Poisson request stream, continuous batching vs plain launches --
     served = served_sat = None
     if not args.no_served:
@@ -613,7 +666,8 @@ def run_ours(args, cfg):
             "reorder_roofline": reorder_roofline(reorder_ms, n, peak),
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
-            "sweep_ms": sweep, "batched": batched, "served": served, "served_saturated": served_sat,
+            "sweep_ms": sweep, "small_configs": small, "batched": batched, "served": served,
+            "served_saturated": served_sat,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
