@@ -34,10 +34,6 @@ using namespace geom;
 constexpr int kThreads = 256;
 constexpr uint64_t kSlot = 128;  // cloud padding and the largest chunk (32 lanes x 4)
 
-#ifndef PCR_BATCH_L2_BUDGET
-#define PCR_BATCH_L2_BUDGET (64ull << 20)
-#endif
-constexpr uint64_t kL2Budget = PCR_BATCH_L2_BUDGET;
 
 struct Tables {
   BatchHeader hdr;
@@ -312,7 +308,7 @@ namespace {
 // framebuffer bytes fit the L2 budget (first fit, largest first); a view
 // larger than the budget gets a pass of its own.
 void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
-                  uint32_t num_views, int phase) {
+                  uint32_t num_views, int phase, uint64_t l2_budget) {
   uint32_t ng = 0, nord = 0;
   uint64_t slot = 0;
   for (uint32_t c = 0; c < num_clouds; ++c) {
@@ -331,7 +327,7 @@ void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds,
     std::vector<uint64_t> used;
     for (const auto& [bytes, vi] : mine) {
       size_t b = 0;
-      while (b < bins.size() && used[b] + bytes > kL2Budget) ++b;
+      while (b < bins.size() && used[b] + bytes > l2_budget) ++b;
       if (b == bins.size()) {
         bins.emplace_back();
         used.push_back(0);
@@ -359,7 +355,8 @@ void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds,
 uint64_t batch_tables_bytes() { return sizeof(Tables); }
 
 void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
-                        uint32_t num_views, float depth_factor, uint32_t background, void* host_tables) {
+                        uint32_t num_views, float depth_factor, uint32_t background, void* host_tables,
+                        uint64_t l2_budget) {
   Tables* t = new (host_tables) Tables();
   t->hdr.num_clouds = num_clouds;
   t->hdr.num_views = num_views;
@@ -397,8 +394,8 @@ void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, cons
   }
   t->hdr.total_pixels = pixel;
   t->hdr.hq_views = hq;
-  build_groups(t, clouds, num_clouds, views, num_views, 0);
-  build_groups(t, clouds, num_clouds, views, num_views, 1);
+  build_groups(t, clouds, num_clouds, views, num_views, 0, l2_budget);
+  build_groups(t, clouds, num_clouds, views, num_views, 1, l2_budget);
 }
 
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
@@ -406,7 +403,7 @@ cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, co
                           cudaStream_t s) {
   void* host = ::operator new(sizeof(Tables), std::nothrow);
   if (!host) return cudaErrorMemoryAllocation;
-  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host);
+  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host, kBatchL2Budget);
   cudaError_t e = cudaMemcpyAsync(workspace, host, sizeof(Tables), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   static_cast<Tables*>(host)->~Tables();

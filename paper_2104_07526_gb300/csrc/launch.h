@@ -96,8 +96,15 @@ uint64_t batch_workspace_bytes();
 // Size of the job tables, and building them into caller-provided host
 // memory (e.g. pinned staging for an asynchronous copy into a workspace).
 uint64_t batch_tables_bytes();
+// l2_budget: framebuffer bytes one pass over a cloud may touch (the views of
+// a cloud are packed into passes that fit it).
 void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
-                        uint32_t num_views, float depth_factor, uint32_t background, void* host_tables);
+                        uint32_t num_views, float depth_factor, uint32_t background, void* host_tables,
+                        uint64_t l2_budget);
+// A batch alone on the GPU (pcr_batch_prepare) packs passes into 96 MB of the
+// 129 MB L2; the server, whose batches may run two at a time, into 64 MB.
+constexpr uint64_t kBatchL2Budget = 96ull << 20;
+constexpr uint64_t kServedL2Budget = 64ull << 20;
 int batch_num_configs();
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                           uint32_t num_views, float depth_factor, uint32_t background, void* workspace,

@@ -318,7 +318,7 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
   const bool shared_cloud = batch_clouds.size() < take.size();  // some cloud has two views or more
   if (shared_cloud)
     pcr::batch_build_tables(bc.data(), static_cast<uint32_t>(bc.size()), bv.data(), static_cast<uint32_t>(bv.size()),
-                            s->cfg.depth_factor, s->cfg.background_rgba, f.staging);
+                            s->cfg.depth_factor, s->cfg.background_rgba, f.staging, pcr::kServedL2Budget);
 
   cudaError_t e = cudaSuccess;
   for (uint32_t id : uploads) {
