@@ -597,12 +597,16 @@ __global__ void k_find_last_batch(const uint32_t* __restrict__ order, uint32_t n
     if (order[t] == nb - 1) misc[6] = static_cast<uint32_t>(t);
 }
 
-// perm[new] = old for the shuffled Morton order: output batch slot t holds
-// batch order[t] of the Morton order; slots after the short last batch start
-// (kBatch - last_size) earlier.
-__global__ void __launch_bounds__(256) k_batch_perm(const uint32_t* __restrict__ order,
-                                                    const uint32_t* __restrict__ morton, uint32_t n, uint32_t nb,
-                                                    const uint32_t* __restrict__ misc, uint32_t* __restrict__ perm) {
+// The shuffled Morton order, gathered: output batch slot t holds batch
+// order[t] of the Morton order; slots after the short last batch start
+// (kBatch - last_size) earlier.  Each record moves straight from its Morton
+// position (perm[new] = old is formed on the fly, and written out only when
+// asked for), so no permutation array makes a round trip through memory.
+__global__ void __launch_bounds__(256) k_gather_batches(const uint4* __restrict__ src,
+                                                        const uint32_t* __restrict__ order,
+                                                        const uint32_t* __restrict__ morton, uint32_t n, uint32_t nb,
+                                                        const uint32_t* __restrict__ misc, uint4* __restrict__ dst,
+                                                        uint32_t* __restrict__ perm_out) {
   const uint32_t t_last = misc[6];
   const uint32_t last_size = n - (nb - 1) * kBatch;
   const uint64_t total = static_cast<uint64_t>(nb) * kBatch;
@@ -612,8 +616,10 @@ __global__ void __launch_bounds__(256) k_batch_perm(const uint32_t* __restrict__
     const uint32_t b = order[t];
     const uint32_t size = (b == nb - 1) ? last_size : kBatch;
     if (k < size) {
-      const uint64_t start = static_cast<uint64_t>(t) * kBatch - (t > t_last ? (kBatch - last_size) : 0u);
-      perm[start + k] = morton[static_cast<uint64_t>(b) * kBatch + k];
+      const uint64_t at = static_cast<uint64_t>(t) * kBatch - (t > t_last ? (kBatch - last_size) : 0u) + k;
+      const uint32_t p = morton[static_cast<uint64_t>(b) * kBatch + k];
+      dst[at] = src[p];
+      if (perm_out) perm_out[at] = p;
     }
   }
 }
@@ -725,10 +731,10 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout);
     if (e != cudaSuccess) return e;
     k_find_last_batch<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, misc);
-    uint32_t* shuffled = keys[out];  // the sorted codes are no longer needed
-    k_batch_perm<<<stream_grid(static_cast<uint64_t>(nb) * kBatch, d), 256, 0, s>>>(bvals[bout], perm, n, nb, misc,
-                                                                                 shuffled);
-    perm = shuffled;
+    if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
+    k_gather_batches<<<stream_grid(static_cast<uint64_t>(nb) * kBatch, d), 256, 0, s>>>(copy, bvals[bout], perm, n, nb,
+                                                                                     misc, pts, perm_out);
+    return cudaGetLastError();
   }
   if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
   k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
