@@ -1,0 +1,87 @@
+"""Host-side logic of bench.py that shapes its JSON line: the traffic record
+that is reported only while it matches the kernel sources, the reorder
+roofline arithmetic, the CPU sample, the workload description and the
+command-line defaults the timing rules require."""
+import hashlib
+import os
+import sys
+
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _write_record(root, sources, variant="early-z", bytes_per_launch=12803000000):
+    h = hashlib.sha256()
+    for p in sources:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    os.makedirs(os.path.join(root, "profiles"), exist_ok=True)
+    with open(os.path.join(root, "profiles", "traffic_render_scan800M.txt"), "w") as f:
+        f.write("# a comment line = with an equals sign\n")
+        f.write(f"sources_sha256={h.hexdigest()}\nvariant={variant}\nbytes_per_launch={bytes_per_launch}\n"
+                "note=test record\n")
+
+
+def test_traffic_record_follows_sources(tmp_path, monkeypatch):
+    srcs = []
+    for name, text in (("a.cu", "kernel a\n"), ("b.cuh", "helper b\n")):
+        p = tmp_path / name
+        p.write_text(text)
+        srcs.append(str(p))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.recorded_traffic(srcs, "early-z") is None  # no record yet
+    _write_record(str(tmp_path), srcs)
+    rec = bench.recorded_traffic(srcs, "early-z")
+    assert rec == {"bytes_per_launch": 12803000000.0, "note": "test record"}
+    assert bench.recorded_traffic(srcs, "dedup+early-z") is None  # another variant was timed
+    (tmp_path / "b.cuh").write_text("helper b changed\n")
+    assert bench.recorded_traffic(srcs, "early-z") is None  # the kernel changed since the capture
+
+
+def test_committed_traffic_record_is_for_the_timed_variant():
+    with open(os.path.join(ROOT, "profiles", "traffic_render_scan800M.txt")) as f:
+        kv = dict(line.split("=", 1) for line in f.read().splitlines() if "=" in line and not line.startswith("#"))
+    assert kv["variant"].strip() == bench.HEADLINE_VARIANT
+    assert 12.8e9 <= float(kv["bytes_per_launch"]) < 12.9e9  # 16 B per point of the 800M scene, plus little
+
+
+def test_reorder_roofline_arithmetic():
+    table = bench.REORDER_BYTES_PER_POINT
+    assert table["morton"] == 172 and table["morton_shuffle128"] == 173 and table["shuffle"] == 156
+    assert table["morton63"] == 304 and table["morton63_shuffle128"] == 305
+    n, peak = 800_000_000, 6760.9
+    out = bench.reorder_roofline({"morton": 27.5, "shuffle": 48.0}, n, peak)
+    assert out["morton"]["algorithmic_gb"] == pytest.approx(137.6)
+    assert out["morton"]["achieved_gbs"] == pytest.approx(137.6 / 27.5e-3)
+    assert out["shuffle"]["frac"] == pytest.approx(124.8 / 48.0e-3 / peak)
+
+
+def test_cpu_sample_and_its_description():
+    assert bench.cpu_sample_indices(10, 3).tolist() == [0, 3, 6]
+    assert bench.cpu_sample_indices(5, 10).tolist() == [0, 1, 2, 3, 4]
+    assert bench.describe_sample(5, 5) == "the first 5 of the 5 points"
+    assert bench.describe_sample(800, 100) == "every 8th point of the 800-point cloud (100 points)"
+
+
+class _View:
+    def __init__(self, name, w, h):
+        self.name, self.width, self.height = name, w, h
+
+
+def test_workload_config_names_the_timed_variant_and_cache_case():
+    big = bench.workload_config(bench.CONFIGS["scan800M"], _View("overview", 1920, 1080), "dedup+early-z")
+    assert big["variant"] == "dedup+early-z" and "basic frame with dedup+early-z" in big["workload"]
+    assert big["points"] == 800_000_000 and big["l2"].startswith("inputs larger than L2")
+    small = bench.workload_config(bench.CONFIGS["sphere1M"], _View("front", 640, 480), bench.HEADLINE_VARIANT)
+    assert small["l2"].startswith("inputs fit in L2")
+
+
+def test_default_arguments_meet_the_timing_rules():
+    args = bench.parse_args([])
+    assert args.gpus == 1 and args.impl == "ours" and args.config == "scan800M"
+    assert args.warmup >= 3 and args.steps >= 50
+    assert bench.HQ_VARIANT in ("early-z", "dedup+early-z")
