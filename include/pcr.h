@@ -349,9 +349,12 @@ PCR_API pcr_status pcr_batch_num_configs(int *count);
  * later launch of this workspace.  Each view gets the frames its flags name,
  * with the results of pcr_render_basic(clear) + pcr_resolve(BASIC) and of
  * pcr_render_hq(depth_factor, clear) + pcr_resolve(HQ), bit for bit (the
- * same for every exact variant; the passes use the early depth test).  Errors: PCR_ERR_ARG for counts of 0 or
- * above the maxima, a bad cloud index, size, flags, pointer or alignment, or
- * a bad depth_factor; PCR_ERR_WORKSPACE for a missing or small workspace. */
+ * same for every exact variant; the passes use the early depth test).  The
+ * views of each cloud are packed into passes over its points whose
+ * framebuffers fit 96 MB of the L2 cache (a larger view gets a pass of its
+ * own).  Errors: PCR_ERR_ARG for counts of 0 or above the maxima, a bad cloud
+ * index, size, flags, pointer or alignment, or a bad depth_factor;
+ * PCR_ERR_WORKSPACE for a missing or small workspace. */
 PCR_API pcr_status pcr_batch_prepare(pcr_ctx *ctx, const pcr_batch_cloud *clouds, uint32_t num_clouds,
                                      const pcr_batch_view *views, uint32_t num_views, float depth_factor,
                                      uint32_t background_rgba, void *dev_workspace, uint64_t workspace_bytes);
