@@ -8,11 +8,14 @@
 // while a batch in flight reads them).  pcr_server_step is the loop body:
 // it retires batches whose completion event has fired, then forms new
 // batches from the queued requests, in arrival order, as long as an
-// in-flight batch, frame slots and cloud memory are free.  Batches rotate over
-// the server's streams (one per in-flight batch unless fewer are asked for),
-// so with several streams they overlap on the GPU; requests that arrive
-// while others render join the next batch.  A request's result stays in its
-// frame slot until the caller releases the ticket.
+// in-flight batch, frame slots and cloud memory are free.  A batch in which
+// some cloud has two views or more runs on the batched renderer; one whose
+// views all have different clouds runs each view through the single-view
+// kernels.  Batches rotate over the server's streams (one per in-flight
+// batch unless fewer are asked for), so with several streams they overlap
+// on the GPU; requests that arrive while others render join the next batch.
+// A request's result stays in its frame slot until the caller releases the
+// ticket.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
