@@ -44,8 +44,9 @@ UNIT = "points/s"
 POINT_BYTES = 16
 FALLBACK_HBM_GBS = 6800.0
 # The timed frame's variant.  Every exact variant leaves the same buffer; on
-# GB300 the early depth test alone is the fastest of them on the scan scene
-# (the sweep in the JSON line times all of them).
+# GB300 the early depth test alone is the fastest of them on the scan scene,
+# or within 1% of early-z with warp deduplication (the sweep in the JSON line
+# times all of them).
 HEADLINE_VARIANT = "early-z"
 # The HQ frames' depth-pass variant (the colour pass sums colours inside the
 # warp for every variant but atomicMin): with the early test the depth pass
