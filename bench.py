@@ -95,6 +95,19 @@ def parse_args(argv=None):
 # distributed plumbing (replicas only)
 # ---------------------------------------------------------------------------
 
+def sections(args, world: int) -> dict:
+    """Which parts of the run take place.  The timed frame always runs; the
+    HQ frames and e2e follow their flags at any N.  The characterisations of
+    one GPU (the variant sweep and 63-bit reorders, the smaller workloads,
+    the batched and served workloads) and the CPU baseline run at N = 1 only:
+    under torchrun every rank would repeat them on its own GPU, and the
+    served workload alone holds about 18 GB of host memory per rank."""
+    single = world == 1
+    return {"hq": not args.no_hq, "e2e": not args.no_e2e, "sweep": single and not args.no_sweep,
+            "batched": single and not args.no_batched, "small": single and not args.no_small,
+            "served": single and not args.no_served, "cpu": single and not args.no_cpu}
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -507,7 +520,8 @@ def run_ours(args, cfg):
         torch.cuda.synchronize()
         reorder_ms[name] = e0.elapsed_time(e1)
         orders[name] = buf
-    if not args.no_sweep:
+    run = sections(args, world)
+    if run["sweep"]:
         # the paper's 21-level Morton code (63 bits): timed, not kept
         for name, mode in (("morton63", pcr.PCR_ORDER_MORTON63),
                            ("morton63_shuffle128", pcr.PCR_ORDER_MORTON63_SHUFFLE128)):
@@ -604,26 +618,26 @@ def run_ours(args, cfg):
         pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ1R, fb["image"], 0)
 
     pcr.pcr_set_hq1r_buffer(h, fb["hq1r_primary"])
-    hq_ms = None if args.no_hq else time_loop(hq_frame, stream, reps=max(5, min(K, 50)), warm=3)
-    hq1r_ms = None if args.no_hq else time_loop(hq1r_frame, stream, reps=max(5, min(K, 50)), warm=3)
+    hq_ms = time_loop(hq_frame, stream, reps=max(5, min(K, 50)), warm=3) if run["hq"] else None
+    hq1r_ms = time_loop(hq1r_frame, stream, reps=max(5, min(K, 50)), warm=3) if run["hq"] else None
 
     # --- end to end through the C ABI with host buffers ---------------------------
     e2e = None
-    if not args.no_e2e:
+    if run["e2e"]:
         e2e = run_e2e(h, pcr, points, n, fb, W, H, variant, stream, dist, dev, world,
                       steps=max(3, min(K, 20)), warm=2)
         pcr.pcr_upload_points(h, points, n)
 
     # --- sweep: variants x orders x cameras ---------------------------------------
     sweep = None
-    if not args.no_sweep:
+    if run["sweep"]:
         sweep = run_sweep(h, pcr, orders, views, n, fb, stream)
         pcr.pcr_upload_points(h, points, n)
         set_view(view)
 
     # --- batched: 8 clouds x 8 views, per-view calls vs one graph -----------------
     batched = None
-    if not args.no_batched:
+    if run["batched"]:
         batched = run_batched(h, pcr, stream, dev, reps=max(3, min(K, 10)))
         pcr.pcr_upload_points(h, points, n)
         set_view(view)
@@ -631,7 +645,7 @@ def run_ours(args, cfg):
 
     # --- CPU oracle baseline (rank 0, one GPU) -------------------------------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and run["cpu"]:
         from oracle import build as oracle_build
         oracle_build.build()
         cpu = oracle_baseline(lambda k: points[cpu_sample_indices(n, k).to(dev)].cpu().numpy(), n, view,
@@ -639,15 +653,15 @@ def run_ours(args, cfg):
 
     # --- the smaller workloads (1M and 50M points), GPU frame and CPU oracle --
     small = None
-    if not args.no_small:
-        small = run_small_configs(h, pcr, stream, dev, with_cpu=(rank == 0 and world == 1 and not args.no_cpu))
+    if run["small"]:
+        small = run_small_configs(h, pcr, stream, dev, with_cpu=(rank == 0 and run["cpu"]))
         pcr.pcr_upload_points(h, points, n)
         set_view(view)
         pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
 
     # --- served: Poisson request stream, continuous batching vs plain launches --
     served = served_sat = None
-    if not args.no_served:
+    if run["served"]:
         orders.clear()
         points = cloud = None
         torch.cuda.empty_cache()

@@ -85,3 +85,15 @@ def test_default_arguments_meet_the_timing_rules():
     assert args.gpus == 1 and args.impl == "ours" and args.config == "scan800M"
     assert args.warmup >= 3 and args.steps >= 50
     assert bench.HQ_VARIANT in ("early-z", "dedup+early-z")
+
+
+def test_sections_at_one_and_several_gpus():
+    args = bench.parse_args([])
+    one = bench.sections(args, 1)
+    assert all(one.values())
+    many = bench.sections(args, 4)
+    assert many["hq"] and many["e2e"]
+    assert not any(many[k] for k in ("sweep", "batched", "small", "served", "cpu"))
+    quiet = bench.sections(bench.parse_args(["--no-hq", "--no-e2e", "--no-served", "--no-cpu"]), 1)
+    assert not quiet["hq"] and not quiet["e2e"] and not quiet["served"] and not quiet["cpu"]
+    assert quiet["sweep"] and quiet["batched"] and quiet["small"]
