@@ -61,3 +61,20 @@ def test_null_context_is_rejected(lib):
     out = ctypes.c_uint64()
     assert lib.pcr_reorder_workspace_size(5, None) == -1
     assert lib.pcr_reorder_workspace_size(5, ctypes.byref(out)) == 0
+
+
+def test_host_only_checks_of_the_later_entry_points(lib):
+    """Argument checks that run before any CUDA call: a NULL context or
+    output pointer is refused with PCR_ERR_ARG (-1); the batch sizes are
+    host computations."""
+    import ctypes
+    assert lib.pcr_upload_points_mapped(None, None, 0) == -1
+    assert lib.pcr_render_rgb(None, 1, 1) == -1
+    assert lib.pcr_set_lock_buffer(None, None, 0) == -1
+    assert lib.pcr_render_hq1r(None, ctypes.c_float(1.01), 1, 1) == -1
+    assert lib.pcr_server_create(None, None, None) == -1
+    assert lib.pcr_batch_workspace_size(None) == -1
+    assert lib.pcr_batch_num_configs(None) == -1
+    size, count = ctypes.c_uint64(), ctypes.c_int()
+    assert lib.pcr_batch_workspace_size(ctypes.byref(size)) == 0 and size.value % 256 == 0 and size.value > 0
+    assert lib.pcr_batch_num_configs(ctypes.byref(count)) == 0 and count.value >= 1
