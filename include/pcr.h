@@ -519,7 +519,14 @@ PCR_API pcr_status pcr_server_stats_get(pcr_server *srv, pcr_server_stats *out);
  *     nothing.
  *   - The first call on a device looks up the array's device address, with
  *     the context's device current.  Make that first call before any stream
- *     capture.
+ *     capture.  The address stays cached for the process; creating a context
+ *     (pcr_create) for the device drops it, so after a device reset
+ *     (cudaDeviceReset) create a new context before calling again.
+ *   - Treat the first call on a device as a warm-up.  Under lazy module
+ *     loading (CUDA's default) the library's device code, this array
+ *     included, is loaded onto a device only when it is first needed there,
+ *     and that load takes device memory on the driver's side and may
+ *     synchronise the device.  Later calls take no device memory.
  *   - All calls on a device share the one array and leave their scratch data
  *     in it.  No call needs it cleared: every scratch word a call reads, it
  *     has written first.
@@ -532,6 +539,33 @@ PCR_API pcr_status pcr_server_stats_get(pcr_server *srv, pcr_server_stats *out);
  * address cannot be obtained. */
 PCR_API pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx *ctx, void *dev_points, uint64_t n, uint64_t seed,
                                                          int mode, uint32_t *dev_perm_out);
+
+/* Check, on the device, the screen division every geometry kernel uses
+ * (Sec. 3.1's projection), against the device's IEEE operations.  The
+ * kernels divide both clip coordinates by w through one reciprocal per point,
+ * y = RN(1/w), got from one Newton step on the hardware estimate, and correct
+ * each quotient q0 = RN(c y) to RN(q0 + (c - q0 w) y) (Markstein, IBM J. Res.
+ * Dev. 34(1), 1990), for w in [2^-40, 2^40); other w take the IEEE division.
+ * A diagnostic: nothing on the render path calls it.
+ *   - Every w bit pattern in [w_first, w_first + w_count) that lies in the
+ *     window has its reciprocal compared with the IEEE reciprocal:
+ *     out[0] = mismatches.
+ *   - Every pair (w, c), w from that range and in the window, c = dev_c_bits[j]
+ *     (device array of c_count float bit patterns) or, when dev_c_bits is
+ *     NULL, c = c_first + j * c_step (bit patterns), j < c_count:
+ *     out[1] = quotients that differ from IEEE c / w where
+ *     2^-30 <= |c / w| <= 2^126 (out[3] = such pairs); out[2] = screen
+ *     coordinates (c / w * 0.5 + 0.5) * size that differ from the ones of the
+ *     IEEE quotient, counting a pair as equal when both are culled
+ *     (out[4] = pairs checked).
+ * Synchronises the context's stream.  The counters live in the library's
+ * device code: calls must not overlap on one device.
+ * Errors: PCR_ERR_ARG for a NULL ctx or out, c_count > 0 with a zero c_step
+ * and no array, or size not in (0, 16384]; PCR_ERR_CUDA if a launch or copy
+ * fails. */
+PCR_API pcr_status pcr_check_division(pcr_ctx *ctx, uint32_t w_first, uint32_t w_count, const uint32_t *dev_c_bits,
+                                      uint32_t c_first, uint32_t c_count, uint32_t c_step, float size,
+                                      uint64_t out[5]);
 
 /* Static, human-readable name of a status code. */
 PCR_API const char *pcr_status_string(pcr_status status);

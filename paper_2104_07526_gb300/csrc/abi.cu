@@ -97,6 +97,7 @@ pcr_status pcr_create(pcr_ctx** out, int device) {
   if (!c) return PCR_ERR_CUDA;
   c->dev.id = device;
   c->dev.num_sms = sms;
+  pcr::forget_noalloc_scratch(device);
   *out = c;
   return PCR_OK;
 }
@@ -487,6 +488,16 @@ pcr_status pcr_graph_launch(pcr_ctx* ctx, void* graph_exec) {
 pcr_status pcr_graph_destroy(void* graph_exec) {
   if (graph_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec));
   return PCR_OK;
+}
+
+pcr_status pcr_check_division(pcr_ctx* ctx, uint32_t w_first, uint32_t w_count, const uint32_t* dev_c_bits,
+                              uint32_t c_first, uint32_t c_count, uint32_t c_step, float size, uint64_t out[5]) {
+  if (!ctx || !out || (c_count > 0 && !dev_c_bits && c_step == 0) || !(size > 0.0f && size <= 16384.0f))
+    return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  return from_cuda(pcr::check_division(w_first, w_count, dev_c_bits, c_first, c_count, c_step, size, out,
+                                       ctx->stream, ctx->dev));
 }
 
 const char* pcr_status_string(pcr_status status) {

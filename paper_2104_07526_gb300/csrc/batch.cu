@@ -84,9 +84,14 @@ __device__ __forceinline__ uint32_t last_not_above(uint32_t count, uint64_t x, K
 }
 
 // Walk the chunks (32 * U points) of every pass of a phase; f(group, r,
-// base, ok) for each chunk of this warp.
-template <int U, class F>
+// base, ok) for each chunk of this warp.  Slot u of lane l holds point
+// slot_index<U, L>(base, u) of the group's cloud (the layouts of the
+// single-view kernels); in the consecutive layout, whole chunks of a 32-byte
+// aligned cloud load their records in 32-byte pairs.
+template <int U, int L, class F>
 __device__ __forceinline__ void for_each_batch_chunk(const Shared& sh, int phase, uint64_t pol, F&& f) {
+  static_assert(L == kInterleaved || U % 2 == 0, "records load in pairs");
+  constexpr uint32_t kLaneStep = L == kConsecutive ? U : 1;
   const uint64_t warps_per_block = blockDim.x >> 5;
   const uint64_t warp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const uint64_t nwarps = gridDim.x * warps_per_block;
@@ -99,14 +104,22 @@ __device__ __forceinline__ void for_each_batch_chunk(const Shared& sh, int phase
         last_not_above(sh.hdr.num_groups[phase], slot0, [&](uint32_t i) { return sh.groups[i].first_slot; });
     const BatchGroup& grp = sh.groups[gi];
     const BatchCloud& cl = sh.clouds[grp.cloud];
-    const uint32_t base = static_cast<uint32_t>(slot0 - grp.first_slot) + lane;
+    const uint64_t start = slot0 - grp.first_slot;
+    const uint32_t base = static_cast<uint32_t>(start) + kLaneStep * lane;
     uint4 r[U];
     bool ok[U];
+    if (L == kConsecutive && start + kChunk <= cl.n && (reinterpret_cast<uintptr_t>(cl.pts) & 31u) == 0) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint64_t i = static_cast<uint64_t>(base) + 32ull * u;
-      ok[u] = i < cl.n;
-      r[u] = ok[u] ? load_point_stream(cl.pts + i, pol) : make_uint4(0u, 0u, 0u, 0u);
+      for (int u = 0; u < U; u += 2) load_pair_stream(cl.pts + base + u, pol, r[u], r[u + 1]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) ok[u] = true;
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint64_t i = slot_index<U, L>(base, u);
+        ok[u] = i < cl.n;
+        r[u] = ok[u] ? load_point_stream(cl.pts + i, pol) : make_uint4(0u, 0u, 0u, 0u);
+      }
     }
     f(grp, r, base, ok);
   }
@@ -115,15 +128,11 @@ __device__ __forceinline__ void for_each_batch_chunk(const Shared& sh, int phase
 template <int U>
 __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&r)[U], const bool (&ok)[U],
                                             uint32_t (&pix)[U], float (&w)[U], bool (&vis)[U]) {
+  // project every slot (a slot past the cloud holds zeros), then mask: no
+  // branch per slot, so the slots' work interleaves
+  project_slots<U>(vp, r, pix, w, vis);
 #pragma unroll
-  for (int u = 0; u < U; ++u) {
-    pix[u] = 0;
-    w[u] = 0.0f;
-    // project every slot (a slot past the cloud holds zeros), then mask: no
-    // branch per slot, so the slots' divisions interleave
-    vis[u] = project(vp, __uint_as_float(r[u].x), __uint_as_float(r[u].y), __uint_as_float(r[u].z), pix[u], w[u]) &&
-             ok[u];
-  }
+  for (int u = 0; u < U; ++u) vis[u] = vis[u] && ok[u];
 }
 
 // Phase 1: per view of the pass, basic key and HQ depth, each with the
@@ -136,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restr
   load_tables(tables, 0, sh);
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_batch_chunk<U>(sh, 0, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t base,
+  for_each_batch_chunk<U, kInterleaved>(sh, 0, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t base,
                                                  const bool(&ok)[U]) {
     for (uint32_t i = grp.first; i < grp.first + grp.count; ++i) {
       const BatchView& bv = sh.views[sh.order[i]];
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restr
       if (basic) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
-          emit_key<PCR_VARIANT_EARLYZ>(bv.keys, vis[u], pix[u], w[u], base + 32u * u, seen_key[u], pol_fb);
+          emit_key<PCR_VARIANT_EARLYZ>(bv.keys, vis[u], pix[u], make_key(w[u], slot_index<U, kInterleaved>(base, u)), seen_key[u], pol_fb);
       }
       if (hq) {
 #pragma unroll
@@ -178,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_phase2(const Tables* __re
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
   const float factor = sh.hdr.depth_factor;
-  for_each_batch_chunk<U>(sh, 1, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t,
+  for_each_batch_chunk<U, kConsecutive>(sh, 1, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t,
                                                  const bool(&ok)[U]) {
     for (uint32_t i = grp.first; i < grp.first + grp.count; ++i) {
       const BatchView& bv = sh.views[sh.order[i]];
@@ -186,15 +195,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_batch_phase2(const Tables* __re
       float w[U];
       bool vis[U];
       project_all<U>(bv.vp, r, ok, pix, w, vis);
-      uint32_t d[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(bv.depth + pix[u]) : 0u;
       bool contrib[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
-      const bool agg = aggregate_chunk(contrib[0], pix[0]);
-#pragma unroll
-      for (int u = 0; u < U; ++u) emit_color(bv.rg, bv.ba, contrib[u], pix[u], r[u].w, pol_fb, agg);
+      contributes<U>(bv.depth, factor, pix, w, vis, contrib);
+      emit_colors<U, true>(bv.rg, bv.ba, contrib, pix, r, pol_fb);
     }
   });
 }

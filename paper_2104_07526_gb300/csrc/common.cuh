@@ -17,6 +17,12 @@
 // The projection has no branch: every slot of a chunk is projected, and
 // culled slots drop out at the one visibility test.  The compiler can then
 // interleave the divisions of a lane's slots.
+//
+// project_pair computes the same results for two slots at once (see there):
+// Blackwell's paired float32 instructions (each half rounded on its own, as
+// the scalar instruction rounds it) for the matrix rows and the screen
+// transform, and one reciprocal per slot shared by both screen divisions,
+// with Markstein's correction making each quotient the IEEE one.
 #pragma once
 
 #include <cstdint>
@@ -64,6 +70,151 @@ __device__ __forceinline__ bool project(const ViewParams& v, float x, float y, f
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Two slots at once.
+// ---------------------------------------------------------------------------
+
+// Two floats in one 64-bit register pair: slot a in the low half, slot b in
+// the high half.  mul/fma .rn.f32x2 round each half on its own, exactly as
+// the scalar .rn instruction would (no flush to zero).
+using f32x2 = unsigned long long;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_bcast(float x) { return f2_pack(x, x); }
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+__device__ __forceinline__ float add_rn(float a, float b) {
+  float r;
+  asm("add.rn.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+// One matrix row for two slots: the three products as paired instructions,
+// the sums as scalar add.rn on the halves.  Paired sums are not used: ptxas
+// fuses a paired product into a following paired add (or into fma with a
+// factor of one) despite the .rn modifier, which would change roundings.
+// A scalar add.rn is never fused.
+__device__ __forceinline__ f32x2 row_dot2(const float r[4], f32x2 x, f32x2 y, f32x2 z) {
+  float a0, b0, a1, b1, a2, b2;
+  f2_unpack(f2_mul(f2_bcast(r[0]), x), a0, b0);
+  f2_unpack(f2_mul(f2_bcast(r[1]), y), a1, b1);
+  f2_unpack(f2_mul(f2_bcast(r[2]), z), a2, b2);
+  return f2_pack(add_rn(add_rn(add_rn(a0, a1), a2), r[3]), add_rn(add_rn(add_rn(b0, b1), b2), r[3]));
+}
+
+// Hardware reciprocal estimate (within 1 ulp of 1/w).
+__device__ __forceinline__ float rcp_estimate(float w) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(w));
+  return r;
+}
+
+// w for which the reciprocal path below is exact: [2^-40, 2^40).  Every
+// quantity it forms is then a normal number or an exact zero, or the point
+// is culled either way (below).
+constexpr uint32_t kRcpWindowLo = 0x2B800000u;                  // bits of 2^-40
+constexpr uint32_t kRcpWindowSpan = 0x53800000u - kRcpWindowLo;  // up to bits of 2^40
+
+__device__ __forceinline__ bool in_rcp_window(float w) {
+  return __float_as_uint(w) - kRcpWindowLo < kRcpWindowSpan;
+}
+
+// RN(1/w) for both halves: one Newton step with fused operations on the
+// estimate y0, y1 = y0 + y0 (1 - w y0).  nw holds -w.
+__device__ __forceinline__ f32x2 reciprocal2(f32x2 nw, float wa, float wb) {
+  const f32x2 y0 = f2_pack(rcp_estimate(wa), rcp_estimate(wb));
+  return f2_fma(y0, f2_fma(nw, y0, f2_bcast(1.0f)), y0);
+}
+
+// c / w rounded to nearest even, given y = RN(1/w) (Markstein, IBM J. Res.
+// Dev. 34(1), 1990): q0 = RN(c y) lies within one ulp of c / w, so the
+// remainder r = c - q0 w is exact in one fused operation, and RN(q0 + r y)
+// is the correctly rounded quotient.  That holds while nothing overflows or
+// underflows: for w in the window and |c / w| >= 2^-30 every term is normal
+// or an exact zero.  Smaller quotients come out below 2^-27 in magnitude, and
+// every such quotient gives ndc * 0.5 + 0.5 = 0.5 exactly, as the exact one
+// does.  Where c y overflows (|c / w| near 2^128) the result is infinite or
+// NaN, and the point is culled, as with the exact quotient (|c / w| > 2).
+__device__ __forceinline__ f32x2 quotient2(f32x2 c, f32x2 nw, f32x2 y) {
+  const f32x2 q0 = f2_mul(c, y);
+  return f2_fma(f2_fma(q0, nw, c), y, q0);
+}
+
+// project() for slots a and b: the same results, bit for bit.  The matrix
+// rows are summed in the same order with the same roundings; the screen
+// transform is the same fused multiply-add and product; each quotient equals
+// the IEEE one (quotient2).  A slot whose w is valid but outside the window
+// takes the IEEE divisions.  pa / pb are meaningful only when va / vb.
+__device__ __forceinline__ void project_pair(const ViewParams& v, const uint4& ra, const uint4& rb, uint32_t& pa,
+                                             uint32_t& pb, float& wa, float& wb, bool& va, bool& vb) {
+  const f32x2 x = f2_pack(__uint_as_float(ra.x), __uint_as_float(rb.x));
+  const f32x2 y = f2_pack(__uint_as_float(ra.y), __uint_as_float(rb.y));
+  const f32x2 z = f2_pack(__uint_as_float(ra.z), __uint_as_float(rb.z));
+  const f32x2 w2 = row_dot2(v.r3, x, y, z);
+  const f32x2 cx = row_dot2(v.r0, x, y, z);
+  const f32x2 cy = row_dot2(v.r1, x, y, z);
+  f2_unpack(w2, wa, wb);
+  const f32x2 nw = f2_mul(w2, f2_bcast(-1.0f));
+  const f32x2 rw = reciprocal2(nw, wa, wb);
+  float sxa, sxb, sya, syb;
+  f2_unpack(f2_mul(f2_fma(quotient2(cx, nw, rw), f2_bcast(0.5f), f2_bcast(0.5f)), f2_bcast(v.fw)), sxa, sxb);
+  f2_unpack(f2_mul(f2_fma(quotient2(cy, nw, rw), f2_bcast(0.5f), f2_bcast(0.5f)), f2_bcast(v.fh)), sya, syb);
+  const bool oka = __float_as_uint(wa) - 1u < 0x7F7FFFFFu;
+  const bool okb = __float_as_uint(wb) - 1u < 0x7F7FFFFFu;
+  const bool slowa = oka && !in_rcp_window(wa);
+  const bool slowb = okb && !in_rcp_window(wb);
+  if (slowa || slowb) {
+    float cxa, cxb, cya, cyb;
+    f2_unpack(cx, cxa, cxb);
+    f2_unpack(cy, cya, cyb);
+    if (slowa) {
+      sxa = to_screen(cxa, wa, v.fw);
+      sya = to_screen(cya, wa, v.fh);
+    }
+    if (slowb) {
+      sxb = to_screen(cxb, wb, v.fw);
+      syb = to_screen(cyb, wb, v.fh);
+    }
+  }
+  const uint32_t bw = __float_as_uint(v.fw), bh = __float_as_uint(v.fh);
+  va = oka && __float_as_uint(sxa) < bw && __float_as_uint(sya) < bh;
+  vb = okb && __float_as_uint(sxb) < bw && __float_as_uint(syb) < bh;
+  pa = __float2uint_rd(sxa) + __float2uint_rd(sya) * v.width;
+  pb = __float2uint_rd(sxb) + __float2uint_rd(syb) * v.width;
+}
+
+// Every slot of a chunk: pairs, then a last single slot when U is odd.
+// pix[u] is meaningful only when vis[u].
+template <int U>
+__device__ __forceinline__ void project_slots(const ViewParams& v, const uint4 (&r)[U], uint32_t (&pix)[U],
+                                              float (&w)[U], bool (&vis)[U]) {
+#pragma unroll
+  for (int u = 0; u + 1 < U; u += 2)
+    project_pair(v, r[u], r[u + 1], pix[u], pix[u + 1], w[u], w[u + 1], vis[u], vis[u + 1]);
+  if constexpr (U % 2 == 1) {
+    pix[U - 1] = 0;
+    w[U - 1] = 0.0f;
+    vis[U - 1] = project(v, __uint_as_float(r[U - 1].x), __uint_as_float(r[U - 1].y), __uint_as_float(r[U - 1].z),
+                         pix[U - 1], w[U - 1]);
+  }
+}
+
 // 16-byte point load that streams past L1 and marks the line first for
 // eviction in L2, so the point stream does not push the framebuffer out.
 // The point buffer is read-only while a kernel runs, so the load is a pure
@@ -74,6 +225,14 @@ __device__ __forceinline__ uint4 load_point_stream(const uint4* p, uint64_t poli
       : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
       : "l"(p), "l"(policy));
   return r;
+}
+
+// Two neighbouring 16-byte records (32-byte aligned) in one 32-byte load,
+// with the same caching as load_point_stream.
+__device__ __forceinline__ void load_pair_stream(const uint4* p, uint64_t policy, uint4& a, uint4& b) {
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], %9;"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+      : "l"(p), "l"(policy));
 }
 
 __device__ __forceinline__ uint64_t policy_evict_first() {

@@ -12,10 +12,6 @@
 namespace pcr {
 namespace geom {
 
-// HQ colour pass: above this many runs of equal pixels in a warp row the
-// warp adds directly instead of aggregating.
-constexpr int kAggregateMaxRuns = 12;
-
 // Key payloads (Sec. 3.1): the point index below the depth bits (the
 // colour is looked up in the resolve), or, as Listing "basic" prints it, the
 // 24-bit colour below depth bits shifted by 24.
@@ -34,10 +30,20 @@ __device__ __forceinline__ unsigned long long make_payload_key(float w, uint32_t
   }
 }
 
+// Depth bits and payload of a key.
+template <int P>
+__device__ __forceinline__ uint32_t key_depth(unsigned long long key) {
+  return static_cast<uint32_t>(key >> (P == kPayloadRgb ? 24 : 32));
+}
+template <int P>
+__device__ __forceinline__ uint32_t key_payload(unsigned long long key) {
+  return static_cast<uint32_t>(key) & (P == kPayloadRgb ? 0xFFFFFFu : 0xFFFFFFFFu);
+}
+
 // The lane of `tied` (the lanes of a group whose depth equals the group's
 // minimum; `mine` says whether this lane is one of them) that holds the
-// group's smallest key.  With the index payload the index grows with the
-// lane inside a row of the chunk, so it is the lowest tied lane; with the
+// group's smallest key.  With the index payload the indices a row holds grow
+// with the lane, so it is the lowest tied lane; with the
 // colour payload it is the lowest tied lane with the smallest colour, found
 // by the tied lanes alone (others get 32, no lane).
 template <int P>
@@ -52,45 +58,70 @@ __device__ __forceinline__ uint32_t min_key_lane(uint32_t tied, bool mine, uint3
   }
 }
 
+// Chunks of 32 * U consecutive points, in one of two layouts:
+//   kInterleaved: slot u of lane l holds point c * 32U + l + 32u.  Each
+//     load instruction covers 512 contiguous bytes, and a row (one slot of
+//     every lane) is 32 neighbouring points.  The key and depth passes use
+//     it: the early reads of a row then meet few distinct pixels.
+//   kConsecutive: slot u of lane l holds point c * 32U + U l + u.  Each lane
+//     takes U neighbouring points, so points that share a pixel in a
+//     coherent vertex order mostly meet inside one lane, where merging them
+//     costs no warp-wide operation.  The grouped colour passes use it.  With V8
+//     (the buffer 32-byte aligned, U even) a lane loads its records as U / 2
+//     32-byte vectors; a warp's loads together read the chunk's bytes once.
+enum Layout { kInterleaved = 0, kConsecutive = 1 };
+
+template <int U, int L>
+__device__ __forceinline__ uint32_t slot_index(uint32_t base, int u) {
+  return base + static_cast<uint32_t>(L == kConsecutive ? u : 32 * u);
+}
+
 // Walk the point chunks of this warp.  For each chunk, f(r, base, full)
-// gets the U records of this lane (slot u holds point base + 32u), and
-// `full` as a compile-time flag: true when every slot of the chunk lies
+// gets the U records of this lane (slot u holds point slot_index(base, u)),
+// and `full` as a compile-time flag: true when every slot of the chunk lies
 // inside the cloud.  Every lane of the warp calls f the same number of times,
 // so f may use warp-collective operations.
-template <int U, class F>
+template <int U, int L, bool V8, class F>
 __device__ __forceinline__ void for_each_chunk(const uint4* __restrict__ pts, uint32_t n, uint64_t pol, F&& f) {
+  static_assert(!V8 || (L == kConsecutive && U % 2 == 0), "32-byte loads take a lane's records in pairs");
   const uint64_t warps_per_block = blockDim.x >> 5;
   const uint64_t warp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
   const uint64_t nwarps = gridDim.x * warps_per_block;
   constexpr uint64_t kChunk = 32ull * U;
+  constexpr uint32_t kLaneStep = L == kConsecutive ? U : 1;
   const uint64_t nfull = n / kChunk;
   const uint32_t lane = lane_id();
   uint64_t c = warp;
   for (; c < nfull; c += nwarps) {
-    const uint32_t base = static_cast<uint32_t>(c * kChunk) + lane;
+    const uint32_t base = static_cast<uint32_t>(c * kChunk) + kLaneStep * lane;
     uint4 r[U];
+    if constexpr (V8) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) r[u] = load_point_stream(pts + base + 32u * u, pol);
+      for (int u = 0; u < U; u += 2) load_pair_stream(pts + base + u, pol, r[u], r[u + 1]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) r[u] = load_point_stream(pts + slot_index<U, L>(base, u), pol);
+    }
     f(r, base, std::true_type{});
   }
   if (c == nfull && nfull * kChunk < n) {  // the one ragged chunk, if any
-    const uint64_t base = c * kChunk + lane;
+    const uint32_t base = static_cast<uint32_t>(c * kChunk) + kLaneStep * lane;
     uint4 r[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const uint64_t i = base + 32ull * u;
+      const uint64_t i = static_cast<uint64_t>(base) + (L == kConsecutive ? u : 32ull * u);
       r[u] = (i < n) ? load_point_stream(pts + i, pol) : make_uint4(0u, 0u, 0u, 0u);
     }
-    f(r, static_cast<uint32_t>(base), std::false_type{});
+    f(r, base, std::false_type{});
   }
 }
 
-template <class Full>
+template <int U, int L, class Full>
 __device__ __forceinline__ bool slot_in_range(uint32_t base, int u, uint32_t n, Full) {
   if constexpr (Full::value) {
     return true;
   } else {
-    return static_cast<uint64_t>(base) + 32ull * u < n;
+    return static_cast<uint64_t>(base) + (L == kConsecutive ? u : 32ull * u) < n;
   }
 }
 
@@ -107,13 +138,11 @@ __host__ __device__ constexpr bool reads_early() {
   return V == PCR_VARIANT_EARLYZ || V == PCR_VARIANT_DEDUP_EARLYZ || V == PCR_VARIANT_REDUCE_EARLYZ;
 }
 
-// One point slot after projection.  `payload` is the point index or its
-// rgba word (P); `seen` is this lane's earlier read of its pixel (variants
-// with the early test only).
+// One point slot after projection: its key (payload P), and `seen`, this
+// lane's earlier read of its pixel (variants with the early test only).
 template <int V, int P = kPayloadIndex>
-__device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix, float w,
-                                         uint32_t payload, unsigned long long seen, uint64_t pol) {
-  const unsigned long long key = make_payload_key<P>(w, payload);
+__device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix,
+                                         unsigned long long key, unsigned long long seen, uint64_t pol) {
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
     // Sec. 3.1: atomicMin(framebuffer[pixelID], point)
     if (vis) red_min_u64(fb + pix, key, pol);
@@ -128,10 +157,10 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
     // warp even when depths tie.
     const uint32_t tag = vis ? pix : kNoPixel;
     const uint32_t peers = __match_any_sync(kFullMask, tag);
-    const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
+    const uint32_t hi = vis ? key_depth<P>(key) : 0xFFFFFFFFu;
     const uint32_t hmin = __reduce_min_sync(peers, hi);
     const uint32_t tied = __ballot_sync(kFullMask, hi == hmin) & peers;
-    const uint32_t first = min_key_lane<P>(tied, hi == hmin, payload);
+    const uint32_t first = min_key_lane<P>(tied, hi == hmin, key_payload<P>(key));
     if (vis && lane_id() == first) red_min_u64(fb + pix, key, pol);
   } else if constexpr (V == PCR_VARIANT_DEDUP_EARLYZ) {
     // Sec. 3.4 with Sec. 3.2, tests swapped: every visible lane has read its
@@ -144,12 +173,12 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
     const uint32_t active = __ballot_sync(kFullMask, want);
     if (active != 0 && want) {
       const uint32_t peers = __match_any_sync(active, pix);
-      const uint32_t hi = __float_as_uint(w);
+      const uint32_t hi = key_depth<P>(key);
       const uint32_t hmin = __reduce_min_sync(peers, hi);
       uint32_t first;
       if constexpr (P == kPayloadRgb) {
         const uint32_t tied = __ballot_sync(peers, hi == hmin);
-        first = min_key_lane<P>(tied, hi == hmin, payload);
+        first = min_key_lane<P>(tied, hi == hmin, key_payload<P>(key));
       } else {
         first = __reduce_min_sync(peers, hi == hmin ? lane_id() : 32u);
       }
@@ -164,10 +193,10 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
     __match_all_sync(kFullMask, tag, &all_equal);
     bool write = vis;
     if (all_equal) {
-      const uint32_t hi = vis ? __float_as_uint(w) : 0xFFFFFFFFu;
+      const uint32_t hi = vis ? key_depth<P>(key) : 0xFFFFFFFFu;
       const uint32_t hmin = __reduce_min_sync(kFullMask, hi);
       const uint32_t tied = __ballot_sync(kFullMask, hi == hmin);
-      write = vis && lane_id() == min_key_lane<P>(tied, hi == hmin, payload);
+      write = vis && lane_id() == min_key_lane<P>(tied, hi == hmin, key_payload<P>(key));
     } else {
       const uint32_t other_tag = __shfl_xor_sync(kFullMask, tag, 1);
       const unsigned long long other_key = __shfl_xor_sync(kFullMask, key, 1);
@@ -212,43 +241,108 @@ __device__ __forceinline__ void emit_depth(uint32_t* __restrict__ depth, bool vi
   }
 }
 
-// Colour pass (Listing "hqs_render"): whether the warp sums its colours
-// before adding, decided once per chunk from its first row of points: the
-// runs of equal pixels among neighbouring contributing lanes.  With at most
-// kAggregateMaxRuns runs (coherent orders: neighbours share pixels) the warp
-// aggregates; otherwise (shuffled orders) matching would cost more than it
-// saves.  The rows of a chunk are 32 points apart in the same order, so the
-// first row speaks for the others.  Warp-uniform.
-__device__ __forceinline__ bool aggregate_chunk(bool contrib0, uint32_t pix0) {
-  const uint32_t tag = contrib0 ? pix0 : kNoPixel;
-  const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
-  const uint32_t starts = __ballot_sync(kFullMask, contrib0 && (lane_id() == 0 || prev != tag));
-  return __popc(starts) <= kAggregateMaxRuns;
+// Sec. 3.5 colour-pass test: a visible point contributes when
+// w <= fl(depth * factor), with the depth its pixel holds after the depth
+// pass.  The products of two slots form one paired instruction (each half
+// rounded as the scalar product).
+template <int U>
+__device__ __forceinline__ void contributes(const uint32_t* __restrict__ depth, float factor, const uint32_t (&pix)[U],
+                                            const float (&w)[U], const bool (&vis)[U], bool (&contrib)[U]) {
+  float d[U], thr[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) d[u] = vis[u] ? __uint_as_float(__ldg(depth + pix[u])) : 0.0f;
+#pragma unroll
+  for (int u = 0; u + 1 < U; u += 2) f2_unpack(f2_mul(f2_pack(d[u], d[u + 1]), f2_bcast(factor)), thr[u], thr[u + 1]);
+  if constexpr (U % 2 == 1) thr[U - 1] = __fmul_rn(d[U - 1], factor);
+#pragma unroll
+  for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= thr[u];
 }
 
-// A visible point contributes when w <= depth * factor, adding (r << 32 | g)
-// and (b << 32 | 1).  With `agg` (warp-uniform), lanes that contribute to
-// the same pixel first sum their colours inside the warp (at most 32 * 255
-// per channel, so r | g << 16 and b | count << 16 cannot carry), then one
-// lane adds.
-__device__ __forceinline__ void emit_color(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
-                                           bool contrib, uint32_t pix, uint32_t rgba, uint64_t pol, bool agg) {
-  // r | g << 16 and b | 1 << 16, each one byte permute of the rgba word
-  uint32_t s_rg = __byte_perm(rgba, 0u, 0x4140u);
-  uint32_t s_bc = __byte_perm(rgba, 0x100u, 0x4542u);
-  bool add = contrib;
-  if (agg) {
-    const uint32_t active = __ballot_sync(kFullMask, contrib);
-    if (contrib) {
-      const uint32_t peers = __match_any_sync(active, pix);
-      s_rg = __reduce_add_sync(peers, s_rg);
-      s_bc = __reduce_add_sync(peers, s_bc);
-      add = lane_id() == static_cast<uint32_t>(__ffs(peers) - 1);
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Colour pass grouping (Listing "hqs_render" adds (r << 32 | g) and
+// (b << 32 | 1) per contributing point; sums do not depend on grouping).
+// With AGG:
+//   - a slot whose pixel equals the previous slot's, both contributing,
+//     joins that slot's run: the lane sums each run of its U neighbouring
+//     points (ALU only);
+//   - the lane's first run (from its first contributing slot) is summed over
+//     the lanes of the warp whose first run has the same pixel (one match and
+//     two reductions per chunk), and the group's lowest lane adds it;
+//   - the lane's other runs add directly.
+// Without AGG every contributing point adds on its own.  A group holds at
+// most 32 U points: for U <= 8, r | g << 16 and b | count << 16 cannot carry.
+// On return, add[u] marks the slots that add s_rg[u] (r | g << 16) and
+// s_bc[u] (b | count << 16) at pix[u].
+template <int U, bool AGG>
+__device__ __forceinline__ void group_colors(const bool (&contrib)[U], const uint32_t (&pix)[U], const uint4 (&r)[U],
+                                             uint32_t (&s_rg)[U], uint32_t (&s_bc)[U], bool (&add)[U]) {
+  static_assert(U <= 8, "group sums would carry");
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    // r | g << 16 and b | 1 << 16, each one byte permute of the rgba word
+    s_rg[u] = __byte_perm(r[u].w, 0u, 0x4140u);
+    s_bc[u] = __byte_perm(r[u].w, 0x100u, 0x4542u);
+    add[u] = contrib[u];
+  }
+  if constexpr (AGG) {
+    bool join[U];
+    join[0] = false;
+#pragma unroll
+    for (int u = 1; u < U; ++u) join[u] = contrib[u] && contrib[u - 1] && pix[u] == pix[u - 1];
+#pragma unroll
+    for (int u = U - 1; u > 0; --u) {
+      if (join[u]) {
+        s_rg[u - 1] += s_rg[u];
+        s_bc[u - 1] += s_bc[u];
+      }
+    }
+    bool first[U], seen = false;
+    uint32_t fpix = kNoPixel, frg = 0, fbc = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      add[u] = contrib[u] && !join[u];
+      first[u] = contrib[u] && !seen;
+      seen = seen || contrib[u];
+      if (first[u]) {
+        fpix = pix[u];
+        frg = s_rg[u];
+        fbc = s_bc[u];
+      }
+    }
+    // lanes with no contributing slot meet under kNoPixel (never a pixel)
+    const uint32_t peers = __match_any_sync(kFullMask, fpix);
+    frg = __reduce_add_sync(peers, frg);
+    fbc = __reduce_add_sync(peers, fbc);
+    const bool lead = (peers & lanemask_lt()) == 0u;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (first[u]) {
+        s_rg[u] = frg;
+        s_bc[u] = fbc;
+        add[u] = lead;
+      }
     }
   }
-  if (add) {
-    red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol);
-    red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol);
+}
+
+template <int U, bool AGG>
+__device__ __forceinline__ void emit_colors(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
+                                            const bool (&contrib)[U], const uint32_t (&pix)[U], const uint4 (&r)[U],
+                                            uint64_t pol) {
+  uint32_t s_rg[U], s_bc[U];
+  bool add[U];
+  group_colors<U, AGG>(contrib, pix, r, s_rg, s_bc, add);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (add[u]) {
+      red_add_u64(rg + pix[u], (static_cast<unsigned long long>(s_rg[u] & 0xFFFFu) << 32) | (s_rg[u] >> 16), pol);
+      red_add_u64(ba + pix[u], (static_cast<unsigned long long>(s_bc[u] & 0xFFFFu) << 32) | (s_bc[u] >> 16), pol);
+    }
   }
 }
 

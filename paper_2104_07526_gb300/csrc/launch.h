@@ -44,6 +44,10 @@ cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigne
 cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
                               uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
+// Division check behind pcr_check_division (selfcheck.cu); synchronous.
+cudaError_t check_division(uint32_t w_first, uint32_t w_count, const uint32_t* c_bits, uint32_t c_first,
+                           uint32_t c_count, uint32_t c_step, float size, uint64_t out[5], cudaStream_t s,
+                           const Device& d);
 
 // Batched rendering (batch.cu).  Tables live in the caller's workspace;
 // views are grouped by cloud.
@@ -121,5 +125,8 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
 // the caller has made d's device current and checked n against the limit.
 cudaError_t launch_reorder_noalloc(uint4* pts, uint32_t n, uint64_t seed, int mode, uint32_t* perm_out,
                                    cudaStream_t s, const Device& d);
+// Drop the cached scratch address of a device (a new context may follow a
+// device reset).
+void forget_noalloc_scratch(int device);
 
 }  // namespace pcr

@@ -53,24 +53,23 @@ constexpr int kHqMinBlocks = kMinBlocks < 6 ? 6 : kMinBlocks;
 template <int V, int U, int P>
 __global__ void __launch_bounds__(kThreads, kRenderMinBlocks) k_render_basic(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                            unsigned long long* __restrict__ fb) {
+  constexpr int L = kInterleaved;
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+  for_each_chunk<U, L, false>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
     uint32_t pix[U];
     float w[U];
     bool vis[U];
+    project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      pix[u] = 0;
-      w[u] = 0.0f;
-      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
-    }
+    for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
     unsigned long long seen[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) seen[u] = (reads_early<V>() && vis[u]) ? load_relaxed_u64(fb + pix[u]) : 0ull;
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      emit_key<V, P>(fb, vis[u], pix[u], w[u], P == kPayloadRgb ? r[u].w : base + 32u * u, seen[u], pol_fb);
+      emit_key<V, P>(fb, vis[u], pix[u], make_payload_key<P>(w[u], P == kPayloadRgb ? r[u].w : slot_index<U, L>(base, u)),
+                     seen[u], pol_fb);
   });
 }
 
@@ -138,22 +137,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_busy(const uint
                                                           unsigned long long* __restrict__ fb,
                                                           uint32_t* __restrict__ locks, uint64_t limit_ns) {
   const uint64_t pol_stream = policy_evict_first();
-  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+  for_each_chunk<U, kInterleaved, false>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
     uint32_t pix[U];
     float w[U];
     bool vis[U];
+    project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      pix[u] = 0;
-      w[u] = 0.0f;
-      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
-    }
+    for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, kInterleaved>(base, u, n, full);
     unsigned long long seen[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) seen[u] = vis[u] ? load_relaxed_u64(fb + pix[u]) : 0ull;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const unsigned long long key = make_key(w[u], base + 32u * u);
+      const unsigned long long key = make_key(w[u], slot_index<U, kInterleaved>(base, u));
       if (vis[u] && key < seen[u]) busy_update(fb, locks, pix[u], key, limit_ns);
     }
   });
@@ -166,54 +162,48 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_busy(const uint
 template <int V, int U>
 __global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_depth(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        uint32_t* __restrict__ depth) {
+  constexpr int L = kInterleaved;
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
   constexpr bool kEarly = V == PCR_VARIANT_EARLYZ || V == PCR_VARIANT_DEDUP_EARLYZ;
-  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+  for_each_chunk<U, L, false>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
     uint32_t pix[U];
     float w[U];
     bool vis[U];
+    project_slots<U>(v, r, pix, w, vis);
+    uint32_t d[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      pix[u] = 0;
-      w[u] = 0.0f;
-      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
+      vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
+      d[u] = __float_as_uint(w[u]);
     }
     uint32_t seen[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) seen[u] = (kEarly && vis[u]) ? load_relaxed_u32(depth + pix[u]) : 0u;
 #pragma unroll
-    for (int u = 0; u < U; ++u) emit_depth<V>(depth, vis[u], pix[u], __float_as_uint(w[u]), seen[u], pol_fb);
+    for (int u = 0; u < U; ++u) emit_depth<V>(depth, vis[u], pix[u], d[u], seen[u], pol_fb);
   });
 }
 
-// Colour pass (Listing "hqs_render"): see aggregate_chunk and emit_color.
-template <bool AGG, int U>
+// Colour pass (Listing "hqs_render"): see group_colors.
+template <bool AGG, int U, bool V8>
 __global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v,
                                                        float factor, const uint32_t* __restrict__ depth,
                                                        unsigned long long* __restrict__ rg,
                                                        unsigned long long* __restrict__ ba) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+  constexpr int L = AGG ? kConsecutive : kInterleaved;
+  for_each_chunk<U, L, V8>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
     uint32_t pix[U];
     float w[U];
     bool vis[U];
+    project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      pix[u] = 0;
-      w[u] = 0.0f;
-      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
-    }
-    uint32_t d[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(depth + pix[u]) : 0u;
+    for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
     bool contrib[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
-    const bool agg = AGG && aggregate_chunk(contrib[0], pix[0]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) emit_color(rg, ba, contrib[u], pix[u], r[u].w, pol_fb, agg);
+    contributes<U>(depth, factor, pix, w, vis, contrib);
+    emit_colors<U, AGG>(rg, ba, contrib, pix, r, pol_fb);
   });
 }
 
@@ -238,75 +228,58 @@ constexpr int kHq1rShiftR = 50, kHq1rShiftG = 36, kHq1rShiftB = 22;
 constexpr unsigned long long kHq1rChannelMask = 0x3FFFull;
 constexpr unsigned long long kHq1rCountMask = 0x3FFFFFull;
 
-template <bool AGG, int U>
+// r << 50 | g << 36 | b << 22 | k, built from 32-bit halves (r, g, b below
+// 2^14, k below 2^22).
+__device__ __forceinline__ unsigned long long hq1r_word(uint32_t r, uint32_t g, uint32_t b, uint32_t k) {
+  const uint32_t hi = (r << (kHq1rShiftR - 32)) | (g << (kHq1rShiftG - 32)) | (b >> (32 - kHq1rShiftB));
+  const uint32_t lo = (b << kHq1rShiftB) | k;
+  return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
+__device__ __forceinline__ uint32_t hq1r_field(unsigned long long word, int shift) {
+  return static_cast<uint32_t>((word >> shift) & kHq1rChannelMask);
+}
+
+template <bool AGG, int U, bool V8>
 __global__ void __launch_bounds__(kThreads, kHqMinBlocks)
     k_hq1r_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v, float factor,
                  const uint32_t* __restrict__ depth, unsigned long long* __restrict__ primary,
                  unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
-  for_each_chunk<U>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
+  constexpr int L = AGG ? kConsecutive : kInterleaved;
+  for_each_chunk<U, L, V8>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
     uint32_t pix[U];
     float w[U];
     bool vis[U];
+    project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      pix[u] = 0;
-      w[u] = 0.0f;
-      vis[u] = slot_in_range(base, u, n, full) && project_record(v, r[u], pix[u], w[u]);
-    }
-    uint32_t d[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) d[u] = vis[u] ? __ldg(depth + pix[u]) : 0u;
-    bool mine[U];
-    uint32_t sr[U], sg[U], sb[U], k[U];
+    for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
     bool contrib[U];
+    contributes<U>(depth, factor, pix, w, vis, contrib);
+    bool mine[U];
+    uint32_t s_rg[U], s_bc[U];
+    group_colors<U, AGG>(contrib, pix, r, s_rg, s_bc, mine);
+    unsigned long long add[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) contrib[u] = vis[u] && w[u] <= __fmul_rn(__uint_as_float(d[u]), factor);
-    const bool agg = AGG && aggregate_chunk(contrib[0], pix[0]);
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      sr[u] = r[u].w & 0xFFu;
-      sg[u] = (r[u].w >> 8) & 0xFFu;
-      sb[u] = (r[u].w >> 16) & 0xFFu;
-      k[u] = 1;
-      mine[u] = contrib[u];
-      if (agg) {
-        const uint32_t active = __ballot_sync(kFullMask, contrib[u]);
-        if (contrib[u]) {
-          const uint32_t peers = __match_any_sync(active, pix[u]);
-          const uint32_t s_rg = __reduce_add_sync(peers, sr[u] | (sg[u] << 16));
-          const uint32_t s_bc = __reduce_add_sync(peers, sb[u] | (1u << 16));
-          mine[u] = lane_id() == static_cast<uint32_t>(__ffs(peers) - 1);
-          sr[u] = s_rg & 0xFFFFu;
-          sg[u] = s_rg >> 16;
-          sb[u] = s_bc & 0xFFFFu;
-          k[u] = s_bc >> 16;
-        }
-      }
-    }
+    for (int u = 0; u < U; ++u) add[u] = hq1r_word(s_rg[u] & 0xFFFFu, s_rg[u] >> 16, s_bc[u] & 0xFFFFu, s_bc[u] >> 16);
     unsigned long long old[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      old[u] = 0;
-      if (mine[u]) {
-        const unsigned long long add = (static_cast<unsigned long long>(sr[u]) << kHq1rShiftR) |
-                                       (static_cast<unsigned long long>(sg[u]) << kHq1rShiftG) |
-                                       (static_cast<unsigned long long>(sb[u]) << kHq1rShiftB) | k[u];
-        old[u] = atom_add_u64(primary + pix[u], add, pol_fb);
-      }
-    }
+    for (int u = 0; u < U; ++u) old[u] = mine[u] ? atom_add_u64(primary + pix[u], add[u], pol_fb) : 0ull;
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!mine[u]) continue;
       const uint32_t c = static_cast<uint32_t>(old[u] & kHq1rCountMask);
-      if (c + k[u] <= kHq1rLimit) continue;
-      uint32_t fr = sr[u], fg = sg[u], fb = sb[u], fk = k[u];
+      const uint32_t k = static_cast<uint32_t>(add[u] & kHq1rCountMask);
+      if (c + k <= kHq1rLimit) continue;
+      uint32_t fr = hq1r_field(add[u], kHq1rShiftR), fg = hq1r_field(add[u], kHq1rShiftG);
+      uint32_t fb = hq1r_field(add[u], kHq1rShiftB), fk = k;
       if (c <= kHq1rLimit) {
+        // the word held c points and no field has carried
         atom_exch_u64(primary + pix[u], 0ull);
-        fr += static_cast<uint32_t>((old[u] >> kHq1rShiftR) & kHq1rChannelMask);
-        fg += static_cast<uint32_t>((old[u] >> kHq1rShiftG) & kHq1rChannelMask);
-        fb += static_cast<uint32_t>((old[u] >> kHq1rShiftB) & kHq1rChannelMask);
+        fr += hq1r_field(old[u], kHq1rShiftR);
+        fg += hq1r_field(old[u], kHq1rShiftG);
+        fb += hq1r_field(old[u], kHq1rShiftB);
         fk += c;
       }
       red_add_u64(rg + pix[u], (static_cast<unsigned long long>(fr) << 32) | fg, pol_fb);
@@ -441,6 +414,11 @@ dim3 screen_grid(uint64_t npx, const Device& d) {
   return dim3(static_cast<unsigned>(need < cap ? (need > 0 ? need : 1) : cap));
 }
 
+// 32-byte record-pair loads need an even number of points per lane and a
+// 32-byte aligned buffer (the interface promises 16 bytes).
+constexpr bool kCanPairLoad = kUnroll % 2 == 0;
+bool pairs_aligned(const uint4* pts) { return kCanPairLoad && (reinterpret_cast<uintptr_t>(pts) & 31u) == 0; }
+
 template <int V, int P>
 cudaError_t launch_basic_v(const uint4* pts, uint32_t n, const ViewParams& v, unsigned long long* keys, cudaStream_t s,
                            const Device& d) {
@@ -533,31 +511,41 @@ cudaError_t launch_hq_depth(int variant, const uint4* pts, uint32_t n, const Vie
   }
 }
 
+template <bool AGG, bool V8>
+void launch_color_k(const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor, const uint32_t* depth,
+                    unsigned long long* rg, unsigned long long* ba, cudaStream_t s, const Device& d) {
+  constexpr auto k = k_hq_color<AGG, kUnroll, V8>;
+  k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, rg, ba);
+}
+
 cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor,
                             const uint32_t* depth, unsigned long long* rg, unsigned long long* ba, cudaStream_t s,
                             const Device& d) {
   if (n == 0) return cudaSuccess;
-  if (variant != PCR_VARIANT_ATOMICMIN) {  // every variant but the basic one aggregates colours
-    constexpr auto k = k_hq_color<true, kUnroll>;
-    k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, rg, ba);
-  } else {
-    constexpr auto k = k_hq_color<false, kUnroll>;
-    k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, rg, ba);
-  }
+  // every variant but the basic one groups colours before adding
+  const bool agg = variant != PCR_VARIANT_ATOMICMIN;
+  if (!agg) launch_color_k<false, false>(pts, n, v, depth_factor, depth, rg, ba, s, d);
+  else if (pairs_aligned(pts)) launch_color_k<true, kCanPairLoad>(pts, n, v, depth_factor, depth, rg, ba, s, d);
+  else launch_color_k<true, false>(pts, n, v, depth_factor, depth, rg, ba, s, d);
   return cudaGetLastError();
+}
+
+template <bool AGG, bool V8>
+void launch_hq1r_k(const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor, const uint32_t* depth,
+                   unsigned long long* primary, unsigned long long* rg, unsigned long long* ba, cudaStream_t s,
+                   const Device& d) {
+  constexpr auto k = k_hq1r_color<AGG, kUnroll, V8>;
+  k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, primary, rg, ba);
 }
 
 cudaError_t launch_hq1r_color(int variant, const uint4* pts, uint32_t n, const ViewParams& v, float depth_factor,
                               const uint32_t* depth, unsigned long long* primary, unsigned long long* rg,
                               unsigned long long* ba, cudaStream_t s, const Device& d) {
   if (n == 0) return cudaSuccess;
-  if (variant != PCR_VARIANT_ATOMICMIN) {  // every variant but the basic one aggregates colours
-    constexpr auto k = k_hq1r_color<true, kUnroll>;
-    k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, primary, rg, ba);
-  } else {
-    constexpr auto k = k_hq1r_color<false, kUnroll>;
-    k<<<geometry_grid<k, kUnroll>(n, d), kThreads, 0, s>>>(pts, n, v, depth_factor, depth, primary, rg, ba);
-  }
+  const bool agg = variant != PCR_VARIANT_ATOMICMIN;
+  if (!agg) launch_hq1r_k<false, false>(pts, n, v, depth_factor, depth, primary, rg, ba, s, d);
+  else if (pairs_aligned(pts)) launch_hq1r_k<true, kCanPairLoad>(pts, n, v, depth_factor, depth, primary, rg, ba, s, d);
+  else launch_hq1r_k<true, false>(pts, n, v, depth_factor, depth, primary, rg, ba, s, d);
   return cudaGetLastError();
 }
 

@@ -658,7 +658,9 @@ std::mutex g_scratch_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of g_reorder_scratch on `device`, looked up once per device
-// with that device current (host code cannot use the symbol itself).
+// with that device current (host code cannot use the symbol itself).  A new
+// context on the device (pcr_create) drops the cached address, so a process
+// that reset the device and created a new context looks it up again.
 cudaError_t noalloc_scratch(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
@@ -673,6 +675,12 @@ cudaError_t noalloc_scratch(int device, void** out) {
 }
 
 }  // namespace
+
+void forget_noalloc_scratch(int device) {
+  if (device < 0 || device >= kMaxDevices) return;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  g_scratch_addr[device] = nullptr;
+}
 
 uint64_t reorder_workspace_bytes(uint64_t n) { return layout(n).total; }
 

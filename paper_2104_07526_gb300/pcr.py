@@ -130,6 +130,7 @@ _SIGS = {
     "pcr_reorder_morton_shuffle128": [_VP, _VP, _U64, _U64, _INT, _VP, _U64, _VP],
     "pcr_reorder_morton_shuffle128_noalloc": [_VP, _VP, _U64, _U64, _INT, _VP],
     "pcr_last_device_error": [_VP, C.POINTER(_U32)],
+    "pcr_check_division": [_VP, _U32, _U32, _VP, _U32, _U32, _U32, _FLT, C.POINTER(_U64)],
     "pcr_batch_workspace_size": [C.POINTER(_U64)],
     "pcr_batch_num_configs": [C.POINTER(_INT)],
     "pcr_batch_prepare": [_VP, C.POINTER(PcrBatchCloud), _U32, C.POINTER(PcrBatchView), _U32, _FLT, _U32, _VP, _U64],
@@ -467,6 +468,19 @@ def pcr_last_device_error(ctx: int) -> int:
     code = _U32()
     _check(lib().pcr_last_device_error(ctx, C.byref(code)), "pcr_last_device_error")
     return code.value
+
+
+def pcr_check_division(ctx: int, w_first: int, w_count: int, c_bits=None, c_first: int = 0, c_count: int = 0,
+                       c_step: int = 1, size: float = 1920.0) -> dict:
+    """Device check of the projection's screen division (synchronous).
+    c_bits: optional CUDA tensor of float32 bit patterns (int32 storage)."""
+    out = (_U64 * 5)()
+    if c_bits is not None:
+        c_count = int(c_bits.numel())
+    _check(lib().pcr_check_division(ctx, w_first, w_count, _dptr(c_bits, "c_bits"), c_first, c_count, c_step, size,
+                                    out), "pcr_check_division")
+    return {"reciprocal_mismatches": out[0], "quotient_mismatches": out[1], "screen_mismatches": out[2],
+            "quotient_pairs": out[3], "pairs": out[4]}
 
 
 # ---------------------------------------------------------------------------
