@@ -270,9 +270,9 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 //   - a slot whose pixel equals the previous slot's, both contributing,
 //     joins that slot's run: the lane sums each run of its U neighbouring
 //     points (ALU only);
-//   - the lane's first run (from its first contributing slot) is summed over
-//     the lanes of the warp whose first run has the same pixel (one match and
-//     two reductions per chunk), and the group's lowest lane adds it;
+//   - the run from the lane's slot 0 (when it contributes) is summed over
+//     the lanes of the warp whose slot-0 run has the same pixel (one match
+//     and two reductions per chunk), and the group's lowest lane adds it;
 //   - the lane's other runs add directly.
 // Without AGG every contributing point adds on its own.  A group holds at
 // most 32 U points: for U <= 8, r | g << 16 and b | count << 16 cannot carry.
@@ -301,32 +301,14 @@ __device__ __forceinline__ void group_colors(const bool (&contrib)[U], const uin
         s_bc[u - 1] += s_bc[u];
       }
     }
-    bool first[U], seen = false;
-    uint32_t fpix = kNoPixel, frg = 0, fbc = 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      add[u] = contrib[u] && !join[u];
-      first[u] = contrib[u] && !seen;
-      seen = seen || contrib[u];
-      if (first[u]) {
-        fpix = pix[u];
-        frg = s_rg[u];
-        fbc = s_bc[u];
-      }
-    }
-    // lanes with no contributing slot meet under kNoPixel (never a pixel)
-    const uint32_t peers = __match_any_sync(kFullMask, fpix);
-    frg = __reduce_add_sync(peers, frg);
-    fbc = __reduce_add_sync(peers, fbc);
-    const bool lead = (peers & lanemask_lt()) == 0u;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (first[u]) {
-        s_rg[u] = frg;
-        s_bc[u] = fbc;
-        add[u] = lead;
-      }
-    }
+    for (int u = 1; u < U; ++u) add[u] = contrib[u] && !join[u];
+    // the run from slot 0, over the warp: lanes whose slot 0 does not
+    // contribute meet under kNoPixel (never a pixel) and add nothing there
+    const uint32_t peers = __match_any_sync(kFullMask, contrib[0] ? pix[0] : kNoPixel);
+    s_rg[0] = __reduce_add_sync(peers, s_rg[0]);
+    s_bc[0] = __reduce_add_sync(peers, s_bc[0]);
+    add[0] = contrib[0] && (peers & lanemask_lt()) == 0u;
   }
 }
 
