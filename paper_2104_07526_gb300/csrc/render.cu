@@ -207,15 +207,17 @@ __global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_color(const uint4
   });
 }
 
-// Sec. 3.5.1, "HQS1R": one 64-bit add per contributing lane, or per group of
-// same-pixel lanes with AGG, into the primary word
+// Sec. 3.5.1, "HQS1R": one 64-bit add per contributing point, or per group
+// of same-pixel points with AGG (see group_colors), into the primary word
 //   r << 50 | g << 36 | b << 22 | count      (14, 14, 14, 22 bits).
 // The paper packs 16-16-16-16 and notes that the pattern must change when
 // more than about 65k adds to one pixel can be in flight at once; on a GB300
 // that many can (152 SMs x 2048 threads x 4 slots), so the count gets 22
 // bits (about 4.2M of margin) and a word holds at most kHq1rLimit = 64
-// points, whose channel sums (at most 64 * 255) fit 14 bits.  Group sums stay
-// below 32 * 255.  Let c be the count the word held before an add of k
+// points, whose channel sums (at most 64 * 255) fit 14 bits.  A group of
+// more than kHq1rLimit points (up to 128 with AGG) never touches the word: it
+// adds its 32-bit sums to the fallback directly.  Let c be the count the
+// word held before an add of k <= kHq1rLimit
 // points.  If c + k > kHq1rLimit the add does not stay in the word: when
 // c <= kHq1rLimit this add crossed the limit, so it resets the word and moves
 // the c points it held (no field has carried) together with its own k points
@@ -260,27 +262,33 @@ __global__ void __launch_bounds__(kThreads, kHqMinBlocks)
     bool mine[U];
     uint32_t s_rg[U], s_bc[U];
     group_colors<U, AGG>(contrib, pix, r, s_rg, s_bc, mine);
-    unsigned long long add[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) add[u] = hq1r_word(s_rg[u] & 0xFFFFu, s_rg[u] >> 16, s_bc[u] & 0xFFFFu, s_bc[u] >> 16);
+    // a group of more points than a word holds goes to the fallback sums
+    // directly; the others add to the word and learn its previous count
     unsigned long long old[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) old[u] = mine[u] ? atom_add_u64(primary + pix[u], add[u], pol_fb) : 0ull;
+    for (int u = 0; u < U; ++u) {
+      const bool to_word = mine[u] && (s_bc[u] >> 16) <= kHq1rLimit;
+      old[u] = to_word ? atom_add_u64(primary + pix[u],
+                                      hq1r_word(s_rg[u] & 0xFFFFu, s_rg[u] >> 16, s_bc[u] & 0xFFFFu, s_bc[u] >> 16),
+                                      pol_fb)
+                       : 0ull;
+    }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       if (!mine[u]) continue;
-      const uint32_t c = static_cast<uint32_t>(old[u] & kHq1rCountMask);
-      const uint32_t k = static_cast<uint32_t>(add[u] & kHq1rCountMask);
-      if (c + k <= kHq1rLimit) continue;
-      uint32_t fr = hq1r_field(add[u], kHq1rShiftR), fg = hq1r_field(add[u], kHq1rShiftG);
-      uint32_t fb = hq1r_field(add[u], kHq1rShiftB), fk = k;
-      if (c <= kHq1rLimit) {
-        // the word held c points and no field has carried
-        atom_exch_u64(primary + pix[u], 0ull);
-        fr += hq1r_field(old[u], kHq1rShiftR);
-        fg += hq1r_field(old[u], kHq1rShiftG);
-        fb += hq1r_field(old[u], kHq1rShiftB);
-        fk += c;
+      uint32_t fr = s_rg[u] & 0xFFFFu, fg = s_rg[u] >> 16, fb = s_bc[u] & 0xFFFFu, fk = s_bc[u] >> 16;
+      if (fk <= kHq1rLimit) {
+        const uint32_t c = static_cast<uint32_t>(old[u] & kHq1rCountMask);
+        if (c + fk <= kHq1rLimit) continue;  // it stays in the word
+        if (c <= kHq1rLimit) {
+          // this add crossed the limit: the word held c points and no field
+          // has carried; reset it and move its contents with this add's
+          atom_exch_u64(primary + pix[u], 0ull);
+          fr += hq1r_field(old[u], kHq1rShiftR);
+          fg += hq1r_field(old[u], kHq1rShiftG);
+          fb += hq1r_field(old[u], kHq1rShiftB);
+          fk += c;
+        }
       }
       red_add_u64(rg + pix[u], (static_cast<unsigned long long>(fr) << 32) | fg, pol_fb);
       red_add_u64(ba + pix[u], (static_cast<unsigned long long>(fb) << 32) | fk, pol_fb);

@@ -260,8 +260,8 @@ def test_hq1r_constructed_and_ragged(r, oracle):
 
 def test_hq1r_overflow_protocol(r, oracle):
     """Hundreds of thousands of points on a few pixels: the primary word
-    crosses 255 points again and again; every contribution must still be
-    counted exactly once."""
+    crosses its 64-point limit again and again; every contribution must still
+    be counted exactly once."""
     n = 400_000
     rng = np.random.default_rng(13)
     px = rng.integers(0, 3, size=n)
@@ -280,6 +280,33 @@ def test_hq1r_overflow_protocol(r, oracle):
     d0, *_ = oracle.render_hq(cloud, cs.camera(), cs.W, cs.H, 1.01)
     counts = oracle.hq_channel_sums(cloud, cs.camera(), cs.W, cs.H, d0, 1.01)[3]
     assert sorted(counts[counts > 0].tolist())[-1] > 100_000  # heavy pixels really were exercised
+
+
+def test_hq1r_groups_larger_than_a_word(r, oracle):
+    """Points sorted by pixel, in runs of every length from 1 to 300: warp
+    groups of up to 128 points (more than the 64 a primary word holds, which
+    go to the fallback sums directly) next to small ones that use the word."""
+    rng = np.random.default_rng(14)
+    runs = np.concatenate([np.arange(1, 301), rng.integers(1, 400, size=700)])
+    px = np.repeat(np.arange(runs.size) % 5, runs)
+    n = px.size
+    d = 2.0 + rng.integers(0, 4, size=n) / 1024.0
+    pts = np.stack([cs.point_on_pixel(100 + 7 * int(k), 60 + 3 * int(k), 2.0) for k in range(5)])
+    xyz = pts[px].copy()
+    xyz[:, 2] = cs.EYE_Z - d
+    xyz[:, 0] *= d / 2.0
+    xyz[:, 1] *= d / 2.0
+    col = rng.integers(0, 256, size=(n, 3))
+    cloud = cs.pack(xyz, cs.rgba_word(col[:, 0], col[:, 1], col[:, 2]))
+    r.upload(cloud)
+    r.view(cs.camera(), cs.W, cs.H)
+    _hq1r_check(r, oracle, cloud, cs.camera(), cs.W, cs.H)
+    # the same sums through the two-atomic HQ pass
+    d0, rg0, ba0 = oracle.render_hq(cloud, cs.camera(), cs.W, cs.H, 1.01)
+    for v in (0, 1, 2, 3):
+        got = r.render_hq(v, 1.01)
+        for a, b in zip(got, (d0, rg0, ba0)):
+            assert np.array_equal(a, b), v
 
 
 def test_host_upload_and_download(r, oracle, sphere):

@@ -112,6 +112,12 @@ def test_scan800M_bench_configuration(r, oracle):
     got = r.render_hq(pcr.PCR_VARIANT_DEDUP_EARLYZ, 1.01)
     for a, b in zip(got, e):
         assert np.array_equal(a, b)
+    # HQS1R: its primary words plus fallback sums give the same channel sums
+    sums = oracle.hq_channel_sums(host, view.matrix, W, H, e[0], 1.01)
+    d, *parts = r.render_hq1r_sums(pcr.PCR_VARIANT_DEDUP_EARLYZ, 1.01)
+    assert np.array_equal(d, e[0])
+    for a, b in zip(parts, sums):
+        assert np.array_equal(a, b)
     # the other two cameras with the benchmark's variant and dedup+early-z
     for name in ("closeup", "empty"):
         vv = views[name]
