@@ -217,14 +217,11 @@ __global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_color(const uint4
 // points, whose channel sums (at most 64 * 255) fit 14 bits.  A group of
 // more than kHq1rLimit points (up to 128 with AGG) never touches the word: it
 // adds its 32-bit sums to the fallback directly.  Let c be the count the
-// word held before an add of k <= kHq1rLimit
-// points.  If c + k > kHq1rLimit the add does not stay in the word: when
-// c <= kHq1rLimit this add crossed the limit, so it resets the word and moves
-// the c points it held (no field has carried) together with its own k points
-// into the 32-bit fallback sums; when c > kHq1rLimit the word is already
-// past the limit (its owner is about to reset it, discarding this add's bits)
-// and the add goes to the fallback.  Each slot's atomic is issued before any
-// slot waits on a returned value.
+// word held before an add of k <= kHq1rLimit points: see hq1r_settle.
+// Without AGG every contributing point adds to the word.  With AGG only the
+// warp group of a lane's slot 0 does (one add in flight per lane), and its
+// returned value is settled one chunk later, so the wait overlaps the next
+// chunk's loads and projection; the lane's other runs add to the fallback.
 constexpr uint32_t kHq1rLimit = 64;
 constexpr int kHq1rShiftR = 50, kHq1rShiftG = 36, kHq1rShiftB = 22;
 constexpr unsigned long long kHq1rChannelMask = 0x3FFFull;
@@ -242,14 +239,61 @@ __device__ __forceinline__ uint32_t hq1r_field(unsigned long long word, int shif
   return static_cast<uint32_t>((word >> shift) & kHq1rChannelMask);
 }
 
+// The word of a group from its sums s_rg = r | g << 16, s_bc = b | k << 16
+// (k <= kHq1rLimit, so each channel fits its field).
+__device__ __forceinline__ unsigned long long hq1r_word(uint32_t s_rg, uint32_t s_bc) {
+  return hq1r_word(s_rg & 0xFFFFu, s_rg >> 16, s_bc & 0xFFFFu, s_bc >> 16);
+}
+
+// A group's sums straight into the 32-bit fallback sums.
+__device__ __forceinline__ void hq1r_fallback(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
+                                              uint32_t pix, uint32_t s_rg, uint32_t s_bc, uint64_t pol) {
+  red_add_u64(rg + pix, (static_cast<unsigned long long>(s_rg & 0xFFFFu) << 32) | (s_rg >> 16), pol);
+  red_add_u64(ba + pix, (static_cast<unsigned long long>(s_bc & 0xFFFFu) << 32) | (s_bc >> 16), pol);
+}
+
+// After an add of a group (sums s_rg, s_bc; k <= kHq1rLimit points) to the
+// word at pix returned the word's previous value `old`, holding c points:
+// c + k <= kHq1rLimit, the add stays; c <= kHq1rLimit < c + k, this add
+// crossed the limit: reset the word and move its c points with this add's k
+// to the fallback (no field has carried); c > kHq1rLimit, the word's owner is
+// about to reset it, discarding this add's bits: this add to the fallback.
+__device__ __forceinline__ void hq1r_settle(unsigned long long* __restrict__ primary,
+                                            unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
+                                            uint32_t pix, uint32_t s_rg, uint32_t s_bc, unsigned long long old,
+                                            uint64_t pol) {
+  const uint32_t c = static_cast<uint32_t>(old & kHq1rCountMask);
+  uint32_t fr = s_rg & 0xFFFFu, fg = s_rg >> 16, fb = s_bc & 0xFFFFu, fk = s_bc >> 16;
+  if (c + fk <= kHq1rLimit) return;
+  if (c <= kHq1rLimit) {
+    atom_exch_u64(primary + pix, 0ull);
+    fr += hq1r_field(old, kHq1rShiftR);
+    fg += hq1r_field(old, kHq1rShiftG);
+    fb += hq1r_field(old, kHq1rShiftB);
+    fk += c;
+  }
+  red_add_u64(rg + pix, (static_cast<unsigned long long>(fr) << 32) | fg, pol);
+  red_add_u64(ba + pix, (static_cast<unsigned long long>(fb) << 32) | fk, pol);
+}
+
+// HQS1R's colour pass carries one add per lane into the next chunk; it runs
+// at 5 resident blocks (48 registers): at 6 it spills, and it was 2% slower.
+#ifndef PCR_HQ1R_MIN_BLOCKS
+#define PCR_HQ1R_MIN_BLOCKS 5
+#endif
 template <bool AGG, int U, bool V8>
-__global__ void __launch_bounds__(kThreads, kHqMinBlocks)
+__global__ void __launch_bounds__(kThreads, PCR_HQ1R_MIN_BLOCKS)
     k_hq1r_color(const uint4* __restrict__ pts, uint32_t n, ViewParams v, float factor,
                  const uint32_t* __restrict__ depth, unsigned long long* __restrict__ primary,
                  unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba) {
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
   constexpr int L = AGG ? kConsecutive : kInterleaved;
+  // with AGG: the one add to a word a lane has in flight, settled in the
+  // next chunk (or after the last)
+  bool live = false;
+  unsigned long long p_old = 0;
+  uint32_t p_pix = 0, p_rg = 0, p_bc = 0;
   for_each_chunk<U, L, V8>(pts, n, pol_stream, [&](const uint4(&r)[U], uint32_t base, auto full) {
     uint32_t pix[U];
     float w[U];
@@ -262,38 +306,35 @@ __global__ void __launch_bounds__(kThreads, kHqMinBlocks)
     bool mine[U];
     uint32_t s_rg[U], s_bc[U];
     group_colors<U, AGG>(contrib, pix, r, s_rg, s_bc, mine);
-    // a group of more points than a word holds goes to the fallback sums
-    // directly; the others add to the word and learn its previous count
-    unsigned long long old[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool to_word = mine[u] && (s_bc[u] >> 16) <= kHq1rLimit;
-      old[u] = to_word ? atom_add_u64(primary + pix[u],
-                                      hq1r_word(s_rg[u] & 0xFFFFu, s_rg[u] >> 16, s_bc[u] & 0xFFFFu, s_bc[u] >> 16),
-                                      pol_fb)
-                       : 0ull;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (!mine[u]) continue;
-      uint32_t fr = s_rg[u] & 0xFFFFu, fg = s_rg[u] >> 16, fb = s_bc[u] & 0xFFFFu, fk = s_bc[u] >> 16;
-      if (fk <= kHq1rLimit) {
-        const uint32_t c = static_cast<uint32_t>(old[u] & kHq1rCountMask);
-        if (c + fk <= kHq1rLimit) continue;  // it stays in the word
-        if (c <= kHq1rLimit) {
-          // this add crossed the limit: the word held c points and no field
-          // has carried; reset it and move its contents with this add's
-          atom_exch_u64(primary + pix[u], 0ull);
-          fr += hq1r_field(old[u], kHq1rShiftR);
-          fg += hq1r_field(old[u], kHq1rShiftG);
-          fb += hq1r_field(old[u], kHq1rShiftB);
-          fk += c;
-        }
+    if constexpr (AGG) {
+      // the previous chunk's add to a word: its previous value has arrived
+      // while this chunk loaded and projected
+      if (live) hq1r_settle(primary, rg, ba, p_pix, p_rg, p_bc, p_old, pol_fb);
+      // the warp group of slot 0 adds to the word when it fits one
+      live = mine[0] && (s_bc[0] >> 16) <= kHq1rLimit;
+      if (live) {
+        p_old = atom_add_u64(primary + pix[0], hq1r_word(s_rg[0], s_bc[0]), pol_fb);
+        p_pix = pix[0];
+        p_rg = s_rg[0];
+        p_bc = s_bc[0];
       }
-      red_add_u64(rg + pix[u], (static_cast<unsigned long long>(fr) << 32) | fg, pol_fb);
-      red_add_u64(ba + pix[u], (static_cast<unsigned long long>(fb) << 32) | fk, pol_fb);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (mine[u] && !(u == 0 && live)) hq1r_fallback(rg, ba, pix[u], s_rg[u], s_bc[u], pol_fb);
+    } else {
+      // one point per add: every add to the word, each settled as soon as
+      // all U have been issued
+      unsigned long long old[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) old[u] = mine[u] ? atom_add_u64(primary + pix[u], hq1r_word(s_rg[u], s_bc[u]), pol_fb) : 0ull;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (mine[u]) hq1r_settle(primary, rg, ba, pix[u], s_rg[u], s_bc[u], old[u], pol_fb);
     }
   });
+  if constexpr (AGG) {
+    if (live) hq1r_settle(primary, rg, ba, p_pix, p_rg, p_bc, p_old, pol_fb);
+  }
 }
 
 // ---------------------------------------------------------------------------
