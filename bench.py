@@ -43,6 +43,9 @@ METRIC = "points/s and HBM GB/s vs roofline per frame"
 UNIT = "points/s"
 POINT_BYTES = 16
 FALLBACK_HBM_GBS = 6800.0
+# Nominal HBM3e bandwidth of a GB300 ("about 8 TB/s"), reported beside the
+# measured copy bandwidth.
+NOMINAL_HBM_GBS = 8000.0
 # The timed frame's variant.  Every exact variant leaves the same buffer; on
 # GB300 the early depth test alone is the fastest of them on the scan scene,
 # or within 1% of early-z with warp deduplication (the sweep in the JSON line
@@ -233,11 +236,16 @@ def measured_hbm_gbs() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(kernel_sources: list[str], variant: str) -> dict | None:
-    """DRAM bytes per render launch from an ncu capture, if it was taken on
-    the current kernel sources and the timed variant
-    (profiles/traffic_render_scan800M.txt)."""
-    path = os.path.join(ROOT, "profiles", "traffic_render_scan800M.txt")
+TRAFFIC_RECORD = "traffic_render_scan100M.txt"
+
+
+def recorded_traffic(kernel_sources: list[str], variant: str, points: int) -> dict | None:
+    """DRAM bytes per render launch from an ncu capture of a smaller case of
+    the same scene (profiles/traffic_render_scan100M.txt), scaled to the
+    launch's points: the render streams every point once, so its traffic
+    grows with the point count.  Reported only while the capture was taken on
+    the current kernel sources and the timed variant."""
+    path = os.path.join(ROOT, "profiles", TRAFFIC_RECORD)
     try:
         with open(path) as f:
             kv = dict(line.split("=", 1) for line in f.read().splitlines() if "=" in line and not line.startswith("#"))
@@ -249,7 +257,10 @@ def recorded_traffic(kernel_sources: list[str], variant: str) -> dict | None:
             h.update(f.read())
     if kv.get("sources_sha256", "").strip() != h.hexdigest() or kv.get("variant", "").strip() != variant:
         return None
-    return {"bytes_per_launch": float(kv["bytes_per_launch"]), "note": kv.get("note", "").strip()}
+    captured = int(kv["points"])
+    per_point = float(kv["bytes_per_launch"]) / captured
+    return {"bytes_per_launch": per_point * points, "captured_points": captured,
+            "captured_bytes_per_launch": float(kv["bytes_per_launch"]), "note": kv.get("note", "").strip()}
 
 
 def make_cloud(cfg: dict, device, seed: int = 0):
@@ -299,8 +310,22 @@ def time_oracle(pts_np: np.ndarray, view, repeats: int = 1, threads: int = 1) ->
     return best
 
 
-# Algorithmic DRAM bytes per point of each one-time reorder (Sec. 4, Sec. 5),
-# counted from what the kernels must read and write at least once:
+# Algorithmic DRAM bytes per point of each one-time reorder (Sec. 4, Sec. 5):
+# what any sort-based reorder must move at least once, counted as 16 B of
+# records read for the bounds, 16 B read for the codes, every radix pass
+# reading and writing a 4-byte key and a 4-byte value (16 B), and the final
+# record gather (16 B read, 16 B written).  The shuffle's keys come from the
+# point index: 8 B written instead of the two record reads.  Morton codes of
+# 30 bits and the 32-bit shuffle keys sort in 4 passes; 63-bit codes in 8.
+REORDER_ALGORITHMIC_BYTES_PER_POINT = {
+    "morton": 16 + 16 + 4 * 16 + 32,
+    "morton_shuffle128": 16 + 16 + 4 * 16 + 32,
+    "shuffle": 8 + 4 * 16 + 32,
+    "morton63": 16 + 16 + 8 * 16 + 32,
+    "morton63_shuffle128": 16 + 16 + 8 * 16 + 32,
+}
+
+# DRAM bytes per point this design moves (its own choices included):
 #   bounds 16 read (plus 16 written: the record copy, for the 30-bit orders);
 #   30-bit codes 16 read + 8 written (key, index); 63-bit codes 16 read + 12
 #   written (low key, high word, index); each sort pass 4 (histogram read) +
@@ -319,10 +344,15 @@ REORDER_BYTES_PER_POINT = {
 
 
 def reorder_roofline(reorder_ms: dict, n: int, peak: float) -> dict:
+    """Per order: the algorithmic bytes over the time as a fraction of the
+    peak, and this design's own bytes as a ratio to the algorithmic ones."""
     out = {}
     for name, ms in reorder_ms.items():
-        gb = REORDER_BYTES_PER_POINT[name] * n / 1e9
-        out[name] = {"ms": ms, "algorithmic_gb": gb, "achieved_gbs": gb / (ms * 1e-3), "frac": gb / (ms * 1e-3) / peak}
+        gb = REORDER_ALGORITHMIC_BYTES_PER_POINT[name] * n / 1e9
+        design_gb = REORDER_BYTES_PER_POINT[name] * n / 1e9
+        out[name] = {"ms": ms, "algorithmic_gb": gb, "achieved_gbs": gb / (ms * 1e-3), "frac": gb / (ms * 1e-3) / peak,
+                     "design_gb": design_gb, "design_over_algorithmic": design_gb / gb,
+                     "design_gbs": design_gb / (ms * 1e-3)}
     return out
 
 
@@ -456,7 +486,8 @@ def run_reference(args, cfg):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/u64", "data": "synthetic",
-        "config": workload_config(cfg, view, args.variant),
+        "config": {**workload_config(cfg, view, args.variant), "sample_points": sample,
+                   "sample": f"timed on {describe_sample(n, sample)}, in shuffled-Morton order"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
                          "sample": f"per step {describe_sample(n, sample)}, put in shuffled-Morton order, "
                                    f"render + resolve, C oracle on every host core"},
@@ -598,10 +629,13 @@ def run_ours(args, cfg):
     peak, peak_src = measured_hbm_gbs()
     achieved = n * POINT_BYTES / (render_ms * 1e-3) / 1e9
     traffic = recorded_traffic([os.path.join(ROOT, "paper_2104_07526_gb300", "csrc", f)
-                                for f in ("render.cu", "common.cuh", "geometry.cuh")], args.variant) \
-        if args.config == "scan800M" else None
+                                for f in ("render.cu", "common.cuh", "geometry.cuh")], args.variant, n) \
+        if cfg["gen"] == "scan" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                 "traffic": traffic["bytes_per_launch"] if traffic else None,
+                "traffic_source": (f"ncu DRAM bytes of a {traffic['captured_points'] // 1_000_000}M-point launch of "
+                                   f"the same scene, scaled to {n // 1_000_000}M points") if traffic else None,
                 "kernel": f"k_render_basic<{args.variant}>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_src == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": n * POINT_BYTES}
@@ -677,7 +711,9 @@ def run_ours(args, cfg):
             "hq_roofline": None if hq_ms is None else {
                 "bound": "hbm", "algorithmic_bytes": 2 * n * POINT_BYTES,
                 "achieved_gbs": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9,
-                "frac": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9 / peak, "note": "two passes over the points"},
+                "frac": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9 / peak,
+                "frac_nominal": 2 * n * POINT_BYTES / (hq_ms * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
+                "note": "two passes over the points"},
             "reorder_roofline": reorder_roofline(reorder_ms, n, peak),
             "roofline": roofline, "clocks": clock_info, "gpu_launches": 3 * K,
             "e2e": e2e, "cpu_baseline": cpu, "reorder_ms": reorder_ms, "generate_s": gen_s,
@@ -955,30 +991,70 @@ def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, m
 
 
 def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
+    """Every render variant x vertex order x camera, timed.  Each cell also
+    records, compared on the device, whether its exact variants left
+    identical buffers: the key buffers of the six exact atomic variants and
+    the busy-loop; the colour-payload keys; the HQ buffers of the three HQ
+    variants; the HQS1R images against the HQ image; and the depth halves of
+    the keys against the original order's for the same camera (any vertex
+    order gives the same nearest depths)."""
+    import torch
     out = {}
+    keys, image = fb["keys"], fb["image"]
     for v in views:
         pcr.pcr_set_matrix(h, v.matrix)
         pcr.pcr_set_viewport(h, v.width, v.height)
         out[v.name] = {}
+        depth_ref = None
         for oname, buf in orders.items():
             pcr.pcr_upload_points(h, buf, n)
             row = {}
+            same = {"keys": True, "rgb": True, "hq": True, "hq1r_image": True}
+            ref = None
             for var in range(7):
                 row[pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_basic(h, var, True), stream, reps=10, warm=2), 4)
+                if var == pcr.PCR_VARIANT_ATOMICMIN:
+                    ref = keys.clone()
+                elif var in pcr.EXACT_VARIANTS:
+                    same["keys"] &= bool(torch.equal(keys, ref))
+            if depth_ref is None:
+                depth_ref = ref >> 32
+            else:
+                same["depth_vs_first_order"] = bool(torch.equal(ref >> 32, depth_ref))
+            rgb_ref = None
             for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_DEDUP_EARLYZ):
                 row["rgb:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_rgb(h, var, True), stream, reps=10, warm=2), 4)
+                if rgb_ref is None:
+                    rgb_ref = keys.clone()
+                else:
+                    same["rgb"] &= bool(torch.equal(keys, rgb_ref))
             pcr.pcr_last_device_error(h)
             busy = round(time_loop(lambda: pcr.pcr_render_basic(h, pcr.PCR_VARIANT_BUSY_LOOP, True), stream,
                                    reps=5, warm=1), 4)
             # a run whose lock waits ran out dropped points: not a valid time
-            row["busy-loop"] = busy if pcr.pcr_last_device_error(h) == 0 else "wait limit reached"
+            if pcr.pcr_last_device_error(h) == 0:
+                row["busy-loop"] = busy
+                same["busy_loop_keys"] = bool(torch.equal(keys, ref))
+            else:
+                row["busy-loop"] = "wait limit reached"
+            hq_ref = hq_img = None
             for var in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_DEDUP_EARLYZ):
                 row["hq:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_hq(h, 1.01, var, True), stream, reps=5, warm=1), 4)
+                got = [fb[k].clone() for k in ("hq_depth", "hq_rg", "hq_ba")]
+                if hq_ref is None:
+                    hq_ref = got
+                    pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, image, 0)
+                    hq_img = image.clone()
+                else:
+                    same["hq"] &= all(bool(torch.equal(a, b)) for a, b in zip(got, hq_ref))
                 row["hq1r:" + pcr.VARIANT_NAMES[var]] = round(time_loop(
                     lambda: pcr.pcr_render_hq1r(h, 1.01, var, True), stream, reps=5, warm=1), 4)
+                pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ1R, image, 0)
+                same["hq1r_image"] &= bool(torch.equal(image, hq_img))
+            row["identical"] = same
             out[v.name][oname] = row
     return out
 

@@ -112,8 +112,9 @@ void oracle_clear_hq(uint32_t *depth, uint64_t *rg, uint64_t *ba, size_t npx) {
     }
 }
 
-/* Sec. 3.1: atomicMin(framebuffer[pixelID], point) for every point.  Order
- * does not matter for a minimum, so a sequential loop states it exactly. */
+/* Sec. 3.1: every visible point's key lowers its pixel's word to the minimum
+ * of the two.  Order does not matter for a minimum, so a sequential loop
+ * states it exactly. */
 void oracle_render_basic(const oracle_point *pts, uint64_t n, const float m[16], int width, int height,
                          uint64_t *keys) {
     for (uint64_t i = 0; i < n; ++i) {

@@ -144,7 +144,7 @@ template <int V, int P = kPayloadIndex>
 __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix,
                                          unsigned long long key, unsigned long long seen, uint64_t pol) {
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
-    // Sec. 3.1: atomicMin(framebuffer[pixelID], point)
+    // Sec. 3.1: a 64-bit minimum of the key into its pixel's word
     if (vis) red_min_u64(fb + pix, key, pol);
   } else if constexpr (V == PCR_VARIANT_EARLYZ) {
     // Sec. 3.2: only call the atomic when the point is closer than what the

@@ -14,50 +14,60 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def _write_record(root, sources, variant="early-z", bytes_per_launch=12803000000):
+def _write_record(root, sources, variant="early-z", points=100_000_000, bytes_per_launch=1600300000):
     h = hashlib.sha256()
     for p in sources:
         with open(p, "rb") as f:
             h.update(f.read())
     os.makedirs(os.path.join(root, "profiles"), exist_ok=True)
-    with open(os.path.join(root, "profiles", "traffic_render_scan800M.txt"), "w") as f:
+    with open(os.path.join(root, "profiles", bench.TRAFFIC_RECORD), "w") as f:
         f.write("# a comment line = with an equals sign\n")
-        f.write(f"sources_sha256={h.hexdigest()}\nvariant={variant}\nbytes_per_launch={bytes_per_launch}\n"
-                "note=test record\n")
+        f.write(f"sources_sha256={h.hexdigest()}\nvariant={variant}\npoints={points}\n"
+                f"bytes_per_launch={bytes_per_launch}\nnote=test record\n")
 
 
-def test_traffic_record_follows_sources(tmp_path, monkeypatch):
+def test_traffic_record_follows_sources_and_scales(tmp_path, monkeypatch):
     srcs = []
     for name, text in (("a.cu", "kernel a\n"), ("b.cuh", "helper b\n")):
         p = tmp_path / name
         p.write_text(text)
         srcs.append(str(p))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.recorded_traffic(srcs, "early-z") is None  # no record yet
+    assert bench.recorded_traffic(srcs, "early-z", 800_000_000) is None  # no record yet
     _write_record(str(tmp_path), srcs)
-    rec = bench.recorded_traffic(srcs, "early-z")
-    assert rec == {"bytes_per_launch": 12803000000.0, "note": "test record"}
-    assert bench.recorded_traffic(srcs, "dedup+early-z") is None  # another variant was timed
+    rec = bench.recorded_traffic(srcs, "early-z", 800_000_000)
+    assert rec["bytes_per_launch"] == pytest.approx(8 * 1600300000.0)  # scaled by the points
+    assert rec["captured_points"] == 100_000_000 and rec["note"] == "test record"
+    assert bench.recorded_traffic(srcs, "early-z", 100_000_000)["bytes_per_launch"] == pytest.approx(1600300000.0)
+    assert bench.recorded_traffic(srcs, "dedup+early-z", 800_000_000) is None  # another variant was timed
     (tmp_path / "b.cuh").write_text("helper b changed\n")
-    assert bench.recorded_traffic(srcs, "early-z") is None  # the kernel changed since the capture
+    assert bench.recorded_traffic(srcs, "early-z", 800_000_000) is None  # the kernel changed since the capture
 
 
 def test_committed_traffic_record_is_for_the_timed_variant():
-    with open(os.path.join(ROOT, "profiles", "traffic_render_scan800M.txt")) as f:
+    path = os.path.join(ROOT, "profiles", bench.TRAFFIC_RECORD)
+    if not os.path.exists(path):
+        pytest.skip("no traffic record for the current kernels")
+    with open(path) as f:
         kv = dict(line.split("=", 1) for line in f.read().splitlines() if "=" in line and not line.startswith("#"))
     assert kv["variant"].strip() == bench.HEADLINE_VARIANT
-    assert 12.8e9 <= float(kv["bytes_per_launch"]) < 12.9e9  # 16 B per point of the 800M scene, plus little
+    per_point = float(kv["bytes_per_launch"]) / int(kv["points"])
+    assert 16.0 <= per_point < 16.2  # 16 B per point, plus little
 
 
 def test_reorder_roofline_arithmetic():
+    alg = bench.REORDER_ALGORITHMIC_BYTES_PER_POINT
+    assert alg["morton"] == alg["morton_shuffle128"] == 128 and alg["shuffle"] == 104
+    assert alg["morton63"] == alg["morton63_shuffle128"] == 192
     table = bench.REORDER_BYTES_PER_POINT
     assert table["morton"] == 172 and table["morton_shuffle128"] == 173 and table["shuffle"] == 156
     assert table["morton63"] == 304 and table["morton63_shuffle128"] == 305
     n, peak = 800_000_000, 6760.9
     out = bench.reorder_roofline({"morton": 27.5, "shuffle": 48.0}, n, peak)
-    assert out["morton"]["algorithmic_gb"] == pytest.approx(137.6)
-    assert out["morton"]["achieved_gbs"] == pytest.approx(137.6 / 27.5e-3)
-    assert out["shuffle"]["frac"] == pytest.approx(124.8 / 48.0e-3 / peak)
+    assert out["morton"]["algorithmic_gb"] == pytest.approx(102.4)
+    assert out["morton"]["achieved_gbs"] == pytest.approx(102.4 / 27.5e-3)
+    assert out["morton"]["design_over_algorithmic"] == pytest.approx(172 / 128)
+    assert out["shuffle"]["frac"] == pytest.approx(83.2 / 48.0e-3 / peak)
 
 
 def test_cpu_sample_and_its_description():
