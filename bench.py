@@ -87,6 +87,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--variant", default=HEADLINE_VARIANT, help="render variant of the timed frame")
+    ap.add_argument("--order", choices=["morton_shuffle128", "morton", "shuffle", "original"],
+                    default="morton_shuffle128", help="vertex order of the timed frame (profiling)")
     ap.add_argument("--no-hq", action="store_true", help="skip the high-quality frame")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (8 clouds x 8 views) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson request stream) measurement")
@@ -497,10 +499,15 @@ def run_reference(args, cfg):
     return 0
 
 
-def workload_config(cfg: dict, view, variant: str) -> dict:
+ORDER_WORDS = {"morton_shuffle128": "shuffled-Morton order", "morton": "Morton order", "shuffle": "shuffled order",
+               "original": "original (generation) order"}
+
+
+def workload_config(cfg: dict, view, variant: str, order: str = "morton_shuffle128") -> dict:
     desc = cfg["desc"].replace(f"basic frame with {HEADLINE_VARIANT}", f"basic frame with {variant}")
+    desc = desc.replace("shuffled-Morton order", ORDER_WORDS[order])
     return {"workload": desc, "points": cfg["points"], "width": view.width, "height": view.height,
-            "order": "morton_shuffle128", "camera": view.name, "variant": variant,
+            "order": order, "camera": view.name, "variant": variant,
             "l2": "inputs larger than L2 (no flush needed)" if cfg["points"] * POINT_BYTES > 129e6
             else "inputs fit in L2 (L2-resident case)", "parallelism": "replicas"}
 
@@ -541,7 +548,7 @@ def run_ours(args, cfg):
     reorder_ms = {}
     for name, mode in (("morton", pcr.PCR_ORDER_MORTON), ("shuffle", pcr.PCR_ORDER_SHUFFLE),
                        ("morton_shuffle128", pcr.PCR_ORDER_MORTON_SHUFFLE128)):
-        if args.no_sweep and name != "morton_shuffle128":
+        if args.no_sweep and name not in ("morton_shuffle128", args.order):
             continue
         buf = cloud.clone()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -565,11 +572,12 @@ def run_ours(args, cfg):
             reorder_ms[name] = e0.elapsed_time(e1)
             del buf
     del ws
+    points = orders[args.order]
     if args.no_sweep:
-        del orders["original"]
+        for name in [k for k in orders if k != args.order]:
+            del orders[name]
         del cloud
     torch.cuda.empty_cache()
-    points = orders["morton_shuffle128"]
 
     def set_view(v):
         pcr.pcr_set_matrix(h, v.matrix)
@@ -705,7 +713,7 @@ def run_ours(args, cfg):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view, args.variant),
+            "dtype": "f32/u64", "data": "synthetic", "config": workload_config(cfg, view, args.variant, args.order),
             "frame_gbs": n * POINT_BYTES / (ms_per_step * 1e-3) / 1e9,
             "phases_ms": phase, "frame_stats": frame_stats, "hq_frame_ms": hq_ms, "hq1r_frame_ms": hq1r_ms,
             "hq_roofline": None if hq_ms is None else {

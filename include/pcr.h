@@ -106,7 +106,9 @@ enum {
 /* Bits of the device-side error word (pcr_last_device_error). */
 enum {
     PCR_DEVICE_ERROR_KEY_RANGE = 1,    /* a resolve found a key naming a point outside the cloud */
-    PCR_DEVICE_ERROR_WAIT_TIMEOUT = 2  /* a busy-loop lock wait gave up (a point was dropped) */
+    PCR_DEVICE_ERROR_WAIT_TIMEOUT = 2, /* a busy-loop lock wait gave up (a point was dropped) */
+    PCR_DEVICE_ERROR_BOUNDS = 4        /* debug builds: a geometry kernel computed a pixel outside the
+                                          viewport (the point was dropped); release builds never set it */
 };
 
 typedef struct pcr_ctx pcr_ctx;
@@ -570,11 +572,26 @@ PCR_API pcr_status pcr_check_division(pcr_ctx *ctx, uint32_t w_first, uint32_t w
 /* Static, human-readable name of a status code. */
 PCR_API const char *pcr_status_string(pcr_status status);
 
+/* Debug builds only (libpcr_debug.so, compiled with PCR_DEBUG): read and
+ * clear the counters of the single-view geometry kernels of pcr_render_basic
+ * and pcr_render_hq (the HQS1R colour pass is not counted) since the last
+ * call, summed over launches:
+ *   out[0] key writes (Sec. 3.1-3.4 atomics, or just-set stores),
+ *   out[1] HQ depth writes (Sec. 3.5),
+ *   out[2] HQ colour add pairs (pcr_render_hq),
+ *   out[3] early reads (Sec. 3.2) of keys and depths.
+ * These show, e.g., that Sec. 3.4's deduplication sends one atomic per
+ * distinct pixel per warp row.  Synchronises the stream.  Errors:
+ * PCR_ERR_UNSUPPORTED in release builds; PCR_ERR_ARG for NULL arguments;
+ * PCR_ERR_CUDA if the copy fails. */
+PCR_API pcr_status pcr_debug_counters(pcr_ctx *ctx, uint64_t out[4]);
+
 /* Read and clear the device-side error word of the context's device
  * (synchronises the stream): PCR_DEVICE_ERROR_KEY_RANGE when a resolve found
  * a key naming a point index outside the borrowed cloud (the pixel took the
  * background colour), PCR_DEVICE_ERROR_WAIT_TIMEOUT when a busy-loop lock
- * wait gave up.  *code is 0 when nothing was reported.  Errors: PCR_ERR_ARG if code is NULL,
+ * wait gave up, PCR_DEVICE_ERROR_BOUNDS (debug builds) when a geometry
+ * kernel's bounds check dropped a point.  *code is 0 when nothing was reported.  Errors: PCR_ERR_ARG if code is NULL,
  * PCR_ERR_CUDA if the read fails. */
 PCR_API pcr_status pcr_last_device_error(pcr_ctx *ctx, uint32_t *code);
 

@@ -512,6 +512,16 @@ const char* pcr_status_string(pcr_status status) {
   }
 }
 
+pcr_status pcr_debug_counters(pcr_ctx* ctx, uint64_t out[4]) {
+  if (!ctx || !out) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  bool available = false;
+  const cudaError_t e = pcr::read_and_clear_debug_counts(out, ctx->stream, &available);
+  if (!available) return PCR_ERR_UNSUPPORTED;
+  return from_cuda(e);
+}
+
 pcr_status pcr_last_device_error(pcr_ctx* ctx, uint32_t* code) {
   if (!ctx || !code) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);

@@ -141,27 +141,38 @@ __host__ __device__ constexpr bool reads_early() {
 // One point slot after projection: its key (payload P), and `seen`, this
 // lane's earlier read of its pixel (variants with the early test only).
 template <int V, int P = kPayloadIndex>
-__device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix,
-                                         unsigned long long key, unsigned long long seen, uint64_t pol) {
+__device__ __forceinline__ bool emit_key(unsigned long long* __restrict__ fb, bool vis, uint32_t pix,
+                                         unsigned long long key, unsigned long long seen, uint64_t pol,
+                                         bool group = true) {
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
     // Sec. 3.1: a 64-bit minimum of the key into its pixel's word
     if (vis) red_min_u64(fb + pix, key, pol);
+    return vis;
   } else if constexpr (V == PCR_VARIANT_EARLYZ) {
     // Sec. 3.2: only call the atomic when the point is closer than what the
     // buffer (possibly stale, never too small) holds.
-    if (vis && key < seen) red_min_u64(fb + pix, key, pol);
+    const bool write = vis && key < seen;
+    if (write) red_min_u64(fb + pix, key, pol);
+    return write;
   } else if constexpr (V == PCR_VARIANT_DEDUP) {
     // Sec. 3.4: lanes with the same pixel form a group; only the lane with
     // the group's smallest key writes.  Keys reduce on the full 64 bits
     // (depth, then payload), so each distinct pixel costs one atomic per
-    // warp even when depths tie.
-    const uint32_t tag = vis ? pix : kNoPixel;
-    const uint32_t peers = __match_any_sync(kFullMask, tag);
-    const uint32_t hi = vis ? key_depth<P>(key) : 0xFFFFFFFFu;
-    const uint32_t hmin = __reduce_min_sync(peers, hi);
-    const uint32_t tied = __ballot_sync(kFullMask, hi == hmin) & peers;
-    const uint32_t first = min_key_lane<P>(tied, hi == hmin, key_payload<P>(key));
-    if (vis && lane_id() == first) red_min_u64(fb + pix, key, pol);
+    // warp even when depths tie.  `group` (warp-uniform, see dedup_pays)
+    // false: the row's pixels are nearly all distinct, so every visible lane
+    // writes without the match, which would find groups of one.
+    bool write = vis;
+    if (group) {
+      const uint32_t tag = vis ? pix : kNoPixel;
+      const uint32_t peers = __match_any_sync(kFullMask, tag);
+      const uint32_t hi = vis ? key_depth<P>(key) : 0xFFFFFFFFu;
+      const uint32_t hmin = __reduce_min_sync(peers, hi);
+      const uint32_t tied = __ballot_sync(kFullMask, hi == hmin) & peers;
+      const uint32_t first = min_key_lane<P>(tied, hi == hmin, key_payload<P>(key));
+      write = vis && lane_id() == first;
+    }
+    if (write) red_min_u64(fb + pix, key, pol);
+    return write;
   } else if constexpr (V == PCR_VARIANT_DEDUP_EARLYZ) {
     // Sec. 3.4 with Sec. 3.2, tests swapped: every visible lane has read its
     // pixel already (cheap, mostly L2 hits); only lanes still closer than the
@@ -182,8 +193,12 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
       } else {
         first = __reduce_min_sync(peers, hi == hmin ? lane_id() : 32u);
       }
-      if (lane_id() == first) red_min_u64(fb + pix, key, pol);
+      if (lane_id() == first) {
+        red_min_u64(fb + pix, key, pol);
+        return true;
+      }
     }
+    return false;
   } else if constexpr (V == PCR_VARIANT_REDUCE || V == PCR_VARIANT_REDUCE_EARLYZ) {
     // Sec. 3.3: if the whole warp targets one pixel, one lane writes the
     // warp's minimum; otherwise pairs of neighbouring lanes merge when they
@@ -205,29 +220,50 @@ __device__ __forceinline__ void emit_key(unsigned long long* __restrict__ fb, bo
         write = vis && (key < other_key || (P == kPayloadRgb && key == other_key && (lane_id() & 1u) == 0u));
       }
     }
-    if (write && (V == PCR_VARIANT_REDUCE || key < seen)) red_min_u64(fb + pix, key, pol);
+    write = write && (V == PCR_VARIANT_REDUCE || key < seen);
+    if (write) red_min_u64(fb + pix, key, pol);
+    return write;
   } else {
     // Sec. 5 "just-set": plain store, no depth test; the last writer wins.
     static_assert(V == PCR_VARIANT_JUST_SET, "unknown variant");
     if (vis) {
       asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(fb + pix), "l"(key));
     }
+    return vis;
   }
 }
 
+// Whether warp deduplication (Sec. 3.4, without the early test) pays in this
+// chunk, judged from its first row: the runs of equal pixels among
+// neighbouring visible lanes.  With more than kDedupMaxRuns the pixels are
+// nearly all distinct (shuffled orders) and the match would find groups of
+// one.  Warp-uniform.
+constexpr int kDedupMaxRuns = 16;
+__device__ __forceinline__ bool dedup_pays(bool vis0, uint32_t pix0) {
+  const uint32_t tag = vis0 ? pix0 : kNoPixel;
+  const uint32_t prev = __shfl_up_sync(kFullMask, tag, 1);
+  const uint32_t starts = __ballot_sync(kFullMask, vis0 && (lane_id() == 0 || prev != tag));
+  return __popc(starts) <= kDedupMaxRuns;
+}
+
 template <int V>
-__device__ __forceinline__ void emit_depth(uint32_t* __restrict__ depth, bool vis, uint32_t pix, uint32_t d,
+__device__ __forceinline__ bool emit_depth(uint32_t* __restrict__ depth, bool vis, uint32_t pix, uint32_t d,
                                            uint32_t seen, uint64_t pol) {
   if constexpr (V == PCR_VARIANT_ATOMICMIN) {
     if (vis) red_min_u32(depth + pix, d, pol);
+    return vis;
   } else if constexpr (V == PCR_VARIANT_EARLYZ) {
-    if (vis && d < seen) red_min_u32(depth + pix, d, pol);
+    const bool write = vis && d < seen;
+    if (write) red_min_u32(depth + pix, d, pol);
+    return write;
   } else if constexpr (V == PCR_VARIANT_DEDUP) {
     // The group's minimum can be written by any of its lanes: the lowest.
     const uint32_t tag = vis ? pix : kNoPixel;
     const uint32_t peers = __match_any_sync(kFullMask, tag);
     const uint32_t dmin = __reduce_min_sync(peers, vis ? d : 0xFFFFFFFFu);
-    if (vis && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) red_min_u32(depth + pix, dmin, pol);
+    const bool write = vis && lane_id() == static_cast<uint32_t>(__ffs(peers) - 1);
+    if (write) red_min_u32(depth + pix, dmin, pol);
+    return write;
   } else {
     // Early test first, then deduplicate the lanes that are still closer.
     static_assert(V == PCR_VARIANT_DEDUP_EARLYZ, "unknown depth variant");
@@ -236,8 +272,12 @@ __device__ __forceinline__ void emit_depth(uint32_t* __restrict__ depth, bool vi
     if (active != 0 && want) {
       const uint32_t peers = __match_any_sync(active, pix);
       const uint32_t dmin = __reduce_min_sync(peers, d);
-      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) red_min_u32(depth + pix, dmin, pol);
+      if (lane_id() == static_cast<uint32_t>(__ffs(peers) - 1)) {
+        red_min_u32(depth + pix, dmin, pol);
+        return true;
+      }
     }
+    return false;
   }
 }
 
@@ -312,20 +352,24 @@ __device__ __forceinline__ void group_colors(const bool (&contrib)[U], const uin
   }
 }
 
+// Returns how many pairs of adds this lane issued.
 template <int U, bool AGG>
-__device__ __forceinline__ void emit_colors(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
-                                            const bool (&contrib)[U], const uint32_t (&pix)[U], const uint4 (&r)[U],
-                                            uint64_t pol) {
+__device__ __forceinline__ int emit_colors(unsigned long long* __restrict__ rg, unsigned long long* __restrict__ ba,
+                                           const bool (&contrib)[U], const uint32_t (&pix)[U], const uint4 (&r)[U],
+                                           uint64_t pol) {
   uint32_t s_rg[U], s_bc[U];
   bool add[U];
   group_colors<U, AGG>(contrib, pix, r, s_rg, s_bc, add);
+  int adds = 0;
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     if (add[u]) {
       red_add_u64(rg + pix[u], (static_cast<unsigned long long>(s_rg[u] & 0xFFFFu) << 32) | (s_rg[u] >> 16), pol);
       red_add_u64(ba + pix[u], (static_cast<unsigned long long>(s_bc[u] & 0xFFFFu) << 32) | (s_bc[u] >> 16), pol);
+      ++adds;
     }
   }
+  return adds;
 }
 
 }  // namespace geom

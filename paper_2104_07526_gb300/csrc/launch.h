@@ -44,6 +44,9 @@ cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigne
 cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
                               uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
+// Debug builds: the geometry kernels' counters (render.cu); *available is
+// false in release builds.
+cudaError_t read_and_clear_debug_counts(uint64_t out[4], cudaStream_t s, bool* available);
 // Division check behind pcr_check_division (selfcheck.cu); synchronous.
 cudaError_t check_division(uint32_t w_first, uint32_t w_count, const uint32_t* c_bits, uint32_t c_first,
                            uint32_t c_count, uint32_t c_step, float size, uint64_t out[5], cudaStream_t s,

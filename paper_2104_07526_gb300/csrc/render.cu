@@ -26,6 +26,39 @@ using namespace geom;
 __device__ uint32_t g_error_word;
 constexpr uint32_t kErrorKeyRange = PCR_DEVICE_ERROR_KEY_RANGE;
 constexpr uint32_t kErrorWaitTimeout = PCR_DEVICE_ERROR_WAIT_TIMEOUT;
+constexpr uint32_t kErrorBounds = PCR_DEVICE_ERROR_BOUNDS;
+
+// Debug builds (PCR_DEBUG) count what the single-view geometry kernels send
+// to the framebuffers: key writes, depth writes, colour add pairs, and the
+// early reads; pcr_debug_counters reads and clears them.  They also check
+// every visible slot's pixel against the viewport before any access (a
+// failure sets kErrorBounds and drops the slot).  Release builds have
+// neither.
+#ifdef PCR_DEBUG
+__device__ unsigned long long g_debug_counts[4];
+#define PCR_DEBUG_COUNT(k, x)                                                     \
+  do {                                                                            \
+    if (x) atomicAdd(&g_debug_counts[k], static_cast<unsigned long long>(x));     \
+  } while (0)
+#else
+#define PCR_DEBUG_COUNT(k, x) \
+  do {                        \
+  } while (0)
+#endif
+
+template <int U>
+__device__ __forceinline__ void debug_check_pixels(const ViewParams& v, const uint32_t (&pix)[U], bool (&vis)[U]) {
+#ifdef PCR_DEBUG
+  const uint64_t npx = static_cast<uint64_t>(v.width) * v.height;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (vis[u] && pix[u] >= npx) {
+      atomicOr(&g_error_word, kErrorBounds);
+      vis[u] = false;
+    }
+  }
+#endif
+}
 
 #ifndef PCR_GEOMETRY_UNROLL
 #define PCR_GEOMETRY_UNROLL 4
@@ -63,13 +96,21 @@ __global__ void __launch_bounds__(kThreads, kRenderMinBlocks) k_render_basic(con
     project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
     for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
+    debug_check_pixels<U>(v, pix, vis);
     unsigned long long seen[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) seen[u] = (reads_early<V>() && vis[u]) ? load_relaxed_u64(fb + pix[u]) : 0ull;
+    for (int u = 0; u < U; ++u) {
+      seen[u] = (reads_early<V>() && vis[u]) ? load_relaxed_u64(fb + pix[u]) : 0ull;
+      PCR_DEBUG_COUNT(3, reads_early<V>() && vis[u]);
+    }
+    const bool group = V != PCR_VARIANT_DEDUP || dedup_pays(vis[0], pix[0]);
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      emit_key<V, P>(fb, vis[u], pix[u], make_payload_key<P>(w[u], P == kPayloadRgb ? r[u].w : slot_index<U, L>(base, u)),
-                     seen[u], pol_fb);
+    for (int u = 0; u < U; ++u) {
+      const bool wrote = emit_key<V, P>(
+          fb, vis[u], pix[u], make_payload_key<P>(w[u], P == kPayloadRgb ? r[u].w : slot_index<U, L>(base, u)),
+          seen[u], pol_fb, group);
+      PCR_DEBUG_COUNT(0, wrote);
+    }
   });
 }
 
@@ -144,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_render_busy(const uint
     project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
     for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, kInterleaved>(base, u, n, full);
+    debug_check_pixels<U>(v, pix, vis);
     unsigned long long seen[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) seen[u] = vis[u] ? load_relaxed_u64(fb + pix[u]) : 0ull;
@@ -177,11 +219,18 @@ __global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_depth(const uint4
       vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
       d[u] = __float_as_uint(w[u]);
     }
+    debug_check_pixels<U>(v, pix, vis);
     uint32_t seen[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) seen[u] = (kEarly && vis[u]) ? load_relaxed_u32(depth + pix[u]) : 0u;
+    for (int u = 0; u < U; ++u) {
+      seen[u] = (kEarly && vis[u]) ? load_relaxed_u32(depth + pix[u]) : 0u;
+      PCR_DEBUG_COUNT(3, kEarly && vis[u]);
+    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) emit_depth<V>(depth, vis[u], pix[u], d[u], seen[u], pol_fb);
+    for (int u = 0; u < U; ++u) {
+      const bool wrote = emit_depth<V>(depth, vis[u], pix[u], d[u], seen[u], pol_fb);
+      PCR_DEBUG_COUNT(1, wrote);
+    }
   });
 }
 
@@ -201,9 +250,11 @@ __global__ void __launch_bounds__(kThreads, kHqMinBlocks) k_hq_color(const uint4
     project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
     for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
+    debug_check_pixels<U>(v, pix, vis);
     bool contrib[U];
     contributes<U>(depth, factor, pix, w, vis, contrib);
-    emit_colors<U, AGG>(rg, ba, contrib, pix, r, pol_fb);
+    const int adds = emit_colors<U, AGG>(rg, ba, contrib, pix, r, pol_fb);
+    PCR_DEBUG_COUNT(2, adds);
   });
 }
 
@@ -301,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, PCR_HQ1R_MIN_BLOCKS)
     project_slots<U>(v, r, pix, w, vis);
 #pragma unroll
     for (int u = 0; u < U; ++u) vis[u] = vis[u] && slot_in_range<U, L>(base, u, n, full);
+    debug_check_pixels<U>(v, pix, vis);
     bool contrib[U];
     contributes<U>(depth, factor, pix, w, vis, contrib);
     bool mine[U];
@@ -619,6 +671,25 @@ cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long 
   if (npx == 0) return cudaSuccess;
   k_resolve_hq<<<screen_grid(npx, d), kThreads, 0, s>>>(rg, ba, npx, background, out);
   return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_debug_counts(uint64_t out[4], cudaStream_t s, bool* available) {
+#ifdef PCR_DEBUG
+  *available = true;
+  unsigned long long got[4];
+  const unsigned long long zero[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpyFromSymbolAsync(got, g_debug_counts, sizeof(got), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_debug_counts, zero, sizeof(zero), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (int k = 0; k < 4; ++k) out[k] = got[k];
+  return e;
+#else
+  (void)out;
+  (void)s;
+  *available = false;
+  return cudaSuccess;
+#endif
 }
 
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s) {

@@ -50,6 +50,7 @@ PCR_ORDER_MORTON63_SHUFFLE128 = 4
 
 PCR_DEVICE_ERROR_KEY_RANGE = 1
 PCR_DEVICE_ERROR_WAIT_TIMEOUT = 2
+PCR_DEVICE_ERROR_BOUNDS = 4
 
 
 class PcrBatchCloud(C.Structure):
@@ -131,6 +132,7 @@ _SIGS = {
     "pcr_reorder_morton_shuffle128_noalloc": [_VP, _VP, _U64, _U64, _INT, _VP],
     "pcr_last_device_error": [_VP, C.POINTER(_U32)],
     "pcr_check_division": [_VP, _U32, _U32, _VP, _U32, _U32, _U32, _FLT, C.POINTER(_U64)],
+    "pcr_debug_counters": [_VP, C.POINTER(_U64)],
     "pcr_batch_workspace_size": [C.POINTER(_U64)],
     "pcr_batch_num_configs": [C.POINTER(_INT)],
     "pcr_batch_prepare": [_VP, C.POINTER(PcrBatchCloud), _U32, C.POINTER(PcrBatchView), _U32, _FLT, _U32, _VP, _U64],
@@ -153,21 +155,30 @@ _SIGS = {
 }
 
 
+DEBUG_LIB_PATH = os.path.join(HERE, "libpcr_debug.so")
+
+
+def load_library(path: str) -> C.CDLL:
+    """Load a build of the library (libpcr.so or libpcr_debug.so) with the
+    C signatures set; raises if it has not been built."""
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2104_07526_gb300.build.build()")
+    L = C.CDLL(path)
+    for name, args in _SIGS.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = _INT
+    L.pcr_status_string.argtypes = [_INT]
+    L.pcr_status_string.restype = C.c_char_p
+    return L
+
+
 def lib() -> C.CDLL:
     """Load libpcr.so (raises if it has not been built)."""
     global _lib
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2104_07526_gb300.build.build()")
-            L = C.CDLL(LIB_PATH)
-            for name, args in _SIGS.items():
-                fn = getattr(L, name)
-                fn.argtypes = args
-                fn.restype = _INT
-            L.pcr_status_string.argtypes = [_INT]
-            L.pcr_status_string.restype = C.c_char_p
-            _lib = L
+            _lib = load_library(LIB_PATH)
     return _lib
 
 

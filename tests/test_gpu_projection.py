@@ -29,7 +29,7 @@ ONE = 0x3F800000
 
 @pytest.fixture(scope="module")
 def ctx():
-    from tests.gpu_helpers import ensure_built
+    from gpu_helpers import ensure_built
     ensure_built()
     c = pcr.Context(0, stream=torch.cuda.current_stream())
     yield c.handle
