@@ -878,16 +878,20 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
             "point_views_per_s": point_views / (batched_ms * 1e-3), "generate_s": gen_s}
 
 
-def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_batch_views: int = 32,
-               batch_config: int = 0, plain_baseline: bool = True, rates=(2000.0,), streams: int = 2,
-               max_batch_clouds: int = 2) -> list:
+def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 3, max_batch_views: int = 64,
+               batch_config: int = 0, plain_baseline: bool = True, rates=(2000.0,), streams: int = 3,
+               max_batch_clouds: int = 1, policy: int | None = None, max_queue: int = 256,
+               deadline_us: int = 0) -> list:
     """16 boxes clouds (1M..300M points, shuffled-Morton order) registered
     with the server from host memory, a 150 GB arena, and for each rate a
     Poisson stream of requests (random cloud, resolution 512^2..3840x2160,
-    basic or HQ, orbit camera).  Latency runs from each request's scheduled
-    arrival to its completion.  The same stream is then served by plain
-    per-request launches (one request at a time, in order).  One result per
-    rate."""
+    basic or HQ, orbit camera).  The server takes the largest groups of one
+    cloud first, 3 batches in flight on 3 streams, and refuses submissions
+    beyond 256 queued requests (admission control), so latency stays bounded
+    when the offered rate exceeds what the GPU renders.  Latency runs from
+    each request's scheduled arrival to its completion.  The same stream is
+    then served by plain per-request launches (one request at a time, in
+    order, every request).  One result per rate."""
     import torch
     from paper_2104_07526_gb300 import scenes
     sizes = scenes.SERVE_CLOUD_SIZES
@@ -897,19 +901,23 @@ def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 2, max_b
     out = []
     for rate in rates:
         out.append(served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, max_inflight,
-                                  max_batch_views, batch_config, plain_baseline, streams, max_batch_clouds))
+                                  max_batch_views, batch_config, plain_baseline, streams, max_batch_clouds,
+                                  pcr.PCR_SERVE_LARGEST_GROUP if policy is None else policy, max_queue,
+                                  deadline_us))
     return out
 
 
 def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, max_inflight, max_batch_views,
-                   batch_config, plain_baseline, streams, max_batch_clouds) -> dict:
+                   batch_config, plain_baseline, streams, max_batch_clouds, policy=0, max_queue=0,
+                   deadline_us=0) -> dict:
     import torch
     from paper_2104_07526_gb300 import scenes
     reqs = scenes.serve_requests(int(rate * seconds), rate, seed=7, num_clouds=len(sizes))
     arena = torch.empty(150 << 30, dtype=torch.uint8, device=dev)
-    srv = pcr.pcr_server_create(h, arena, 3840, 2160, num_slots=64, max_batch_views=max_batch_views,
+    srv = pcr.pcr_server_create(h, arena, 3840, 2160, num_slots=128, max_batch_views=max_batch_views,
                                 max_inflight=max_inflight, streams=streams, max_batch_clouds=max_batch_clouds,
-                                batch_config=batch_config, depth_factor=1.01, background_rgba=0)
+                                batch_config=batch_config, depth_factor=1.01, background_rgba=0,
+                                max_queue=max_queue, deadline_us=deadline_us, policy=policy)
     try:
         for i, hc in enumerate(host_clouds):
             pcr.pcr_server_add_cloud(srv, i, hc)
@@ -928,20 +936,29 @@ def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, m
 
         t0 = us() + 1000.0
         arrival = [t0 + r[0] * 1e6 for r in reqs]
-        lat, pts, last_done, i, done = [], 0, 0.0, 0, 0
+        lat, pts, last_done, i, done, refused, expired = [], 0, 0.0, 0, 0, 0, 0
         owner = {}
-        while done < len(reqs):
+        while done + refused < len(reqs):
             now = us()
             while i < len(reqs) and arrival[i] <= now:
                 _, c, m, W, H, flags = reqs[i]
-                owner[pcr.pcr_server_submit(srv, c, m, W, H, flags)] = i
+                try:
+                    owner[pcr.pcr_server_submit(srv, c, m, W, H, flags)] = i
+                except pcr.PcrError as e:  # admission control: the queue is full
+                    if e.status != pcr.PCR_ERR_BUSY:
+                        raise
+                    refused += 1
                 i += 1
             pcr.pcr_server_step(srv)
             for t in pcr.pcr_server_poll_completed(srv):
                 res = pcr.pcr_server_get_result(srv, t)
-                lat.append((res.done_us - arrival[owner.pop(t)]) / 1e3)
-                pts += res.points
-                last_done = max(last_done, res.done_us)
+                k = owner.pop(t)
+                if res.points or res.keys or res.hq_rg:
+                    lat.append((res.done_us - arrival[k]) / 1e3)
+                    pts += res.points
+                    last_done = max(last_done, res.done_us)
+                else:  # expired at its deadline, unrendered
+                    expired += 1
                 pcr.pcr_server_release(srv, t)
                 done += 1
         stats = pcr.pcr_server_stats_get(srv)
@@ -949,7 +966,10 @@ def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, m
         pcr.pcr_server_destroy(srv)
     span_s = (last_done - arrival[0]) / 1e6
     served = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-              "requests_per_s": len(reqs) / span_s, "points_per_s": pts / span_s,
+              "max_ms": float(np.max(lat)), "completed": len(lat), "refused": refused, "expired": expired,
+              "requests_per_s": len(lat) / span_s, "points_per_s": pts / span_s,
+              "policy": "largest groups" if policy == pcr.PCR_SERVE_LARGEST_GROUP else "arrival order",
+              "max_queue": max_queue, "deadline_ms": deadline_us / 1e3,
               "batches": stats["batches"] - stats0["batches"],
               "mean_batch": (stats["views_launched"] - stats0["views_launched"]) / max(1, stats["batches"] -
                                                                                       stats0["batches"]),

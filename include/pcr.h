@@ -64,7 +64,9 @@ enum {
     PCR_ERR_TIMEOUT = -4,      /* reserved: bounded device-side waits report through
                                   pcr_last_device_error (PCR_DEVICE_ERROR_WAIT_TIMEOUT),
                                   since launches return before the kernel runs */
-    PCR_ERR_UNSUPPORTED = -5   /* valid request this build does not provide */
+    PCR_ERR_UNSUPPORTED = -5,  /* valid request this build does not provide */
+    PCR_ERR_BUSY = -6          /* a server's queue is full (pcr_server_config.max_queue);
+                                  nothing was queued */
 };
 
 /* Render variants (Sec. 3.1 to 3.4, and the method list of Sec. 5).  Every
@@ -341,7 +343,9 @@ typedef struct pcr_batch_view {
 PCR_API pcr_status pcr_batch_workspace_size(uint64_t *bytes);
 
 /* Number of launch configurations pcr_batch_launch accepts (0 .. n-1);
- * pcr_batch_autotune picks among them. */
+ * pcr_batch_autotune and pcr_batch_tune pick among them.  Configuration c
+ * runs the geometry phases with 256 << (c >> 2) threads per block and
+ * (c & 2 ? 2 : 4), (c & 1 ? 2 : 4) points per lane; 0 is the default. */
 PCR_API pcr_status pcr_batch_num_configs(int *count);
 
 /* Describe a batch: copy the job tables (clouds, views grouped by cloud)
@@ -372,6 +376,36 @@ PCR_API pcr_status pcr_batch_launch(pcr_ctx *ctx, const void *dev_workspace, int
  * times; the outputs are overwritten) and return the fastest in *config.
  * Synchronises the stream.  Errors: PCR_ERR_ARG on NULL arguments. */
 PCR_API pcr_status pcr_batch_autotune(pcr_ctx *ctx, const void *dev_workspace, int *config);
+
+/* Result of pcr_batch_tune. */
+typedef struct pcr_batch_tuning {
+    uint32_t l2_budget_mb;     /* framebuffer bytes one pass over a cloud may touch (64, 96 or 128 MB) */
+    int32_t config;            /* launch configuration for pcr_batch_launch / pcr_batch_capture */
+    uint32_t threads;          /* its threads per block (256 or 512) */
+    uint32_t unroll1, unroll2; /* its points per lane in the two geometry phases (2 or 4) */
+    uint32_t from_cache;       /* 1: read from cache_path, nothing was timed */
+    uint32_t tried;            /* (budget, configuration) pairs timed */
+    uint32_t pad;
+    double best_ms;            /* the winner's time per batch (0 when from the cache) */
+    double default_ms;         /* pcr_batch_prepare's budget with configuration 0 (0 when from the cache) */
+} pcr_batch_tuning;
+
+/* Prepare a batch (as pcr_batch_prepare) with its tuned L2 budget, and
+ * choose its launch configuration.  Tries every budget in {64, 96, 128} MB
+ * with every launch configuration (threads per block x points per lane of
+ * each phase: 8), each timed over three launches after a warm-up, on the
+ * batch's own clouds and buffers (they are rendered), and leaves the
+ * workspace prepared with the fastest budget.  With cache_path (a file of
+ * JSON lines, created if missing; NULL for none), a result found for this
+ * GPU (name and SM count) and batch shape (cloud sizes, and each view's
+ * size, flags and cloud; not its camera) is used without timing, and a new
+ * result is appended.  Synchronises the context's stream.  Errors: as
+ * pcr_batch_prepare; PCR_ERR_ARG for a NULL out.  A cache file that cannot
+ * be read or written is ignored. */
+PCR_API pcr_status pcr_batch_tune(pcr_ctx *ctx, const pcr_batch_cloud *clouds, uint32_t num_clouds,
+                                  const pcr_batch_view *views, uint32_t num_views, float depth_factor,
+                                  uint32_t background_rgba, void *dev_workspace, uint64_t workspace_bytes,
+                                  const char *cache_path, pcr_batch_tuning *out);
 
 /* Record pcr_batch_launch(config) into a CUDA graph and instantiate it;
  * *graph_exec receives a cudaGraphExec_t.  Launch it with pcr_graph_launch,
@@ -408,7 +442,20 @@ typedef struct pcr_server_config {
     int32_t batch_config;      /* launch configuration of pcr_batch_launch */
     float depth_factor;        /* HQ depth band, e.g. 1.01 */
     uint32_t background_rgba;
+    uint32_t max_queue;        /* admission: queued requests at most, 0 = no bound; beyond it
+                                  pcr_server_submit returns PCR_ERR_BUSY */
+    uint32_t deadline_us;      /* a request still queued this long after its submission expires
+                                  instead of rendering (PCR_REQUEST_EXPIRED), 0 = never */
+    uint32_t policy;           /* PCR_SERVE_ARRIVAL or PCR_SERVE_LARGEST_GROUP */
 } pcr_server_config;
+
+/* Which queued requests a new batch takes (pcr_server_step). */
+enum {
+    PCR_SERVE_ARRIVAL = 0,       /* in arrival order, up to max_batch_clouds distinct clouds */
+    PCR_SERVE_LARGEST_GROUP = 1  /* the oldest request's cloud, then the clouds with the most queued
+                                    requests (up to max_batch_clouds), each cloud's requests in arrival
+                                    order: more views share each pass over a cloud's points */
+};
 
 typedef struct pcr_request {
     uint32_t cloud_id;
@@ -432,9 +479,11 @@ typedef struct pcr_server_stats {
     uint64_t submitted, completed, batches, views_launched;
     uint64_t uploads, evictions, bytes_uploaded, points_rendered;
     uint64_t peak_queue, queued, resident_clouds, resident_bytes;
+    uint64_t rejected;         /* submissions refused with PCR_ERR_BUSY */
+    uint64_t expired;          /* requests that reached their deadline while queued */
 } pcr_server_stats;
 
-enum { PCR_REQUEST_QUEUED = 0, PCR_REQUEST_RUNNING = 1, PCR_REQUEST_DONE = 2 };
+enum { PCR_REQUEST_QUEUED = 0, PCR_REQUEST_RUNNING = 1, PCR_REQUEST_DONE = 2, PCR_REQUEST_EXPIRED = 3 };
 
 /* Create a server on the context's device.  Frame slots (36 bytes per pixel
  * of max_width x max_height each) and one batch workspace per in-flight batch
@@ -463,16 +512,20 @@ PCR_API pcr_status pcr_server_add_device_cloud(pcr_server *srv, uint32_t cloud_i
 
 /* Queue a view request; *ticket identifies it.  Time stamps use the host
  * steady clock.  Errors: PCR_ERR_ARG for an unknown cloud, a size above the
- * maxima or bad flags; PCR_ERR_WORKSPACE if the cloud can never fit. */
+ * maxima or bad flags; PCR_ERR_WORKSPACE if the cloud can never fit;
+ * PCR_ERR_BUSY when max_queue requests are already queued (admission
+ * control: the caller may retry later). */
 PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, uint64_t *ticket);
 
 /* One turn of the serving loop, never blocking on the GPU: retire batches
- * that have finished (their requests become PCR_REQUEST_DONE), then launch new
- * batches from the queued requests, in arrival order, as far as in-flight
- * batches, frame slots, cloud memory and max_batch_clouds allow (a request
- * that cannot join now waits while later ones go ahead; the oldest request
- * always joins the next batch that has room).  *completed (may be NULL)
- * counts the requests this call retired.  A batch in which some cloud has
+ * that have finished (their requests become PCR_REQUEST_DONE), expire queued
+ * requests past their deadline (PCR_REQUEST_EXPIRED, reported like finished
+ * ones), then launch new batches from the queued requests (policy: in arrival
+ * order, or largest groups of one cloud first) as far as in-flight batches,
+ * frame slots, cloud memory and max_batch_clouds allow (a request that cannot
+ * join now waits while later ones go ahead; the oldest request always joins
+ * the next batch that has room).  *completed (may be NULL) counts the
+ * requests this call retired or expired.  A batch in which some cloud has
  * two views or more runs through pcr_batch_launch; a batch whose views all
  * have different clouds runs each view through the single-view kernels
  * (pcr_render_basic with early-z, pcr_render_hq with dedup+early-z, and the
@@ -481,20 +534,22 @@ PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, ui
  * shared its batch. */
 PCR_API pcr_status pcr_server_step(pcr_server *srv, uint32_t *completed);
 
-/* PCR_REQUEST_QUEUED, _RUNNING or _DONE for a ticket not yet released. */
+/* PCR_REQUEST_QUEUED, _RUNNING, _DONE or _EXPIRED for a ticket not yet
+ * released. */
 PCR_API pcr_status pcr_server_state(pcr_server *srv, uint64_t ticket, int *state);
 
 /* Result of a finished request: device pointers into its frame slot (valid
- * until pcr_server_release) and its time stamps. */
+ * until pcr_server_release) and its time stamps.  An expired request has
+ * NULL pointers, flags 0, points 0 and done_us at its expiry. */
 PCR_API pcr_status pcr_server_get_result(pcr_server *srv, uint64_t ticket, pcr_server_result *out);
 
-/* Report up to `capacity` tickets that finished since the previous call, in
- * completion order; *count receives how many were written. */
+/* Report up to `capacity` tickets that finished or expired since the previous
+ * call, in completion order; *count receives how many were written. */
 PCR_API pcr_status pcr_server_poll_completed(pcr_server *srv, uint64_t *tickets, uint32_t capacity, uint32_t *count);
 
-/* Give a finished request's frame slot back.  Reads of the slot issued on
- * other streams must have completed first: the slot may be rewritten by the
- * next batch. */
+/* Give a finished request's frame slot back (or forget an expired request).
+ * Reads of the slot issued on other streams must have completed first: the
+ * slot may be rewritten by the next batch. */
 PCR_API pcr_status pcr_server_release(pcr_server *srv, uint64_t ticket);
 
 /* Counters since creation, plus the current queue length and residency. */

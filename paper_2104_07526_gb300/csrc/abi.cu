@@ -1,8 +1,11 @@
 // C interface (include/pcr.h): argument checks, context state and launches.
 // No exception leaves this file; every entry point returns a pcr_status.
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "../../include/pcr.h"
 #include "launch.h"
@@ -72,6 +75,142 @@ pcr::ViewParams view_params(const pcr_ctx* c) {
 uint64_t pixels(const pcr_ctx* c) { return static_cast<uint64_t>(c->width) * static_cast<uint64_t>(c->height); }
 
 bool view_ready(const pcr_ctx* c) { return c->has_matrix && c->width > 0 && c->height > 0; }
+
+// Arguments of pcr_batch_prepare and pcr_batch_tune.
+pcr_status check_batch(const pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t num_clouds,
+                       const pcr_batch_view* views, uint32_t num_views, float depth_factor, const void* dev_workspace,
+                       uint64_t workspace_bytes) {
+  if (!ctx || !clouds || !views) return PCR_ERR_ARG;
+  if (num_clouds == 0 || num_clouds > PCR_BATCH_MAX_CLOUDS || num_views == 0 || num_views > PCR_BATCH_MAX_VIEWS)
+    return PCR_ERR_ARG;
+  if (!(depth_factor > 0.0f) || !(depth_factor < 3.0e38f)) return PCR_ERR_ARG;
+  for (uint32_t c = 0; c < num_clouds; ++c) {
+    if (clouds[c].n > kMaxPoints) return PCR_ERR_ARG;
+    if (clouds[c].n > 0 && (!clouds[c].points || !aligned(clouds[c].points, 16))) return PCR_ERR_ARG;
+  }
+  for (uint32_t i = 0; i < num_views; ++i) {
+    const pcr_batch_view& v = views[i];
+    if (v.cloud >= num_clouds || v.width < 1 || v.height < 1 || v.width > kMaxViewport || v.height > kMaxViewport)
+      return PCR_ERR_ARG;
+    if (v.flags == 0 || (v.flags & ~static_cast<uint32_t>(PCR_BATCH_BASIC | PCR_BATCH_HQ))) return PCR_ERR_ARG;
+    if ((v.flags & PCR_BATCH_BASIC) &&
+        (!v.keys || !aligned(v.keys, 8) || (v.image && !aligned(v.image, 4))))
+      return PCR_ERR_ARG;
+    if ((v.flags & PCR_BATCH_HQ) && (!v.hq_depth || !aligned(v.hq_depth, 4) || !v.hq_rg || !aligned(v.hq_rg, 8) ||
+                                     !v.hq_ba || !aligned(v.hq_ba, 8) || (v.hq_image && !aligned(v.hq_image, 4))))
+      return PCR_ERR_ARG;
+  }
+  if (!dev_workspace || !aligned(dev_workspace, 256) || workspace_bytes < pcr::batch_workspace_bytes())
+    return PCR_ERR_WORKSPACE;
+  return PCR_OK;
+}
+
+// L2 budgets (MB of framebuffer one pass over a cloud may touch) the batch
+// tuner tries; the middle one is pcr_batch_prepare's.
+constexpr int kTuneBudgetsMb[] = {64, 96, 128};
+constexpr int kNumTuneBudgets = 3;
+
+// "<device name> sm<count>": the GPU a tuning result belongs to.
+std::string gpu_id(const pcr::Device& d) {
+  cudaDeviceProp prop{};
+  std::string name = cudaGetDeviceProperties(&prop, d.id) == cudaSuccess ? prop.name : "unknown";
+  for (char& ch : name)
+    if (ch == '"' || ch == '\\' || ch < 32) ch = '_';
+  return name + " sm" + std::to_string(d.num_sms);
+}
+
+// The shape of a batch: cloud sizes and each view's size, flags and cloud
+// (not its camera), as counts and a 64-bit FNV-1a hash.
+std::string batch_shape_key(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
+                            uint32_t num_views) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&h](uint64_t v) {
+    for (int k = 0; k < 8; ++k) {
+      h ^= (v >> (8 * k)) & 0xFF;
+      h *= 1099511628211ull;
+    }
+  };
+  for (uint32_t c = 0; c < num_clouds; ++c) mix(clouds[c].n);
+  for (uint32_t i = 0; i < num_views; ++i) {
+    mix(static_cast<uint64_t>(views[i].width) << 32 | static_cast<uint32_t>(views[i].height));
+    mix(static_cast<uint64_t>(views[i].flags) << 32 | views[i].cloud);
+  }
+  char buf[64];
+  std::snprintf(buf, sizeof(buf), "c%uv%u-%016llx", num_clouds, num_views, static_cast<unsigned long long>(h));
+  return buf;
+}
+
+// The integer after `"name": ` in a line of the cache, if present.
+bool json_int(const std::string& line, const char* name, long long* v) {
+  const std::string tag = std::string("\"") + name + "\": ";
+  const size_t at = line.find(tag);
+  if (at == std::string::npos) return false;
+  char* end = nullptr;
+  *v = std::strtoll(line.c_str() + at + tag.size(), &end, 10);
+  return end != line.c_str() + at + tag.size();
+}
+
+// The cache is a file of JSON lines, one per tuned (GPU, shape); the last
+// line for a pair wins.
+bool read_tuning(const char* path, const std::string& gpu, const std::string& shape, int* budget_mb, int* config) {
+  std::FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  bool found = false;
+  char buf[1024];
+  const std::string want_gpu = "\"gpu\": \"" + gpu + "\"", want_shape = "\"shape\": \"" + shape + "\"";
+  while (std::fgets(buf, sizeof(buf), f)) {
+    const std::string line(buf);
+    long long b = 0, c = 0;
+    if (line.find(want_gpu) == std::string::npos || line.find(want_shape) == std::string::npos) continue;
+    if (!json_int(line, "budget_mb", &b) || !json_int(line, "config", &c)) continue;
+    bool known = false;
+    for (int k = 0; k < kNumTuneBudgets; ++k) known = known || b == kTuneBudgetsMb[k];
+    if (!known || c < 0 || c >= pcr::batch_num_configs()) continue;
+    *budget_mb = static_cast<int>(b);
+    *config = static_cast<int>(c);
+    found = true;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void fill_tuning(pcr_batch_tuning* out, int budget_mb, int config, int from_cache, int tried, double best_ms,
+                 double default_ms) {
+  out->l2_budget_mb = static_cast<uint32_t>(budget_mb);
+  out->config = config;
+  out->threads = static_cast<uint32_t>(pcr::batch_config_threads(config));
+  out->unroll1 = static_cast<uint32_t>(pcr::batch_config_unroll(config, 0));
+  out->unroll2 = static_cast<uint32_t>(pcr::batch_config_unroll(config, 1));
+  out->from_cache = static_cast<uint32_t>(from_cache);
+  out->tried = static_cast<uint32_t>(tried);
+  out->best_ms = best_ms;
+  out->default_ms = default_ms;
+}
+
+void write_tuning(const char* path, const std::string& gpu, const std::string& shape, const pcr_batch_tuning& t) {
+  std::FILE* f = std::fopen(path, "a");
+  if (!f) return;  // the cache is an optimisation: a read-only location only loses it
+  std::fprintf(f,
+               "{\"gpu\": \"%s\", \"shape\": \"%s\", \"budget_mb\": %u, \"config\": %d, \"threads\": %u, "
+               "\"unroll1\": %u, \"unroll2\": %u, \"ms\": %.4f, \"default_ms\": %.4f}\n",
+               gpu.c_str(), shape.c_str(), t.l2_budget_mb, t.config, t.threads, t.unroll1, t.unroll2, t.best_ms,
+               t.default_ms);
+  std::fclose(f);
+}
+
+// Time one launch configuration on the prepared workspace: one warm-up
+// launch, then three timed ones; *ms per launch.
+cudaError_t time_batch(const void* ws, int config, pcr_ctx* ctx, cudaEvent_t a, cudaEvent_t b, double* ms) {
+  cudaError_t e = pcr::batch_launch(ws, config, ctx->stream, ctx->dev);
+  if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = pcr::batch_launch(ws, config, ctx->stream, ctx->dev);
+  if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  *ms = t / 3.0;
+  return e;
+}
 
 }  // namespace
 
@@ -383,32 +522,70 @@ pcr_status pcr_batch_num_configs(int* count) {
 pcr_status pcr_batch_prepare(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t num_clouds,
                              const pcr_batch_view* views, uint32_t num_views, float depth_factor,
                              uint32_t background_rgba, void* dev_workspace, uint64_t workspace_bytes) {
-  if (!ctx || !clouds || !views) return PCR_ERR_ARG;
-  if (num_clouds == 0 || num_clouds > PCR_BATCH_MAX_CLOUDS || num_views == 0 || num_views > PCR_BATCH_MAX_VIEWS)
-    return PCR_ERR_ARG;
-  if (!(depth_factor > 0.0f) || !(depth_factor < 3.0e38f)) return PCR_ERR_ARG;
-  for (uint32_t c = 0; c < num_clouds; ++c) {
-    if (clouds[c].n > kMaxPoints) return PCR_ERR_ARG;
-    if (clouds[c].n > 0 && (!clouds[c].points || !aligned(clouds[c].points, 16))) return PCR_ERR_ARG;
-  }
-  for (uint32_t i = 0; i < num_views; ++i) {
-    const pcr_batch_view& v = views[i];
-    if (v.cloud >= num_clouds || v.width < 1 || v.height < 1 || v.width > kMaxViewport || v.height > kMaxViewport)
-      return PCR_ERR_ARG;
-    if (v.flags == 0 || (v.flags & ~static_cast<uint32_t>(PCR_BATCH_BASIC | PCR_BATCH_HQ))) return PCR_ERR_ARG;
-    if ((v.flags & PCR_BATCH_BASIC) &&
-        (!v.keys || !aligned(v.keys, 8) || (v.image && !aligned(v.image, 4))))
-      return PCR_ERR_ARG;
-    if ((v.flags & PCR_BATCH_HQ) && (!v.hq_depth || !aligned(v.hq_depth, 4) || !v.hq_rg || !aligned(v.hq_rg, 8) ||
-                                     !v.hq_ba || !aligned(v.hq_ba, 8) || (v.hq_image && !aligned(v.hq_image, 4))))
-      return PCR_ERR_ARG;
-  }
-  if (!dev_workspace || !aligned(dev_workspace, 256) || workspace_bytes < pcr::batch_workspace_bytes())
-    return PCR_ERR_WORKSPACE;
+  const pcr_status st = check_batch(ctx, clouds, num_clouds, views, num_views, depth_factor, dev_workspace,
+                                    workspace_bytes);
+  if (st != PCR_OK) return st;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   return from_cuda(pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba,
                                       dev_workspace, ctx->stream));
+}
+
+pcr_status pcr_batch_tune(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t num_clouds,
+                          const pcr_batch_view* views, uint32_t num_views, float depth_factor,
+                          uint32_t background_rgba, void* dev_workspace, uint64_t workspace_bytes,
+                          const char* cache_path, pcr_batch_tuning* out) {
+  if (!out) return PCR_ERR_ARG;
+  const pcr_status st = check_batch(ctx, clouds, num_clouds, views, num_views, depth_factor, dev_workspace,
+                                    workspace_bytes);
+  if (st != PCR_OK) return st;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  *out = pcr_batch_tuning{};
+  const std::string gpu = gpu_id(ctx->dev);
+  const std::string shape = batch_shape_key(clouds, num_clouds, views, num_views);
+  int cached_budget = 0, cached_config = -1;
+  if (cache_path && read_tuning(cache_path, gpu, shape, &cached_budget, &cached_config)) {
+    const cudaError_t e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba,
+                                             dev_workspace, ctx->stream, static_cast<uint64_t>(cached_budget) << 20);
+    if (e != cudaSuccess) return PCR_ERR_CUDA;
+    fill_tuning(out, cached_budget, cached_config, 1, 0, 0.0, 0.0);
+    return PCR_OK;
+  }
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return PCR_ERR_CUDA;
+  }
+  cudaError_t e = pcr::batch_prewarm(ctx->dev);
+  int best_budget = kTuneBudgetsMb[1], best_config = 0, tried = 0;
+  double best_ms = 0.0, default_ms = 0.0;
+  for (int bi = 0; bi < kNumTuneBudgets && e == cudaSuccess; ++bi) {
+    const int budget = kTuneBudgetsMb[bi];
+    e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, dev_workspace,
+                           ctx->stream, static_cast<uint64_t>(budget) << 20);
+    for (int c = 0; c < pcr::batch_num_configs() && e == cudaSuccess; ++c) {
+      double ms = 0.0;
+      e = time_batch(dev_workspace, c, ctx, a, b, &ms);
+      if (e != cudaSuccess) break;
+      ++tried;
+      if (budget == kTuneBudgetsMb[1] && c == 0) default_ms = ms;
+      if (tried == 1 || ms < best_ms) {
+        best_ms = ms;
+        best_budget = budget;
+        best_config = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e == cudaSuccess)  // leave the workspace prepared with the winner
+    e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, dev_workspace,
+                           ctx->stream, static_cast<uint64_t>(best_budget) << 20);
+  if (e != cudaSuccess) return PCR_ERR_CUDA;
+  fill_tuning(out, best_budget, best_config, 0, tried, best_ms, default_ms);
+  if (cache_path) write_tuning(cache_path, gpu, shape, *out);
+  return PCR_OK;
 }
 
 pcr_status pcr_batch_launch(pcr_ctx* ctx, const void* dev_workspace, int config) {
@@ -508,6 +685,7 @@ const char* pcr_status_string(pcr_status status) {
     case PCR_ERR_WORKSPACE: return "workspace missing or too small";
     case PCR_ERR_TIMEOUT: return "device wait timed out";
     case PCR_ERR_UNSUPPORTED: return "unsupported";
+    case PCR_ERR_BUSY: return "queue full";
     default: return "unknown status";
   }
 }

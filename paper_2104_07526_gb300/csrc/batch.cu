@@ -139,8 +139,8 @@ __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&
 // early depth test (on GB300 the fastest exact form once the buffer is
 // filling: warp deduplication saves no atomics after the early test), both
 // from one projection.
-template <int U>
-__global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restrict__ tables) {
+template <int U, int T>
+__global__ void __launch_bounds__(T) k_batch_phase1(const Tables* __restrict__ tables) {
   __shared__ Shared sh;
   load_tables(tables, 0, sh);
   const uint64_t pol_stream = policy_evict_first();
@@ -179,9 +179,9 @@ __global__ void __launch_bounds__(kThreads) k_batch_phase1(const Tables* __restr
 }
 
 // Phase 2: HQ colours (warp-aggregated adds) for the HQ views of the pass.
-// Held to 64 registers: 4 resident blocks instead of 3.
-template <int U>
-__global__ void __launch_bounds__(kThreads, 4) k_batch_phase2(const Tables* __restrict__ tables) {
+// Held to 64 registers (1024 threads per SM) at either block size.
+template <int U, int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_batch_phase2(const Tables* __restrict__ tables) {
   __shared__ Shared sh;
   load_tables(tables, 1, sh);
   const uint64_t pol_stream = policy_evict_first();
@@ -275,28 +275,41 @@ __global__ void __launch_bounds__(kThreads) k_batch_resolve(const Tables* __rest
   }
 }
 
-// Launch configurations the autotuner chooses among: points per lane of
-// the two geometry phases (phase 2 keeps more state per point).
-struct BatchConfig {
-  int unroll1;
-  int unroll2;
-};
-constexpr BatchConfig kConfigs[] = {{4, 4}, {4, 2}, {2, 4}, {2, 2}};
-constexpr int kNumConfigs = sizeof(kConfigs) / sizeof(kConfigs[0]);
+// Launch configurations the autotuner chooses among: threads per block, and
+// points per lane of the two geometry phases (phase 2 keeps more state per
+// point).  Configuration c: threads 256 << (c >> 2), phase-1 points per lane
+// (c & 2) ? 2 : 4, phase-2 (c & 1) ? 2 : 4.  Configuration 0 is the default.
+constexpr int kNumConfigs = 8;
 
 template <auto K>
-int batch_resident() {
-  static const int blocks = [] {
+int batch_resident(int threads) {
+  static const int blocks = [threads] {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, kThreads, 0) != cudaSuccess || b < 1) b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, threads, 0) != cudaSuccess || b < 1) b = 1;
     return b;
   }();
   return blocks;
 }
 
-template <auto K>
+template <auto K, int T>
 void launch_persistent(const Tables* t, cudaStream_t s, const Device& d) {
-  K<<<d.num_sms * batch_resident<K>(), kThreads, 0, s>>>(t);
+  K<<<d.num_sms * batch_resident<K>(T), T, 0, s>>>(t);
+}
+
+template <int T>
+void launch_phases(const Tables* t, int config, cudaStream_t s, const Device& d) {
+  if (config & 2) launch_persistent<k_batch_phase1<2, T>, T>(t, s, d);
+  else launch_persistent<k_batch_phase1<4, T>, T>(t, s, d);
+  if (config & 1) launch_persistent<k_batch_phase2<2, T>, T>(t, s, d);
+  else launch_persistent<k_batch_phase2<4, T>, T>(t, s, d);
+}
+
+template <int T>
+void prewarm_phases() {
+  batch_resident<k_batch_phase1<4, T>>(T);
+  batch_resident<k_batch_phase2<4, T>>(T);
+  batch_resident<k_batch_phase1<2, T>>(T);
+  batch_resident<k_batch_phase2<2, T>>(T);
 }
 
 }  // namespace
@@ -403,10 +416,10 @@ void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, cons
 
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                           uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
-                          cudaStream_t s) {
+                          cudaStream_t s, uint64_t l2_budget) {
   void* host = ::operator new(sizeof(Tables), std::nothrow);
   if (!host) return cudaErrorMemoryAllocation;
-  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host, kBatchL2Budget);
+  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host, l2_budget);
   cudaError_t e = cudaMemcpyAsync(workspace, host, sizeof(Tables), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   static_cast<Tables*>(host)->~Tables();
@@ -415,23 +428,21 @@ cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, co
 }
 
 cudaError_t batch_prewarm(const Device&) {
-  batch_resident<k_batch_phase1<4>>();
-  batch_resident<k_batch_phase2<4>>();
-  batch_resident<k_batch_phase1<2>>();
-  batch_resident<k_batch_phase2<2>>();
+  prewarm_phases<256>();
+  prewarm_phases<512>();
   return cudaGetLastError();
 }
+
+int batch_config_threads(int config) { return 256 << (config >> 2); }
+int batch_config_unroll(int config, int phase) { return (config & (phase == 0 ? 2 : 1)) ? 2 : 4; }
 
 cudaError_t batch_launch(const void* workspace, int config, cudaStream_t s, const Device& d) {
   if (config < 0 || config >= kNumConfigs) return cudaErrorInvalidValue;
   const Tables* t = static_cast<const Tables*>(workspace);
   const int screen_blocks = d.num_sms * 8;
-  const BatchConfig cfg = kConfigs[config];
   k_batch_clear<<<screen_blocks, kThreads, 0, s>>>(t);
-  if (cfg.unroll1 == 4) launch_persistent<k_batch_phase1<4>>(t, s, d);
-  else launch_persistent<k_batch_phase1<2>>(t, s, d);
-  if (cfg.unroll2 == 4) launch_persistent<k_batch_phase2<4>>(t, s, d);
-  else launch_persistent<k_batch_phase2<2>>(t, s, d);
+  if (config & 4) launch_phases<512>(t, config, s, d);
+  else launch_phases<256>(t, config, s, d);
   k_batch_resolve<<<screen_blocks, kThreads, 0, s>>>(t);
   return cudaGetLastError();
 }

@@ -115,7 +115,11 @@ constexpr uint64_t kServedL2Budget = 64ull << 20;
 int batch_num_configs();
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                           uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
-                          cudaStream_t s);
+                          cudaStream_t s, uint64_t l2_budget = kBatchL2Budget);
+// Threads per block and points per lane (phase 0 or 1) of a launch
+// configuration.
+int batch_config_threads(int config);
+int batch_config_unroll(int config, int phase);
 cudaError_t batch_launch(const void* workspace, int config, cudaStream_t s, const Device& d);
 // Run the occupancy queries of every configuration once (before a capture).
 cudaError_t batch_prewarm(const Device& d);

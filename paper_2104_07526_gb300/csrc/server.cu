@@ -92,7 +92,7 @@ struct Cloud {
   bool uploaded_once = false;
 };
 
-enum : int { kQueued = 0, kRunning = 1, kDone = 2 };
+enum : int { kQueued = 0, kRunning = 1, kDone = 2, kExpired = 3 };
 
 struct Request {
   uint32_t cloud = 0;
@@ -143,6 +143,7 @@ struct pcr_server {
 namespace {
 
 using pcr::kDone;
+using pcr::kExpired;
 using pcr::kQueued;
 using pcr::kRunning;
 
@@ -255,6 +256,46 @@ cudaError_t launch_single_views(pcr_server* s, const std::vector<uint64_t>& take
   return cudaSuccess;
 }
 
+// Requests still queued deadline_us after their submission expire: they
+// leave the queue unrendered and are reported like finished ones.  The queue
+// is in arrival order, so they are at its front.
+void expire(pcr_server* s, uint32_t* completed) {
+  if (s->cfg.deadline_us == 0) return;
+  const double t = pcr::now_us();
+  while (!s->queue.empty()) {
+    pcr::Request& r = s->requests[s->queue.front()];
+    if (t - r.t_submit < s->cfg.deadline_us) break;
+    r.state = kExpired;
+    r.t_done = t;
+    s->finished.push_back(s->queue.front());
+    s->queue.pop_front();
+    ++s->stats.expired;
+    if (completed) ++*completed;
+  }
+}
+
+// The clouds a new batch may take requests of, or an empty list for any
+// cloud (arrival order with no cloud limit).  Arrival order: filled as the
+// queue is walked.  Largest groups: the oldest request's cloud, then the
+// clouds with the most queued requests.
+std::vector<uint32_t> batch_cloud_choice(const pcr_server* s, uint32_t cloud_cap) {
+  std::vector<uint32_t> chosen;
+  if (s->cfg.policy != PCR_SERVE_LARGEST_GROUP || s->queue.empty()) return chosen;
+  std::unordered_map<uint32_t, uint32_t> count;
+  for (uint64_t tk : s->queue) ++count[s->requests.at(tk).cloud];
+  const uint32_t oldest = s->requests.at(s->queue.front()).cloud;
+  std::vector<std::pair<uint32_t, uint32_t>> by_count(count.begin(), count.end());
+  std::sort(by_count.begin(), by_count.end(), [](const auto& a, const auto& b) {
+    return a.second != b.second ? a.second > b.second : a.first < b.first;
+  });
+  chosen.push_back(oldest);
+  for (const auto& kv : by_count) {
+    if (chosen.size() >= cloud_cap) break;
+    if (kv.first != oldest) chosen.push_back(kv.first);
+  }
+  return chosen;
+}
+
 // Form and launch one batch on the free in-flight slot `f`.  Returns
 // PCR_OK with nothing launched when no queued request can run now.
 pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
@@ -262,13 +303,17 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
   std::vector<uint64_t> take;
   std::vector<uint32_t> batch_clouds;  // distinct cloud ids, in order of first use
   std::vector<uint32_t> uploads;       // clouds this batch uploads
+  const uint32_t cloud_cap =
+      std::min<uint32_t>(s->cfg.max_batch_clouds ? s->cfg.max_batch_clouds : PCR_BATCH_MAX_CLOUDS,
+                         PCR_BATCH_MAX_CLOUDS);
+  const std::vector<uint32_t> allowed = batch_cloud_choice(s, cloud_cap);
   for (auto it = s->queue.begin(); it != s->queue.end();) {
     if (take.size() >= s->cfg.max_batch_views || s->free_slots.empty()) break;
     pcr::Request& r = s->requests[*it];
     pcr::Cloud& c = s->clouds[r.cloud];
     const bool in_batch = std::find(batch_clouds.begin(), batch_clouds.end(), r.cloud) != batch_clouds.end();
-    const uint32_t cloud_cap = s->cfg.max_batch_clouds ? s->cfg.max_batch_clouds : PCR_BATCH_MAX_CLOUDS;
-    if (!in_batch && batch_clouds.size() >= std::min<uint32_t>(cloud_cap, PCR_BATCH_MAX_CLOUDS)) {
+    const bool excluded = !allowed.empty() && std::find(allowed.begin(), allowed.end(), r.cloud) == allowed.end();
+    if (excluded || (!in_batch && batch_clouds.size() >= cloud_cap)) {
       ++it;
       continue;
     }
@@ -406,6 +451,7 @@ pcr_status pcr_server_create(pcr_ctx* ctx, const pcr_server_config* cfg, pcr_ser
     return PCR_ERR_ARG;
   if (!(cfg->depth_factor > 0.0f) || !(cfg->depth_factor < 3.0e38f)) return PCR_ERR_ARG;
   if (cfg->batch_config < 0 || cfg->batch_config >= pcr::batch_num_configs()) return PCR_ERR_ARG;
+  if (cfg->policy != PCR_SERVE_ARRIVAL && cfg->policy != PCR_SERVE_LARGEST_GROUP) return PCR_ERR_ARG;
   pcr_server* s = new (std::nothrow) pcr_server();
   if (!s) return PCR_ERR_CUDA;
   s->dev = pcr::ctx_device(ctx);
@@ -494,6 +540,10 @@ pcr_status pcr_server_submit(pcr_server* s, const pcr_request* req, uint64_t* ti
   if (req->flags == 0 || (req->flags & ~static_cast<uint32_t>(PCR_BATCH_BASIC | PCR_BATCH_HQ))) return PCR_ERR_ARG;
   const pcr::Cloud& c = s->clouds[req->cloud_id];
   if (!c.device && pcr::align_up(c.bytes) > s->cfg.arena_bytes - s->cloud_base) return PCR_ERR_WORKSPACE;  // never fits
+  if (s->cfg.max_queue && s->queue.size() >= s->cfg.max_queue) {
+    ++s->stats.rejected;
+    return PCR_ERR_BUSY;
+  }
   pcr::Request r;
   r.cloud = req->cloud_id;
   std::memcpy(r.matrix, req->matrix, sizeof(r.matrix));
@@ -517,6 +567,7 @@ pcr_status pcr_server_step(pcr_server* s, uint32_t* completed) {
   cudaGetDevice(&prev);
   if (prev != s->dev.id) cudaSetDevice(s->dev.id);
   pcr_status st = retire(s, completed);
+  expire(s, completed);
   for (pcr::Inflight& f : s->inflight) {
     if (st != PCR_OK || s->queue.empty()) break;
     if (f.busy) continue;
@@ -539,8 +590,16 @@ pcr_status pcr_server_state(pcr_server* s, uint64_t ticket, int* state) {
 pcr_status pcr_server_get_result(pcr_server* s, uint64_t ticket, pcr_server_result* out) {
   if (!s || !out) return PCR_ERR_ARG;
   auto it = s->requests.find(ticket);
-  if (it == s->requests.end() || it->second.state != kDone) return PCR_ERR_ARG;
+  if (it == s->requests.end() || (it->second.state != kDone && it->second.state != kExpired)) return PCR_ERR_ARG;
   const pcr::Request& r = it->second;
+  if (r.state == kExpired) {
+    *out = pcr_server_result{};
+    out->width = r.width;
+    out->height = r.height;
+    out->submit_us = r.t_submit;
+    out->done_us = r.t_done;
+    return PCR_OK;
+  }
   const SlotPtrs p = slot_ptrs(s, r.slot);
   out->width = r.width;
   out->height = r.height;
@@ -572,8 +631,8 @@ pcr_status pcr_server_poll_completed(pcr_server* s, uint64_t* tickets, uint32_t 
 pcr_status pcr_server_release(pcr_server* s, uint64_t ticket) {
   if (!s) return PCR_ERR_ARG;
   auto it = s->requests.find(ticket);
-  if (it == s->requests.end() || it->second.state != kDone) return PCR_ERR_ARG;
-  s->free_slots.push_back(it->second.slot);
+  if (it == s->requests.end() || (it->second.state != kDone && it->second.state != kExpired)) return PCR_ERR_ARG;
+  if (it->second.state == kDone) s->free_slots.push_back(it->second.slot);
   s->requests.erase(it);
   return PCR_OK;
 }

@@ -16,6 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpcr.so")
 
 PCR_OK, PCR_ERR_ARG, PCR_ERR_CUDA, PCR_ERR_WORKSPACE, PCR_ERR_TIMEOUT, PCR_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+PCR_ERR_BUSY = -6
+PCR_SERVE_ARRIVAL, PCR_SERVE_LARGEST_GROUP = 0, 1
 
 PCR_VARIANT_ATOMICMIN = 0
 PCR_VARIANT_EARLYZ = 1
@@ -65,12 +67,20 @@ class PcrBatchView(C.Structure):
                 ("hq_rg", C.c_void_p), ("hq_ba", C.c_void_p), ("hq_image", C.c_void_p)]
 
 
+class PcrBatchTuning(C.Structure):
+    """pcr_batch_tuning"""
+    _fields_ = [("l2_budget_mb", C.c_uint32), ("config", C.c_int32), ("threads", C.c_uint32),
+                ("unroll1", C.c_uint32), ("unroll2", C.c_uint32), ("from_cache", C.c_uint32), ("tried", C.c_uint32),
+                ("pad", C.c_uint32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+
 class PcrServerConfig(C.Structure):
     """pcr_server_config"""
     _fields_ = [("dev_arena", C.c_void_p), ("arena_bytes", C.c_uint64), ("max_width", C.c_uint32),
                 ("max_height", C.c_uint32), ("num_slots", C.c_uint32), ("max_batch_views", C.c_uint32),
                 ("max_inflight", C.c_uint32), ("streams", C.c_uint32), ("max_batch_clouds", C.c_uint32),
-                ("batch_config", C.c_int32), ("depth_factor", C.c_float), ("background_rgba", C.c_uint32)]
+                ("batch_config", C.c_int32), ("depth_factor", C.c_float), ("background_rgba", C.c_uint32),
+                ("max_queue", C.c_uint32), ("deadline_us", C.c_uint32), ("policy", C.c_uint32)]
 
 
 class PcrRequest(C.Structure):
@@ -91,10 +101,10 @@ class PcrServerStats(C.Structure):
     """pcr_server_stats"""
     _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "batches", "views_launched", "uploads",
                                           "evictions", "bytes_uploaded", "points_rendered", "peak_queue", "queued",
-                                          "resident_clouds", "resident_bytes")]
+                                          "resident_clouds", "resident_bytes", "rejected", "expired")]
 
 
-PCR_REQUEST_QUEUED, PCR_REQUEST_RUNNING, PCR_REQUEST_DONE = 0, 1, 2
+PCR_REQUEST_QUEUED, PCR_REQUEST_RUNNING, PCR_REQUEST_DONE, PCR_REQUEST_EXPIRED = 0, 1, 2, 3
 
 
 class PcrError(RuntimeError):
@@ -138,6 +148,8 @@ _SIGS = {
     "pcr_batch_prepare": [_VP, C.POINTER(PcrBatchCloud), _U32, C.POINTER(PcrBatchView), _U32, _FLT, _U32, _VP, _U64],
     "pcr_batch_launch": [_VP, _VP, _INT],
     "pcr_batch_autotune": [_VP, _VP, C.POINTER(_INT)],
+    "pcr_batch_tune": [_VP, C.POINTER(PcrBatchCloud), _U32, C.POINTER(PcrBatchView), _U32, _FLT, _U32, _VP, _U64,
+                       C.c_char_p, C.POINTER(PcrBatchTuning)],
     "pcr_batch_capture": [_VP, _VP, _INT, C.POINTER(_VP)],
     "pcr_graph_launch": [_VP, _VP],
     "pcr_graph_destroy": [_VP],
@@ -387,6 +399,19 @@ def pcr_batch_autotune(ctx: int, workspace) -> int:
     return out.value
 
 
+def pcr_batch_tune(ctx: int, clouds, views, depth_factor: float, background_rgba: int, workspace,
+                   cache_path: str | None = None) -> dict:
+    """Prepare the batch with its tuned L2 budget and pick its launch
+    configuration (see pcr.h); returns the pcr_batch_tuning fields."""
+    ca = (PcrBatchCloud * len(clouds))(*clouds)
+    va = (PcrBatchView * len(views))(*views)
+    out = PcrBatchTuning()
+    _check(lib().pcr_batch_tune(ctx, ca, len(clouds), va, len(views), depth_factor, background_rgba & 0xFFFFFFFF,
+                                _dptr(workspace, "workspace"), _nbytes(workspace) if workspace is not None else 0,
+                                cache_path.encode() if cache_path else None, C.byref(out)), "pcr_batch_tune")
+    return {k: getattr(out, k) for k, _ in PcrBatchTuning._fields_ if k != "pad"}
+
+
 def pcr_batch_capture(ctx: int, workspace, config: int) -> int:
     out = _VP()
     _check(lib().pcr_batch_capture(ctx, _dptr(workspace, "workspace"), config, C.byref(out)), "pcr_batch_capture")
@@ -403,11 +428,12 @@ def pcr_graph_destroy(graph_exec: int):
 
 def pcr_server_create(ctx: int, arena, max_width: int, max_height: int, num_slots: int, max_batch_views: int = 64,
                       max_inflight: int = 2, streams: int = 0, max_batch_clouds: int = 0, batch_config: int = 0,
-                      depth_factor: float = 1.01, background_rgba: int = 0) -> int:
+                      depth_factor: float = 1.01, background_rgba: int = 0, max_queue: int = 0,
+                      deadline_us: int = 0, policy: int = PCR_SERVE_ARRIVAL) -> int:
     """arena: CUDA uint8 tensor (the server's device memory)."""
     cfg = PcrServerConfig(_dptr(arena, "arena"), _nbytes(arena), max_width, max_height, num_slots, max_batch_views,
                           max_inflight, streams, max_batch_clouds, batch_config, depth_factor,
-                          background_rgba & 0xFFFFFFFF)
+                          background_rgba & 0xFFFFFFFF, max_queue, deadline_us, policy)
     out = _VP()
     _check(lib().pcr_server_create(ctx, C.byref(cfg), C.byref(out)), "pcr_server_create")
     return out.value
@@ -433,6 +459,8 @@ def pcr_server_add_device_cloud(srv: int, cloud_id: int, dev_points, n: int | No
 
 
 def pcr_server_submit(srv: int, cloud_id: int, matrix, width: int, height: int, flags: int) -> int:
+    """Ticket of the queued request; raises PcrError (status PCR_ERR_BUSY)
+    when admission control refuses it."""
     vals = [float(v) for v in (matrix.reshape(-1).tolist() if hasattr(matrix, "reshape") else matrix)]
     req = PcrRequest(cloud_id, (C.c_float * 16)(*vals), width, height, flags)
     t = _U64()

@@ -182,3 +182,45 @@ def test_batch_table_limits(ctx, oracle):
             _poison(bufs)
             pcr.pcr_batch_launch(ctx, ws, config)
             _check(bufs, expected, f"limits config {config}")
+
+
+def test_batch_tune_chooses_and_caches(ctx, oracle, tmp_path):
+    """pcr_batch_tune times every (L2 budget, launch configuration) pair,
+    leaves the workspace prepared with the winner, and records it per (GPU,
+    batch shape): a second call reads the cache and times nothing.  The
+    tuned batch renders the oracle's buffers."""
+    clouds, views = _make_batch()
+    expected = _expected(oracle, clouds, views)
+    dev = [torch.from_numpy(c.copy()).cuda() for c in clouds]
+    bufs = [_buffers(W, H) for (_, _, W, H, _) in views]
+    vs = []
+    for (c, m, W, H, flags), b in zip(views, bufs):
+        kw = {}
+        if flags & BASIC:
+            kw.update(keys=b["keys"], image=b["image"])
+        if flags & HQ:
+            kw.update(hq_depth=b["hq_depth"], hq_rg=b["hq_rg"], hq_ba=b["hq_ba"], hq_image=b["hq_image"])
+        vs.append(pcr.batch_view(m, W, H, c, flags, **kw))
+    cs_ = [pcr.batch_cloud(d) for d in dev]
+    ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device="cuda")
+    cache = str(tmp_path / "batch_tuning.jsonl")
+    first = pcr.pcr_batch_tune(ctx, cs_, vs, 1.01, BG, ws, cache)
+    assert first["from_cache"] == 0 and first["tried"] == 3 * pcr.pcr_batch_num_configs()
+    assert first["l2_budget_mb"] in (64, 96, 128) and 0 <= first["config"] < pcr.pcr_batch_num_configs()
+    assert first["threads"] in (256, 512) and first["unroll1"] in (2, 4) and first["unroll2"] in (2, 4)
+    assert 0 < first["best_ms"] <= first["default_ms"]
+    _poison(bufs)
+    pcr.pcr_batch_launch(ctx, ws, first["config"])
+    _check(bufs, expected, "tuned")
+    again = pcr.pcr_batch_tune(ctx, cs_, vs, 1.01, BG, ws, cache)
+    assert again["from_cache"] == 1 and again["tried"] == 0
+    assert (again["l2_budget_mb"], again["config"]) == (first["l2_budget_mb"], first["config"])
+    _poison(bufs)
+    pcr.pcr_batch_launch(ctx, ws, again["config"])
+    _check(bufs, expected, "from cache")
+    with open(cache) as f:
+        lines = f.read().splitlines()
+    assert len(lines) == 1 and '"budget_mb": %d' % first["l2_budget_mb"] in lines[0]
+    # another shape misses the cache
+    other = pcr.pcr_batch_tune(ctx, cs_, vs[:3], 1.01, BG, ws, cache)
+    assert other["from_cache"] == 0

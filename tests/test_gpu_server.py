@@ -291,3 +291,73 @@ def test_full_batches_of_small_requests(ctx, oracle):
         assert st["completed"] == 300 and st["batches"] <= 20
     finally:
         pcr.pcr_server_destroy(srv)
+
+
+def test_largest_group_policy_keeps_results_exact(ctx, oracle):
+    """Largest groups first: batches take the oldest request's cloud and the
+    clouds with the most queued requests; every result is still exact, and
+    views of one cloud share batches."""
+    clouds = _clouds()
+    dev = [torch.from_numpy(c.copy()).cuda() for c in clouds]
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, 200, 150, num_slots=40, max_batch_views=8, max_inflight=2,
+                                max_batch_clouds=2, background_rgba=BG, policy=pcr.PCR_SERVE_LARGEST_GROUP)
+    try:
+        for i, d in enumerate(dev):
+            pcr.pcr_server_add_device_cloud(srv, i, d)
+        rng = np.random.default_rng(44)
+        reqs = _requests(rng, clouds, 36, 200, 150)
+        by_ticket = {pcr.pcr_server_submit(srv, *r): r for r in reqs}
+
+        def finish(t):
+            c, m, W, H, flags = by_ticket.pop(t)
+            _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+            pcr.pcr_server_release(srv, t)
+
+        _drain(srv, list(by_ticket), finish)
+        assert not by_ticket
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["completed"] == len(reqs) and st["batches"] <= len(reqs) // 2
+    finally:
+        pcr.pcr_server_destroy(srv)
+
+
+def test_admission_bound_and_deadline(ctx, oracle):
+    """max_queue refuses submissions beyond it (PCR_ERR_BUSY, nothing queued);
+    requests queued past deadline_us expire unrendered and are reported,
+    while fresh ones render exactly."""
+    cloud = scenes.sphere_plane(30_011, seed=5).numpy()
+    dev = torch.from_numpy(cloud.copy()).cuda()
+    arena = torch.empty(128 << 20, dtype=torch.uint8, device="cuda")
+    W, H = 96, 64
+    m = scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), W, H)
+    srv = pcr.pcr_server_create(ctx, arena, W, H, num_slots=8, max_batch_views=4, max_inflight=1,
+                                background_rgba=BG, max_queue=5, deadline_us=20_000)
+    try:
+        pcr.pcr_server_add_device_cloud(srv, 0, dev)
+        old = [pcr.pcr_server_submit(srv, 0, m, W, H, BASIC) for _ in range(5)]
+        with pytest.raises(pcr.PcrError) as e:
+            pcr.pcr_server_submit(srv, 0, m, W, H, BASIC)
+        assert e.value.status == pcr.PCR_ERR_BUSY
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["rejected"] == 1 and st["queued"] == 5 and st["submitted"] == 5
+        time.sleep(0.05)  # all five are now past their 20 ms deadline
+        pcr.pcr_server_step(srv)
+        assert [pcr.pcr_server_state(srv, t) for t in old] == [pcr.PCR_REQUEST_EXPIRED] * 5
+        assert sorted(pcr.pcr_server_poll_completed(srv)) == sorted(old)
+        for t in old:
+            res = pcr.pcr_server_get_result(srv, t)
+            assert not res.keys and not res.image and res.points == 0 and res.done_us >= res.submit_us
+            pcr.pcr_server_release(srv, t)
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["expired"] == 5 and st["queued"] == 0 and st["batches"] == 0
+        fresh = [pcr.pcr_server_submit(srv, 0, m, W, H, f) for f in (BASIC, HQ, BASIC | HQ)]
+        _drain(srv, fresh)
+        for t, f in zip(fresh, (BASIC, HQ, BASIC | HQ)):
+            _check_result(ctx, srv, t, cloud, m, W, H, f, oracle)
+            pcr.pcr_server_release(srv, t)
+    finally:
+        pcr.pcr_server_destroy(srv)
+    with pytest.raises(pcr.PcrError) as e:
+        pcr.pcr_server_create(ctx, arena, W, H, 2, policy=7)
+    assert e.value.status == pcr.PCR_ERR_ARG
