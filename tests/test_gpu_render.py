@@ -32,6 +32,29 @@ def sphere():
     return scenes.sphere_plane(200_003, seed=0).numpy()
 
 
+def test_sphere1M_config_in_every_order(r, oracle):
+    """The 1M-point sphere-and-plane scene at 640x480, as its configuration
+    states it, in its generation order and after each one-time reorder: every
+    exact variant's keys and the resolved image equal the oracle's."""
+    from gpu_helpers import reorder_gpu
+    cloud = scenes.sphere_plane(1_000_000, seed=0)
+    view = scenes.sphere_plane_views()[0]
+    assert (view.width, view.height) == (640, 480)
+    dev = cloud.cuda()
+    for mode in (None, pcr.PCR_ORDER_MORTON, pcr.PCR_ORDER_MORTON_SHUFFLE128, pcr.PCR_ORDER_SHUFFLE):
+        pts = dev.clone()
+        if mode is not None:
+            reorder_gpu(r.h, pts, 0x5EED, mode)
+        host = pts.cpu().numpy()
+        expect = oracle.render_basic(host, view.matrix, view.width, view.height)
+        img = oracle.resolve_basic(expect, host, 0)
+        r.upload(pts)
+        r.view(view.matrix, view.width, view.height)
+        for v in EXACT:
+            assert np.array_equal(r.render_basic(v), expect), (mode, pcr.VARIANT_NAMES[v])
+            assert np.array_equal(r.resolve(pcr.PCR_RESOLVE_BASIC, 0), img), (mode, pcr.VARIANT_NAMES[v])
+
+
 def test_sphere_plane_all_variants(r, oracle, sphere):
     view = scenes.sphere_plane_views()[0]
     expect = oracle.render_basic(sphere, view.matrix, view.width, view.height)
