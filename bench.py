@@ -94,6 +94,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (8 clouds x 8 views) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson request stream) measurement")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the served request stream")
+    ap.add_argument("--part", choices=["reorder", "batch"],
+                    help="time one part alone and print its timings (for running under a profiler): every "
+                         "vertex order of the scan scene (--points, --orders), or the 8-cloud x 8-view batch")
+    ap.add_argument("--points", type=int, default=100_000_000, help="scan-scene points for --part reorder")
+    ap.add_argument("--orders", default="morton,morton_shuffle128,shuffle,morton63,morton63_shuffle128",
+                    help="comma-separated vertex orders for --part reorder")
     return ap.parse_args(argv)
 
 
@@ -1098,9 +1104,71 @@ def run_sweep(h, pcr, orders, views, n, fb, stream) -> dict:
     return out
 
 
+ORDER_MODES = {"morton": 0, "morton_shuffle128": 1, "shuffle": 2, "morton63": 3, "morton63_shuffle128": 4}
+
+
+def run_part(args) -> int:
+    """One part alone, through the C ABI, so a profiler sees the library's
+    own kernels and little else.  reorder: each order of the scan scene from
+    its generation order, run twice (the first warms up), CUDA events.  batch:
+    the 8 boxes clouds x 8 orbit views (shuffled-Morton order, basic + HQ),
+    prepared once and launched four times with configuration 0."""
+    import torch
+    from paper_2104_07526_gb300 import build as lib_build
+    from paper_2104_07526_gb300 import pcr, scenes
+    lib_build.build()
+    stream = torch.cuda.current_stream()
+    ctx = pcr.Context(0, stream=stream)
+    h = ctx.handle
+    out = {}
+    if args.part == "reorder":
+        n = args.points
+        cloud = scenes.scan(n, seed=0, device="cuda")
+        ws = torch.empty(pcr.pcr_reorder_workspace_size(n), dtype=torch.uint8, device="cuda")
+        for name in args.orders.split(","):
+            best = None
+            for _ in range(2):
+                buf = cloud.clone()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(stream)
+                pcr.pcr_reorder_morton_shuffle128(h, buf, n, 0x5EED, ORDER_MODES[name], ws)
+                b.record(stream)
+                torch.cuda.synchronize()
+                best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
+                del buf
+            out[name] = round(best, 3)
+    else:
+        clouds = [scenes.boxes(nc, seed=i, device="cuda") for i, nc in enumerate(scenes.BATCH_CLOUD_SIZES)]
+        vertex_order(h, pcr, clouds, "cuda")
+        views = scenes.batch_views(len(clouds))
+        bufs = [{k: torch.empty(v.width * v.height, dtype=t, device="cuda") for k, t in
+                 (("keys", torch.int64), ("image", torch.int32), ("hq_depth", torch.int32), ("hq_rg", torch.int64),
+                  ("hq_ba", torch.int64), ("hq_image", torch.int32))} for _, v in views]
+        flags = pcr.PCR_BATCH_BASIC | pcr.PCR_BATCH_HQ
+        ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device="cuda")
+        pcr.pcr_batch_prepare(h, [pcr.batch_cloud(c) for c in clouds],
+                              [pcr.batch_view(v.matrix, v.width, v.height, c, flags, **b) for (c, v), b in
+                               zip(views, bufs)], 1.01, 0, ws)
+        times = []
+        for _ in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pcr.pcr_batch_launch(h, ws, 0)
+            b.record(stream)
+            torch.cuda.synchronize()
+            times.append(round(a.elapsed_time(b), 3))
+        out["batch_ms"] = times
+    ctx.close()
+    print(json.dumps({"part": args.part, **out}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     cfg = CONFIGS[args.config]
+    if args.part:
+        return run_part(args)
     if args.impl == "reference":
         return run_reference(args, cfg)
     return run_ours(args, cfg)

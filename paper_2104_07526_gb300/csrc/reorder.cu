@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t se
                                                      uint4* __restrict__ copy) {
   for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < count; i += gridDim.x * 256ull) {
     keys[i] = static_cast<uint32_t>(splitmix64(seed, i) >> 32);
-    vals[i] = static_cast<uint32_t>(i);
+    if (vals) vals[i] = static_cast<uint32_t>(i);
     if (copy) __stcs(copy + i, __ldcs(pts + i));
   }
 }
@@ -362,14 +362,21 @@ __device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_sr
 }
 
 // `cin`/`cout` (may be null): a second 32-bit value carried with each key
-// (the high words of 63-bit codes while their low words are sorted).
+// (the high words of 63-bit codes while their low words are sorted).  `vin`/
+// `vout` may be null when no value is carried.  With REC, the 16-byte point
+// record `rin[i]` moves with its key to `rout` (the random order sorts the
+// records themselves: every pass reads them in tile order and writes them in
+// digit runs, instead of one random gather at the end).
+template <bool REC>
 __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
                                                                   uint32_t* __restrict__ kout,
                                                                   uint32_t* __restrict__ vout, uint32_t n, int shift,
                                                                   const uint32_t* __restrict__ offsets,
                                                                   uint32_t tiles, const uint32_t* __restrict__ cin,
-                                                                  uint32_t* __restrict__ cout) {
+                                                                  uint32_t* __restrict__ cout,
+                                                                  const uint4* __restrict__ rin,
+                                                                  uint4* __restrict__ rout) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
   uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
@@ -451,8 +458,9 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
     const uint32_t d = (key >> shift) & (kRadix - 1);
     const uint32_t g = global_start[d] + (l - local_start[d]);
     kout[g] = key;
-    vout[g] = __ldg(vin + tile_base + src);
+    if (vout) vout[g] = __ldg(vin + tile_base + src);
     if (cout) cout[g] = __ldg(cin + tile_base + src);
+    if constexpr (REC) __stcs(rout + g, __ldg(rin + tile_base + src));
   }
 }
 
@@ -566,22 +574,30 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 
 // Stable sort of count (key, value) pairs on the low key_bits bits.  The
 // result ends in buffer index `out` (0 or 1).  With `carry` (may be null),
-// a second value per key moves with it through its own two buffers.
+// a second value per key moves with it through its own two buffers; with
+// `recs` (may be null), a 16-byte record does.  vals may hold null buffers
+// when no value is needed.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
-                       uint32_t* partials, cudaStream_t s, int& out, uint32_t* const* carry = nullptr) {
+                       uint32_t* partials, cudaStream_t s, int& out, uint32_t* const* carry = nullptr,
+                       uint4* const* recs = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
-  cudaError_t e = cudaFuncSetAttribute(k_sort_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(kScatterSmem));
+  cudaError_t e = cudaFuncSetAttribute(recs ? k_sort_scatter<true> : k_sort_scatter<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kScatterSmem));
   if (e != cudaSuccess) return e;
   for (int shift = 0; shift < key_bits; shift += kDigitBits) {
     k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
     e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
-    k_sort_scatter<<<tiles, kSortThreads, kScatterSmem, s>>>(keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count,
-                                                             shift, counts, tiles, carry ? carry[out] : nullptr,
-                                                             carry ? carry[out ^ 1] : nullptr);
+    if (recs)
+      k_sort_scatter<true><<<tiles, kSortThreads, kScatterSmem, s>>>(
+          keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, nullptr, nullptr, recs[out],
+          recs[out ^ 1]);
+    else
+      k_sort_scatter<false><<<tiles, kSortThreads, kScatterSmem, s>>>(
+          keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
+          carry ? carry[out ^ 1] : nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     out ^= 1;
@@ -702,8 +718,17 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   // the records, except for the 63-bit code, whose sort uses its region
   const bool wide = mode == PCR_ORDER_MORTON63 || mode == PCR_ORDER_MORTON63_SHUFFLE128;
   if (mode == PCR_ORDER_SHUFFLE) {
-    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], vals[0], pts, copy);
-    e = radix_sort(keys, vals, n, 32, counts, partials, s, out);
+    // the records themselves are sorted by their random keys (4 passes, an
+    // even number: they end back in the caller's buffer); indices ride along
+    // only when the permutation is asked for
+    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], perm_out ? vals[0] : nullptr, nullptr, nullptr);
+    uint32_t* ivals[2] = {perm_out ? vals[0] : nullptr, perm_out ? vals[1] : nullptr};
+    uint4* recs[2] = {pts, copy};
+    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, nullptr, recs);
+    if (e != cudaSuccess) return e;
+    if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes
+    if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
+    return e;
   } else if (!wide) {
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
