@@ -888,7 +888,8 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
                         "(256^2..2048^2), basic + HQ",
             "per_request_ms": per_ms, "per_request_launches": 7 * len(views), "batched_graph_ms": batched_ms,
             "batched_launches": 4, "speedup": per_ms / batched_ms, "identical": identical, "config": config,
-            "tuning": {**{k: tuning[k] for k in ("l2_budget_mb", "config", "threads", "unroll1", "unroll2", "tried")},
+            "tuning": {**{k: tuning[k] for k in ("l2_budget_mb", "config", "threads", "unroll1", "unroll2",
+                                                 "single_colors", "tried")},
                        "tuned_ms": tuning["best_ms"], "default_ms": tuning["default_ms"],
                        "speedup_over_default": tuning["default_ms"] / tuning["best_ms"],
                        "second_call_from_cache": bool(cached["from_cache"])},

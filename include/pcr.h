@@ -344,8 +344,10 @@ PCR_API pcr_status pcr_batch_workspace_size(uint64_t *bytes);
 
 /* Number of launch configurations pcr_batch_launch accepts (0 .. n-1);
  * pcr_batch_autotune and pcr_batch_tune pick among them.  Configuration c
- * runs the geometry phases with 256 << (c >> 2) threads per block and
- * (c & 2 ? 2 : 4), (c & 1 ? 2 : 4) points per lane; 0 is the default. */
+ * runs the geometry phases with 256 << ((c >> 2) & 1) threads per block and
+ * (c & 2 ? 2 : 4), (c & 1 ? 2 : 4) points per lane; with c & 8 every HQ
+ * view's colours are added by the single-view colour pass instead of
+ * phase 2.  0 is the default. */
 PCR_API pcr_status pcr_batch_num_configs(int *count);
 
 /* Describe a batch: copy the job tables (clouds, views grouped by cloud)
@@ -358,7 +360,11 @@ PCR_API pcr_status pcr_batch_num_configs(int *count);
  * same for every exact variant; the passes use the early depth test).  The
  * views of each cloud are packed into passes over its points whose
  * framebuffers fit 96 MB of the L2 cache (a larger view gets a pass of its
- * own).  Errors: PCR_ERR_ARG for counts of 0 or above the maxima, a bad cloud
+ * own).  A view alone in its pass shares no point loads and is rendered by
+ * the single-view kernels (in the keys-and-depth phase only when it asks
+ * for one of the two frames).  The context keeps a host copy of the tables
+ * (about 52 KB per workspace, until pcr_destroy), which pcr_batch_launch
+ * reads for those views.  Errors: PCR_ERR_ARG for counts of 0 or above the maxima, a bad cloud
  * index, size, flags, pointer or alignment, or a bad depth_factor;
  * PCR_ERR_WORKSPACE for a missing or small workspace. */
 PCR_API pcr_status pcr_batch_prepare(pcr_ctx *ctx, const pcr_batch_cloud *clouds, uint32_t num_clouds,
@@ -366,10 +372,12 @@ PCR_API pcr_status pcr_batch_prepare(pcr_ctx *ctx, const pcr_batch_cloud *clouds
                                      uint32_t background_rgba, void *dev_workspace, uint64_t workspace_bytes);
 
 /* Render a prepared batch: clear, geometry phase 1 (keys and HQ depth),
- * geometry phase 2 (HQ colours), resolve; four kernel launches on the
- * context's stream with launch configuration `config`.  Makes no other CUDA
- * call, so it can be recorded by stream capture.  Errors: PCR_ERR_ARG for a
- * bad config or workspace pointer. */
+ * geometry phase 2 (HQ colours), resolve, on the context's stream with
+ * launch configuration `config`; a view alone in its pass gets the
+ * single-view kernels' launches between them.  Makes no other CUDA call, so
+ * it can be recorded by stream capture.  Errors: PCR_ERR_ARG for a bad
+ * config, or a workspace pointer this context has not prepared
+ * (pcr_batch_prepare or pcr_batch_tune). */
 PCR_API pcr_status pcr_batch_launch(pcr_ctx *ctx, const void *dev_workspace, int config);
 
 /* Time every launch configuration on the prepared batch (each rendered a few
@@ -385,7 +393,7 @@ typedef struct pcr_batch_tuning {
     uint32_t unroll1, unroll2; /* its points per lane in the two geometry phases (2 or 4) */
     uint32_t from_cache;       /* 1: read from cache_path, nothing was timed */
     uint32_t tried;            /* (budget, configuration) pairs timed */
-    uint32_t pad;
+    uint32_t single_colors;    /* 1: the configuration adds HQ colours with the single-view pass */
     double best_ms;            /* the winner's time per batch (0 when from the cache) */
     double default_ms;         /* pcr_batch_prepare's budget with configuration 0 (0 when from the cache) */
 } pcr_batch_tuning;
@@ -393,7 +401,7 @@ typedef struct pcr_batch_tuning {
 /* Prepare a batch (as pcr_batch_prepare) with its tuned L2 budget, and
  * choose its launch configuration.  Tries every budget in {64, 96, 128} MB
  * with every launch configuration (threads per block x points per lane of
- * each phase: 8), each timed over three launches after a warm-up, on the
+ * each phase x where the colours are added: 16), each timed over three launches after a warm-up, on the
  * batch's own clouds and buffers (they are rendered), and leaves the
  * workspace prepared with the fastest budget.  With cache_path (a file of
  * JSON lines, created if missing; NULL for none), a result found for this
@@ -525,13 +533,13 @@ PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, ui
  * frame slots, cloud memory and max_batch_clouds allow (a request that cannot
  * join now waits while later ones go ahead; the oldest request always joins
  * the next batch that has room).  *completed (may be NULL) counts the
- * requests this call retired or expired.  A batch in which some cloud has
- * two views or more runs through pcr_batch_launch; a batch whose views all
- * have different clouds runs each view through the single-view kernels
- * (pcr_render_basic with early-z, pcr_render_hq with dedup+early-z, and the
- * resolves).  Both give every request exactly the buffers of the request
- * rendered alone, so a result does not depend on which other requests
- * shared its batch. */
+ * requests this call retired or expired.  Every batch runs as
+ * pcr_batch_launch does (passes over a cloud's points packed into 64 MB of
+ * L2, since batches may run two at a time), so a view that shares no pass
+ * with another goes through the single-view kernels (pcr_render_basic with
+ * early-z, pcr_render_hq with dedup+early-z).  Every request gets exactly the
+ * buffers of the request rendered alone, so a result does not depend on
+ * which other requests shared its batch. */
 PCR_API pcr_status pcr_server_step(pcr_server *srv, uint32_t *completed);
 
 /* PCR_REQUEST_QUEUED, _RUNNING, _DONE or _EXPIRED for a ticket not yet

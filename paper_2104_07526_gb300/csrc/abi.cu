@@ -6,6 +6,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
+#include <vector>
 
 #include "../../include/pcr.h"
 #include "launch.h"
@@ -26,6 +28,10 @@ struct pcr_ctx {
   unsigned long long* primary = nullptr;  // HQS1R primary words
   uint32_t* locks = nullptr;              // busy-loop lock words
   uint64_t lock_wait_ns = 100000000ull;
+  // Host copy of the tables of every batch workspace this context prepared:
+  // a batch launch reads the views it renders through the single-view
+  // kernels from it.
+  std::unordered_map<const void*, std::vector<unsigned char>> batch_plans;
 };
 
 namespace {
@@ -181,6 +187,7 @@ void fill_tuning(pcr_batch_tuning* out, int budget_mb, int config, int from_cach
   out->threads = static_cast<uint32_t>(pcr::batch_config_threads(config));
   out->unroll1 = static_cast<uint32_t>(pcr::batch_config_unroll(config, 0));
   out->unroll2 = static_cast<uint32_t>(pcr::batch_config_unroll(config, 1));
+  out->single_colors = pcr::batch_config_single_colors(config) ? 1u : 0u;
   out->from_cache = static_cast<uint32_t>(from_cache);
   out->tried = static_cast<uint32_t>(tried);
   out->best_ms = best_ms;
@@ -198,12 +205,32 @@ void write_tuning(const char* path, const std::string& gpu, const std::string& s
   std::fclose(f);
 }
 
+// The host tables of a workspace this context prepared (nullptr if none),
+// and room for them (nullptr if out of memory).
+const void* find_plan(const pcr_ctx* ctx, const void* ws) {
+  const auto it = ctx->batch_plans.find(ws);
+  return it == ctx->batch_plans.end() ? nullptr : it->second.data();
+}
+
+void* plan_for(pcr_ctx* ctx, const void* ws) {
+  try {
+    std::vector<unsigned char>& v = ctx->batch_plans[ws];
+    v.resize(pcr::batch_tables_bytes());
+    return v.data();
+  } catch (const std::bad_alloc&) {
+    ctx->batch_plans.erase(ws);
+    return nullptr;
+  }
+}
+
 // Time one launch configuration on the prepared workspace: one warm-up
 // launch, then three timed ones; *ms per launch.
 cudaError_t time_batch(const void* ws, int config, pcr_ctx* ctx, cudaEvent_t a, cudaEvent_t b, double* ms) {
-  cudaError_t e = pcr::batch_launch(ws, config, ctx->stream, ctx->dev);
+  const void* plan = find_plan(ctx, ws);
+  if (!plan) return cudaErrorInvalidValue;
+  cudaError_t e = pcr::batch_launch(plan, ws, config, ctx->stream, ctx->dev);
   if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
-  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = pcr::batch_launch(ws, config, ctx->stream, ctx->dev);
+  for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = pcr::batch_launch(plan, ws, config, ctx->stream, ctx->dev);
   if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
   if (e == cudaSuccess) e = cudaEventSynchronize(b);
   float t = 0.0f;
@@ -527,7 +554,9 @@ pcr_status pcr_batch_prepare(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32
   if (st != PCR_OK) return st;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
-  return from_cuda(pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba,
+  void* plan = plan_for(ctx, dev_workspace);
+  if (!plan) return PCR_ERR_CUDA;  // no host memory for the tables
+  return from_cuda(pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, plan,
                                       dev_workspace, ctx->stream));
 }
 
@@ -542,12 +571,15 @@ pcr_status pcr_batch_tune(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t 
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   *out = pcr_batch_tuning{};
+  void* plan = plan_for(ctx, dev_workspace);
+  if (!plan) return PCR_ERR_CUDA;  // no host memory for the tables
   const std::string gpu = gpu_id(ctx->dev);
   const std::string shape = batch_shape_key(clouds, num_clouds, views, num_views);
   int cached_budget = 0, cached_config = -1;
   if (cache_path && read_tuning(cache_path, gpu, shape, &cached_budget, &cached_config)) {
     const cudaError_t e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba,
-                                             dev_workspace, ctx->stream, static_cast<uint64_t>(cached_budget) << 20);
+                                             plan, dev_workspace, ctx->stream,
+                                             static_cast<uint64_t>(cached_budget) << 20);
     if (e != cudaSuccess) return PCR_ERR_CUDA;
     fill_tuning(out, cached_budget, cached_config, 1, 0, 0.0, 0.0);
     return PCR_OK;
@@ -562,8 +594,8 @@ pcr_status pcr_batch_tune(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t 
   double best_ms = 0.0, default_ms = 0.0;
   for (int bi = 0; bi < kNumTuneBudgets && e == cudaSuccess; ++bi) {
     const int budget = kTuneBudgetsMb[bi];
-    e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, dev_workspace,
-                           ctx->stream, static_cast<uint64_t>(budget) << 20);
+    e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, plan,
+                           dev_workspace, ctx->stream, static_cast<uint64_t>(budget) << 20);
     for (int c = 0; c < pcr::batch_num_configs() && e == cudaSuccess; ++c) {
       double ms = 0.0;
       e = time_batch(dev_workspace, c, ctx, a, b, &ms);
@@ -580,8 +612,8 @@ pcr_status pcr_batch_tune(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t 
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e == cudaSuccess)  // leave the workspace prepared with the winner
-    e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, dev_workspace,
-                           ctx->stream, static_cast<uint64_t>(best_budget) << 20);
+    e = pcr::batch_prepare(clouds, num_clouds, views, num_views, depth_factor, background_rgba, plan,
+                           dev_workspace, ctx->stream, static_cast<uint64_t>(best_budget) << 20);
   if (e != cudaSuccess) return PCR_ERR_CUDA;
   fill_tuning(out, best_budget, best_config, 0, tried, best_ms, default_ms);
   if (cache_path) write_tuning(cache_path, gpu, shape, *out);
@@ -591,13 +623,17 @@ pcr_status pcr_batch_tune(pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t 
 pcr_status pcr_batch_launch(pcr_ctx* ctx, const void* dev_workspace, int config) {
   if (!ctx || !dev_workspace || !aligned(dev_workspace, 256) || config < 0 || config >= pcr::batch_num_configs())
     return PCR_ERR_ARG;
+  const void* plan = find_plan(ctx, dev_workspace);
+  if (!plan) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
-  return from_cuda(pcr::batch_launch(dev_workspace, config, ctx->stream, ctx->dev));
+  return from_cuda(pcr::batch_launch(plan, dev_workspace, config, ctx->stream, ctx->dev));
 }
 
 pcr_status pcr_batch_autotune(pcr_ctx* ctx, const void* dev_workspace, int* config) {
   if (!ctx || !dev_workspace || !config || !aligned(dev_workspace, 256)) return PCR_ERR_ARG;
+  const void* plan = find_plan(ctx, dev_workspace);
+  if (!plan) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -609,9 +645,10 @@ pcr_status pcr_batch_autotune(pcr_ctx* ctx, const void* dev_workspace, int* conf
   float best_ms = 0.0f;
   cudaError_t e = cudaSuccess;
   for (int c = 0; c < pcr::batch_num_configs() && e == cudaSuccess; ++c) {
-    e = pcr::batch_launch(dev_workspace, c, ctx->stream, ctx->dev);  // warm-up
+    e = pcr::batch_launch(plan, dev_workspace, c, ctx->stream, ctx->dev);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
-    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = pcr::batch_launch(dev_workspace, c, ctx->stream, ctx->dev);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+      e = pcr::batch_launch(plan, dev_workspace, c, ctx->stream, ctx->dev);
     if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.0f;
@@ -633,6 +670,8 @@ pcr_status pcr_batch_capture(pcr_ctx* ctx, const void* dev_workspace, int config
       config >= pcr::batch_num_configs())
     return PCR_ERR_ARG;
   *graph_exec = nullptr;
+  const void* plan = find_plan(ctx, dev_workspace);
+  if (!plan) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   cudaError_t e = pcr::batch_prewarm(ctx->dev);  // occupancy queries happen before the capture
@@ -642,7 +681,7 @@ pcr_status pcr_batch_capture(pcr_ctx* ctx, const void* dev_workspace, int config
   cudaGraph_t graph = nullptr;
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    const cudaError_t le = pcr::batch_launch(dev_workspace, config, cs, ctx->dev);
+    const cudaError_t le = pcr::batch_launch(plan, dev_workspace, config, cs, ctx->dev);
     e = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess) e = le;
   }

@@ -41,6 +41,11 @@ struct Tables {
   BatchView views[kBatchMaxViews];
   BatchGroup groups[2][kBatchMaxViews];
   uint16_t order[2][kBatchMaxViews];
+  // Per phase, the views that are alone in their pass (phase 1: with one
+  // flag) and run through the single-view kernels instead; the host reads
+  // these from its copy of the tables when it launches the batch.
+  uint32_t num_single[2];
+  uint16_t single[2][kBatchMaxViews];
 };
 
 struct Shared {
@@ -277,9 +282,13 @@ __global__ void __launch_bounds__(kThreads) k_batch_resolve(const Tables* __rest
 
 // Launch configurations the autotuner chooses among: threads per block, and
 // points per lane of the two geometry phases (phase 2 keeps more state per
-// point).  Configuration c: threads 256 << (c >> 2), phase-1 points per lane
-// (c & 2) ? 2 : 4, phase-2 (c & 1) ? 2 : 4.  Configuration 0 is the default.
-constexpr int kNumConfigs = 8;
+// point), and where the colours are added.  Configuration c: threads
+// 256 << ((c >> 2) & 1), phase-1 points per lane (c & 2) ? 2 : 4, phase-2
+// (c & 1) ? 2 : 4; with c & 8, every HQ view's colours are added by the
+// single-view colour pass (one pass over the points per view, the kernel
+// with the fewest instructions per point) and phase 2 is not launched.
+// Configuration 0 is the default.
+constexpr int kNumConfigs = 16;
 
 template <auto K>
 int batch_resident(int threads) {
@@ -297,11 +306,36 @@ void launch_persistent(const Tables* t, cudaStream_t s, const Device& d) {
 }
 
 template <int T>
-void launch_phases(const Tables* t, int config, cudaStream_t s, const Device& d) {
-  if (config & 2) launch_persistent<k_batch_phase1<2, T>, T>(t, s, d);
-  else launch_persistent<k_batch_phase1<4, T>, T>(t, s, d);
-  if (config & 1) launch_persistent<k_batch_phase2<2, T>, T>(t, s, d);
-  else launch_persistent<k_batch_phase2<4, T>, T>(t, s, d);
+void launch_phase(const Tables* t, int config, int phase, cudaStream_t s, const Device& d) {
+  if (phase == 0) {
+    if (config & 2) launch_persistent<k_batch_phase1<2, T>, T>(t, s, d);
+    else launch_persistent<k_batch_phase1<4, T>, T>(t, s, d);
+  } else {
+    if (config & 1) launch_persistent<k_batch_phase2<2, T>, T>(t, s, d);
+    else launch_persistent<k_batch_phase2<4, T>, T>(t, s, d);
+  }
+}
+
+void launch_batch_phase(const Tables* t, int config, int phase, cudaStream_t s, const Device& d) {
+  if (config & 4) launch_phase<512>(t, config, phase, s, d);
+  else launch_phase<256>(t, config, phase, s, d);
+}
+
+// The single-view kernels of one view and phase: phase 0 the basic keys
+// (early-z) and the HQ depth (dedup+early-z), phase 1 the HQ colours (warp
+// aggregated) -- the kernels pcr_render_basic and pcr_render_hq run.
+cudaError_t launch_single(const Tables& h, uint32_t vi, int phase, cudaStream_t s, const Device& d) {
+  const BatchView& v = h.views[vi];
+  const BatchCloud& c = h.clouds[v.cloud];
+  cudaError_t e = cudaSuccess;
+  if (phase == 0) {
+    if (v.flags & PCR_BATCH_BASIC) e = launch_render_basic(PCR_VARIANT_EARLYZ, c.pts, c.n, v.vp, v.keys, s, d);
+    if (e == cudaSuccess && (v.flags & PCR_BATCH_HQ))
+      e = launch_hq_depth(PCR_VARIANT_DEDUP_EARLYZ, c.pts, c.n, v.vp, v.depth, s, d);
+  } else if (v.flags & PCR_BATCH_HQ) {
+    e = launch_hq_color(PCR_VARIANT_DEDUP_EARLYZ, c.pts, c.n, v.vp, h.hdr.depth_factor, v.depth, v.rg, v.ba, s, d);
+  }
+  return e;
 }
 
 template <int T>
@@ -322,10 +356,13 @@ namespace {
 
 // Pack the views of each cloud that take part in a phase into passes whose
 // framebuffer bytes fit the L2 budget (first fit, largest first); a view
-// larger than the budget gets a pass of its own.
+// larger than the budget gets a pass of its own.  A pass of one view shares
+// no point loads: that view goes to the phase's single-view list instead
+// (in phase 1 only when it asks for one frame; with both, the batch pass
+// still reads its points once for the two).
 void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                   uint32_t num_views, int phase, uint64_t l2_budget) {
-  uint32_t ng = 0, nord = 0;
+  uint32_t ng = 0, nord = 0, nsingle = 0;
   uint64_t slot = 0;
   for (uint32_t c = 0; c < num_clouds; ++c) {
     std::vector<std::pair<uint64_t, uint32_t>> mine;  // (bytes, view)
@@ -353,6 +390,11 @@ void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds,
     }
     const uint64_t padded = (clouds[c].n + kSlot - 1) / kSlot * kSlot;
     for (const auto& bin : bins) {
+      const uint32_t f = views[bin[0]].flags;
+      if (bin.size() == 1 && (phase == 1 || f != (PCR_BATCH_BASIC | PCR_BATCH_HQ))) {
+        t->single[phase][nsingle++] = static_cast<uint16_t>(bin[0]);
+        continue;
+      }
       BatchGroup& g = t->groups[phase][ng++];
       g.cloud = c;
       g.first = nord;
@@ -364,6 +406,7 @@ void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds,
   }
   t->hdr.num_groups[phase] = ng;
   t->hdr.total_slots[phase] = slot;
+  t->num_single[phase] = nsingle;
 }
 
 }  // namespace
@@ -415,34 +458,51 @@ void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, cons
 }
 
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
-                          uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
-                          cudaStream_t s, uint64_t l2_budget) {
-  void* host = ::operator new(sizeof(Tables), std::nothrow);
-  if (!host) return cudaErrorMemoryAllocation;
-  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host, l2_budget);
-  cudaError_t e = cudaMemcpyAsync(workspace, host, sizeof(Tables), cudaMemcpyHostToDevice, s);
+                          uint32_t num_views, float depth_factor, uint32_t background, void* host_tables,
+                          void* workspace, cudaStream_t s, uint64_t l2_budget) {
+  batch_build_tables(clouds, num_clouds, views, num_views, depth_factor, background, host_tables, l2_budget);
+  cudaError_t e = cudaMemcpyAsync(workspace, host_tables, sizeof(Tables), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  static_cast<Tables*>(host)->~Tables();
-  ::operator delete(host);
   return e;
 }
 
-cudaError_t batch_prewarm(const Device&) {
+cudaError_t batch_prewarm(const Device& d) {
   prewarm_phases<256>();
   prewarm_phases<512>();
+  prewarm_single_view(d);
   return cudaGetLastError();
 }
 
-int batch_config_threads(int config) { return 256 << (config >> 2); }
+int batch_config_threads(int config) { return 256 << ((config >> 2) & 1); }
 int batch_config_unroll(int config, int phase) { return (config & (phase == 0 ? 2 : 1)) ? 2 : 4; }
+bool batch_config_single_colors(int config) { return (config & 8) != 0; }
 
-cudaError_t batch_launch(const void* workspace, int config, cudaStream_t s, const Device& d) {
+// clear, phase 1 (the batch passes, then the single-view passes of views
+// alone in theirs), phase 2 (likewise, or every HQ view single-view), and
+// resolve, in stream order: phase 2 reads complete depth buffers.
+cudaError_t batch_launch(const void* host_tables, const void* workspace, int config, cudaStream_t s,
+                         const Device& d) {
   if (config < 0 || config >= kNumConfigs) return cudaErrorInvalidValue;
+  const Tables& h = *static_cast<const Tables*>(host_tables);
   const Tables* t = static_cast<const Tables*>(workspace);
   const int screen_blocks = d.num_sms * 8;
   k_batch_clear<<<screen_blocks, kThreads, 0, s>>>(t);
-  if (config & 4) launch_phases<512>(t, config, s, d);
-  else launch_phases<256>(t, config, s, d);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && h.hdr.total_slots[0] > 0) {
+    launch_batch_phase(t, config, 0, s, d);
+    e = cudaGetLastError();
+  }
+  for (uint32_t k = 0; k < h.num_single[0] && e == cudaSuccess; ++k) e = launch_single(h, h.single[0][k], 0, s, d);
+  if (batch_config_single_colors(config)) {
+    for (uint32_t vi = 0; vi < h.hdr.num_views && e == cudaSuccess; ++vi) e = launch_single(h, vi, 1, s, d);
+  } else {
+    if (e == cudaSuccess && h.hdr.total_slots[1] > 0) {
+      launch_batch_phase(t, config, 1, s, d);
+      e = cudaGetLastError();
+    }
+    for (uint32_t k = 0; k < h.num_single[1] && e == cudaSuccess; ++k) e = launch_single(h, h.single[1][k], 1, s, d);
+  }
+  if (e != cudaSuccess) return e;
   k_batch_resolve<<<screen_blocks, kThreads, 0, s>>>(t);
   return cudaGetLastError();
 }

@@ -44,6 +44,9 @@ cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigne
 cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
                               uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
+// Run the occupancy queries of the single-view kernels the batch launches
+// (before a capture).
+void prewarm_single_view(const Device& d);
 // Debug builds: the geometry kernels' counters (render.cu); *available is
 // false in release builds.
 cudaError_t read_and_clear_debug_counts(uint64_t out[4], cudaStream_t s, bool* available);
@@ -113,14 +116,20 @@ void batch_build_tables(const pcr_batch_cloud* clouds, uint32_t num_clouds, cons
 constexpr uint64_t kBatchL2Budget = 96ull << 20;
 constexpr uint64_t kServedL2Budget = 64ull << 20;
 int batch_num_configs();
+// Build the tables into host_tables (batch_tables_bytes()), copy them into
+// the workspace and wait for the copy.
 cudaError_t batch_prepare(const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
-                          uint32_t num_views, float depth_factor, uint32_t background, void* workspace,
-                          cudaStream_t s, uint64_t l2_budget = kBatchL2Budget);
+                          uint32_t num_views, float depth_factor, uint32_t background, void* host_tables,
+                          void* workspace, cudaStream_t s, uint64_t l2_budget = kBatchL2Budget);
 // Threads per block and points per lane (phase 0 or 1) of a launch
-// configuration.
+// configuration, and whether it adds every HQ view's colours single-view.
 int batch_config_threads(int config);
 int batch_config_unroll(int config, int phase);
-cudaError_t batch_launch(const void* workspace, int config, cudaStream_t s, const Device& d);
+bool batch_config_single_colors(int config);
+// host_tables: the host copy of the tables in `workspace` (the single-view
+// launches read their views from it during the call).
+cudaError_t batch_launch(const void* host_tables, const void* workspace, int config, cudaStream_t s,
+                         const Device& d);
 // Run the occupancy queries of every configuration once (before a capture).
 cudaError_t batch_prewarm(const Device& d);
 

@@ -26,7 +26,6 @@ using namespace geom;
 __device__ uint32_t g_error_word;
 constexpr uint32_t kErrorKeyRange = PCR_DEVICE_ERROR_KEY_RANGE;
 constexpr uint32_t kErrorWaitTimeout = PCR_DEVICE_ERROR_WAIT_TIMEOUT;
-constexpr uint32_t kErrorBounds = PCR_DEVICE_ERROR_BOUNDS;
 
 // Debug builds (PCR_DEBUG) count what the single-view geometry kernels send
 // to the framebuffers: key writes, depth writes, colour add pairs, and the
@@ -35,6 +34,7 @@ constexpr uint32_t kErrorBounds = PCR_DEVICE_ERROR_BOUNDS;
 // failure sets kErrorBounds and drops the slot).  Release builds have
 // neither.
 #ifdef PCR_DEBUG
+constexpr uint32_t kErrorBounds = PCR_DEVICE_ERROR_BOUNDS;
 __device__ unsigned long long g_debug_counts[4];
 #define PCR_DEBUG_COUNT(k, x)                                                     \
   do {                                                                            \
@@ -629,6 +629,13 @@ cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const Vie
   else if (pairs_aligned(pts)) launch_color_k<true, kCanPairLoad>(pts, n, v, depth_factor, depth, rg, ba, s, d);
   else launch_color_k<true, false>(pts, n, v, depth_factor, depth, rg, ba, s, d);
   return cudaGetLastError();
+}
+
+void prewarm_single_view(const Device& d) {
+  geometry_grid<k_render_basic<PCR_VARIANT_EARLYZ, kUnroll, kPayloadIndex>, kUnroll>(1, d);
+  geometry_grid<k_hq_depth<PCR_VARIANT_DEDUP_EARLYZ, kUnroll>, kUnroll>(1, d);
+  geometry_grid<k_hq_color<true, kUnroll, kCanPairLoad>, kUnroll>(1, d);
+  geometry_grid<k_hq_color<true, kUnroll, false>, kUnroll>(1, d);
 }
 
 template <bool AGG, bool V8>

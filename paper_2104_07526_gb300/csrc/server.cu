@@ -8,12 +8,12 @@
 // while a batch in flight reads them).  pcr_server_step is the loop body:
 // it retires batches whose completion event has fired, then forms new
 // batches from the queued requests, in arrival order, as long as an
-// in-flight batch, frame slots and cloud memory are free.  A batch in which
-// some cloud has two views or more runs on the batched renderer; one whose
-// views all have different clouds runs each view through the single-view
-// kernels.  Batches rotate over the server's streams (one per in-flight
-// batch unless fewer are asked for), so with several streams they overlap
-// on the GPU; requests that arrive while others render join the next batch.
+// in-flight batch, frame slots and cloud memory are free.  Every batch runs
+// on the batched renderer, which sends a view that shares no pass over its
+// cloud's points with another through the single-view kernels.  Batches
+// rotate over the server's streams (one per in-flight batch unless fewer are
+// asked for), so with several streams they overlap on the GPU; requests that
+// arrive while others render join the next batch.
 // A request's result stays in its frame slot until the caller releases the
 // ticket.
 #include <algorithm>
@@ -214,48 +214,6 @@ pcr_status retire(pcr_server* s, uint32_t* completed) {
   return PCR_OK;
 }
 
-// A batch in which no two views share a cloud shares no point loads.  Its
-// views then run through the single-view kernels instead of the batch
-// kernels (early-z keys, dedup+early-z HQ depth, warp-aggregated colours):
-// the same buffers bit for bit, with the kernels tuned for one view.
-cudaError_t launch_single_views(pcr_server* s, const std::vector<uint64_t>& take, cudaStream_t st) {
-  for (uint64_t tk : take) {
-    const pcr::Request& r = s->requests[tk];
-    const pcr::Cloud& c = s->clouds[r.cloud];
-    const uint4* pts = static_cast<const uint4*>(cloud_points(s, c));
-    const uint32_t n = static_cast<uint32_t>(c.n);
-    pcr::ViewParams v{};
-    for (int k = 0; k < 4; ++k) {
-      v.r0[k] = r.matrix[k];
-      v.r1[k] = r.matrix[4 + k];
-      v.r3[k] = r.matrix[12 + k];
-    }
-    v.fw = static_cast<float>(r.width);
-    v.fh = static_cast<float>(r.height);
-    v.width = static_cast<uint32_t>(r.width);
-    v.height = static_cast<uint32_t>(r.height);
-    const uint64_t npx = static_cast<uint64_t>(r.width) * static_cast<uint64_t>(r.height);
-    const SlotPtrs p = slot_ptrs(s, r.slot);
-    cudaError_t e = cudaSuccess;
-    if (r.flags & PCR_BATCH_BASIC) {
-      e = pcr::launch_fill_u64(p.keys, npx, pcr::kEmptyKey, st, s->dev);
-      if (e == cudaSuccess) e = pcr::launch_render_basic(PCR_VARIANT_EARLYZ, pts, n, v, p.keys, st, s->dev);
-      if (e == cudaSuccess)
-        e = pcr::launch_resolve_basic(p.keys, npx, pts, n, s->cfg.background_rgba, p.image, st, s->dev);
-    }
-    if (e == cudaSuccess && (r.flags & PCR_BATCH_HQ)) {
-      e = pcr::launch_clear_hq(p.depth, p.rg, p.ba, npx, st, s->dev);
-      if (e == cudaSuccess) e = pcr::launch_hq_depth(PCR_VARIANT_DEDUP_EARLYZ, pts, n, v, p.depth, st, s->dev);
-      if (e == cudaSuccess)
-        e = pcr::launch_hq_color(PCR_VARIANT_DEDUP_EARLYZ, pts, n, v, s->cfg.depth_factor, p.depth, p.rg, p.ba, st,
-                                 s->dev);
-      if (e == cudaSuccess) e = pcr::launch_resolve_hq(p.rg, p.ba, npx, s->cfg.background_rgba, p.hq_image, st, s->dev);
-    }
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
 // Requests still queued deadline_us after their submission expire: they
 // leave the queue unrendered and are reported like finished ones.  The queue
 // is in arrival order, so they are at its front.
@@ -363,10 +321,8 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
     v.hq_ba = (r.flags & PCR_BATCH_HQ) ? p.ba : nullptr;
     v.hq_image = (r.flags & PCR_BATCH_HQ) ? p.hq_image : nullptr;
   }
-  const bool shared_cloud = batch_clouds.size() < take.size();  // some cloud has two views or more
-  if (shared_cloud)
-    pcr::batch_build_tables(bc.data(), static_cast<uint32_t>(bc.size()), bv.data(), static_cast<uint32_t>(bv.size()),
-                            s->cfg.depth_factor, s->cfg.background_rgba, f.staging, pcr::kServedL2Budget);
+  pcr::batch_build_tables(bc.data(), static_cast<uint32_t>(bc.size()), bv.data(), static_cast<uint32_t>(bv.size()),
+                          s->cfg.depth_factor, s->cfg.background_rgba, f.staging, pcr::kServedL2Budget);
 
   cudaError_t e = cudaSuccess;
   for (uint32_t id : uploads) {
@@ -384,11 +340,9 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
         std::find(uploads.begin(), uploads.end(), id) == uploads.end())
       e = cudaStreamWaitEvent(f.stream, c.ready, 0);
   }
-  if (e == cudaSuccess && shared_cloud)
-    e = cudaMemcpyAsync(f.workspace, f.staging, pcr::batch_tables_bytes(), cudaMemcpyHostToDevice, f.stream);
   if (e == cudaSuccess)
-    e = shared_cloud ? pcr::batch_launch(f.workspace, s->cfg.batch_config, f.stream, s->dev)
-                     : launch_single_views(s, take, f.stream);
+    e = cudaMemcpyAsync(f.workspace, f.staging, pcr::batch_tables_bytes(), cudaMemcpyHostToDevice, f.stream);
+  if (e == cudaSuccess) e = pcr::batch_launch(f.staging, f.workspace, s->cfg.batch_config, f.stream, s->dev);
   if (e == cudaSuccess) e = cudaEventRecord(f.done, f.stream);
   if (e != cudaSuccess) {
     // nothing of this batch is known to have run: its requests go back to the

@@ -71,7 +71,7 @@ class PcrBatchTuning(C.Structure):
     """pcr_batch_tuning"""
     _fields_ = [("l2_budget_mb", C.c_uint32), ("config", C.c_int32), ("threads", C.c_uint32),
                 ("unroll1", C.c_uint32), ("unroll2", C.c_uint32), ("from_cache", C.c_uint32), ("tried", C.c_uint32),
-                ("pad", C.c_uint32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+                ("single_colors", C.c_uint32), ("best_ms", C.c_double), ("default_ms", C.c_double)]
 
 
 class PcrServerConfig(C.Structure):
@@ -409,7 +409,7 @@ def pcr_batch_tune(ctx: int, clouds, views, depth_factor: float, background_rgba
     _check(lib().pcr_batch_tune(ctx, ca, len(clouds), va, len(views), depth_factor, background_rgba & 0xFFFFFFFF,
                                 _dptr(workspace, "workspace"), _nbytes(workspace) if workspace is not None else 0,
                                 cache_path.encode() if cache_path else None, C.byref(out)), "pcr_batch_tune")
-    return {k: getattr(out, k) for k, _ in PcrBatchTuning._fields_ if k != "pad"}
+    return {k: getattr(out, k) for k, _ in PcrBatchTuning._fields_}
 
 
 def pcr_batch_capture(ctx: int, workspace, config: int) -> int:

@@ -158,6 +158,16 @@ def test_batch_rejects_bad_descriptions(ctx):
     assert e.value.status == pcr.PCR_ERR_WORKSPACE
     with pytest.raises(pcr.PcrError):
         pcr.pcr_batch_launch(ctx, ws, pcr.pcr_batch_num_configs())
+    # a launch reads the host copy of the tables its context made: another
+    # context has none for this workspace, and launches nothing
+    pcr.pcr_batch_prepare(ctx, [pcr.batch_cloud(cloud)], [pcr.batch_view(m, 4, 4, 0, BASIC, **good)], 1.01, 0, ws)
+    with pcr.Context(0, stream=torch.cuda.current_stream()) as other:
+        for call in (lambda: pcr.pcr_batch_launch(other.handle, ws, 0),
+                     lambda: pcr.pcr_batch_capture(other.handle, ws, 0),
+                     lambda: pcr.pcr_batch_autotune(other.handle, ws)):
+            with pytest.raises(pcr.PcrError) as e:
+                call()
+            assert e.value.status == pcr.PCR_ERR_ARG
 
 
 def test_batch_table_limits(ctx, oracle):
@@ -208,6 +218,7 @@ def test_batch_tune_chooses_and_caches(ctx, oracle, tmp_path):
     assert first["from_cache"] == 0 and first["tried"] == 3 * pcr.pcr_batch_num_configs()
     assert first["l2_budget_mb"] in (64, 96, 128) and 0 <= first["config"] < pcr.pcr_batch_num_configs()
     assert first["threads"] in (256, 512) and first["unroll1"] in (2, 4) and first["unroll2"] in (2, 4)
+    assert first["single_colors"] == (first["config"] >> 3) & 1
     assert 0 < first["best_ms"] <= first["default_ms"]
     _poison(bufs)
     pcr.pcr_batch_launch(ctx, ws, first["config"])
