@@ -48,33 +48,66 @@ struct Tables {
   uint16_t single[2][kBatchMaxViews];
 };
 
-struct Shared {
-  BatchHeader hdr;
-  BatchCloud clouds[kBatchMaxClouds];
-  BatchView views[kBatchMaxViews];
-  BatchGroup groups[kBatchMaxViews];
-  uint16_t order[kBatchMaxViews];
+// The kernels copy the tables they read into dynamic shared memory, sized
+// to the batch: header, clouds, views and (geometry phases) the phase's
+// groups and view order, each 16-byte aligned.  A batch of 64 views over a
+// few clouds takes about 10 KB, so shared memory does not bound the resident
+// blocks (the full 256 x 256 tables take 42 KB, under the 48 KB a launch
+// gets without opting in).
+struct SharedLayout {
+  uint32_t clouds, views, groups, order, bytes;
 };
+
+__host__ __device__ constexpr uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
+
+__host__ __device__ inline SharedLayout shared_layout(uint32_t num_clouds, uint32_t num_views, uint32_t num_groups,
+                                                      bool geometry) {
+  SharedLayout l{};
+  l.clouds = align16(sizeof(BatchHeader));
+  l.views = l.clouds + align16(num_clouds * static_cast<uint32_t>(sizeof(BatchCloud)));
+  l.groups = l.views + align16(num_views * static_cast<uint32_t>(sizeof(BatchView)));
+  l.order = l.groups + (geometry ? align16(num_groups * static_cast<uint32_t>(sizeof(BatchGroup))) : 0u);
+  l.bytes = l.order + (geometry ? align16(num_views * static_cast<uint32_t>(sizeof(uint16_t))) : 0u);
+  return l;
+}
+
+// Views of the tables in shared memory.
+struct Shared {
+  const BatchHeader& hdr;
+  const BatchCloud* clouds;
+  const BatchView* views;
+  const BatchGroup* groups;
+  const uint16_t* order;
+};
+
+extern __shared__ __align__(16) unsigned char g_smem_tables[];
 
 constexpr uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
-// Copy the header, clouds, views and (phase >= 0) that phase's groups into
-// shared memory.
-__device__ __forceinline__ void load_tables(const Tables* __restrict__ g, int phase, Shared& sh) {
-  if (threadIdx.x == 0) sh.hdr = g->hdr;
+// Copy the header, clouds, views and (phase >= 0) that phase's groups and
+// order into shared memory.
+__device__ __forceinline__ Shared load_tables(const Tables* __restrict__ g, int phase) {
+  BatchHeader* hdr = reinterpret_cast<BatchHeader*>(g_smem_tables);
+  if (threadIdx.x == 0) *hdr = g->hdr;
   __syncthreads();
+  const SharedLayout l =
+      shared_layout(hdr->num_clouds, hdr->num_views, phase >= 0 ? hdr->num_groups[phase] : 0u, phase >= 0);
   auto copy = [](const void* src, void* dst, uint32_t bytes) {
     const uint32_t* s4 = static_cast<const uint32_t*>(src);
     uint32_t* d4 = static_cast<uint32_t*>(dst);
     for (uint32_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d4[i] = s4[i];
   };
-  copy(g->clouds, sh.clouds, sh.hdr.num_clouds * sizeof(BatchCloud));
-  copy(g->views, sh.views, sh.hdr.num_views * sizeof(BatchView));
+  copy(g->clouds, g_smem_tables + l.clouds, hdr->num_clouds * sizeof(BatchCloud));
+  copy(g->views, g_smem_tables + l.views, hdr->num_views * sizeof(BatchView));
   if (phase >= 0) {
-    copy(g->groups[phase], sh.groups, sh.hdr.num_groups[phase] * sizeof(BatchGroup));
-    copy(g->order[phase], sh.order, (sh.hdr.num_views * sizeof(uint16_t) + 3) / 4 * 4);
+    copy(g->groups[phase], g_smem_tables + l.groups, hdr->num_groups[phase] * sizeof(BatchGroup));
+    copy(g->order[phase], g_smem_tables + l.order, (hdr->num_views * sizeof(uint16_t) + 3) / 4 * 4);
   }
   __syncthreads();
+  return Shared{*hdr, reinterpret_cast<const BatchCloud*>(g_smem_tables + l.clouds),
+                reinterpret_cast<const BatchView*>(g_smem_tables + l.views),
+                reinterpret_cast<const BatchGroup*>(g_smem_tables + l.groups),
+                reinterpret_cast<const uint16_t*>(g_smem_tables + l.order)};
 }
 
 // Largest i in [0, count) with key(i) <= x (key(0) is 0, so i exists).
@@ -146,8 +179,7 @@ __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&
 // from one projection.
 template <int U, int T>
 __global__ void __launch_bounds__(T) k_batch_phase1(const Tables* __restrict__ tables) {
-  __shared__ Shared sh;
-  load_tables(tables, 0, sh);
+  const Shared sh = load_tables(tables, 0);
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
   for_each_batch_chunk<U, kInterleaved>(sh, 0, pol_stream, [&](const BatchGroup& grp, const uint4(&r)[U], uint32_t base,
@@ -187,8 +219,7 @@ __global__ void __launch_bounds__(T) k_batch_phase1(const Tables* __restrict__ t
 // Held to 64 registers (1024 threads per SM) at either block size.
 template <int U, int T>
 __global__ void __launch_bounds__(T, 1024 / T) k_batch_phase2(const Tables* __restrict__ tables) {
-  __shared__ Shared sh;
-  load_tables(tables, 1, sh);
+  const Shared sh = load_tables(tables, 1);
   const uint64_t pol_stream = policy_evict_first();
   const uint64_t pol_fb = policy_evict_last();
   const float factor = sh.hdr.depth_factor;
@@ -222,8 +253,7 @@ __device__ __forceinline__ uint32_t view_of_pixel(const Shared& sh, uint64_t p) 
 }
 
 __global__ void __launch_bounds__(kThreads) k_batch_clear(const Tables* __restrict__ tables) {
-  __shared__ Shared sh;
-  load_tables(tables, -1, sh);
+  const Shared sh = load_tables(tables, -1);
   const BatchHeader& hdr = sh.hdr;
   const BatchView* views = sh.views;
   const uint64_t stride = static_cast<uint64_t>(gridDim.x) * blockDim.x;
@@ -244,8 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_clear(const Tables* __restri
 }
 
 __global__ void __launch_bounds__(kThreads) k_batch_resolve(const Tables* __restrict__ tables) {
-  __shared__ Shared sh;
-  load_tables(tables, -1, sh);
+  const Shared sh = load_tables(tables, -1);
   const BatchHeader& hdr = sh.hdr;
   const BatchView* views = sh.views;
   const BatchCloud* clouds = sh.clouds;
@@ -290,35 +319,36 @@ __global__ void __launch_bounds__(kThreads) k_batch_resolve(const Tables* __rest
 // Configuration 0 is the default.
 constexpr int kNumConfigs = 16;
 
+// Resident blocks per SM of a geometry kernel with `smem` bytes of tables
+// (the occupancy query is host arithmetic; its first call per kernel loads
+// the kernel, which the prewarm does before any capture).
 template <auto K>
-int batch_resident(int threads) {
-  static const int blocks = [threads] {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, threads, 0) != cudaSuccess || b < 1) b = 1;
-    return b;
-  }();
-  return blocks;
+int batch_resident(int threads, uint32_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, K, threads, smem) != cudaSuccess || b < 1) b = 1;
+  return b;
 }
 
 template <auto K, int T>
-void launch_persistent(const Tables* t, cudaStream_t s, const Device& d) {
-  K<<<d.num_sms * batch_resident<K>(T), T, 0, s>>>(t);
+void launch_persistent(const Tables* t, uint32_t smem, cudaStream_t s, const Device& d) {
+  K<<<d.num_sms * batch_resident<K>(T, smem), T, smem, s>>>(t);
 }
 
 template <int T>
-void launch_phase(const Tables* t, int config, int phase, cudaStream_t s, const Device& d) {
+void launch_phase(const Tables* t, uint32_t smem, int config, int phase, cudaStream_t s, const Device& d) {
   if (phase == 0) {
-    if (config & 2) launch_persistent<k_batch_phase1<2, T>, T>(t, s, d);
-    else launch_persistent<k_batch_phase1<4, T>, T>(t, s, d);
+    if (config & 2) launch_persistent<k_batch_phase1<2, T>, T>(t, smem, s, d);
+    else launch_persistent<k_batch_phase1<4, T>, T>(t, smem, s, d);
   } else {
-    if (config & 1) launch_persistent<k_batch_phase2<2, T>, T>(t, s, d);
-    else launch_persistent<k_batch_phase2<4, T>, T>(t, s, d);
+    if (config & 1) launch_persistent<k_batch_phase2<2, T>, T>(t, smem, s, d);
+    else launch_persistent<k_batch_phase2<4, T>, T>(t, smem, s, d);
   }
 }
 
-void launch_batch_phase(const Tables* t, int config, int phase, cudaStream_t s, const Device& d) {
-  if (config & 4) launch_phase<512>(t, config, phase, s, d);
-  else launch_phase<256>(t, config, phase, s, d);
+void launch_batch_phase(const Tables& h, const Tables* t, int config, int phase, cudaStream_t s, const Device& d) {
+  const uint32_t smem = shared_layout(h.hdr.num_clouds, h.hdr.num_views, h.hdr.num_groups[phase], true).bytes;
+  if (config & 4) launch_phase<512>(t, smem, config, phase, s, d);
+  else launch_phase<256>(t, smem, config, phase, s, d);
 }
 
 // The single-view kernels of one view and phase: phase 0 the basic keys
@@ -340,10 +370,10 @@ cudaError_t launch_single(const Tables& h, uint32_t vi, int phase, cudaStream_t 
 
 template <int T>
 void prewarm_phases() {
-  batch_resident<k_batch_phase1<4, T>>(T);
-  batch_resident<k_batch_phase2<4, T>>(T);
-  batch_resident<k_batch_phase1<2, T>>(T);
-  batch_resident<k_batch_phase2<2, T>>(T);
+  batch_resident<k_batch_phase1<4, T>>(T, 0);
+  batch_resident<k_batch_phase2<4, T>>(T, 0);
+  batch_resident<k_batch_phase1<2, T>>(T, 0);
+  batch_resident<k_batch_phase2<2, T>>(T, 0);
 }
 
 }  // namespace
@@ -486,10 +516,11 @@ cudaError_t batch_launch(const void* host_tables, const void* workspace, int con
   const Tables& h = *static_cast<const Tables*>(host_tables);
   const Tables* t = static_cast<const Tables*>(workspace);
   const int screen_blocks = d.num_sms * 8;
-  k_batch_clear<<<screen_blocks, kThreads, 0, s>>>(t);
+  const uint32_t screen_smem = shared_layout(h.hdr.num_clouds, h.hdr.num_views, 0, false).bytes;
+  k_batch_clear<<<screen_blocks, kThreads, screen_smem, s>>>(t);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && h.hdr.total_slots[0] > 0) {
-    launch_batch_phase(t, config, 0, s, d);
+    launch_batch_phase(h, t, config, 0, s, d);
     e = cudaGetLastError();
   }
   for (uint32_t k = 0; k < h.num_single[0] && e == cudaSuccess; ++k) e = launch_single(h, h.single[0][k], 0, s, d);
@@ -497,13 +528,13 @@ cudaError_t batch_launch(const void* host_tables, const void* workspace, int con
     for (uint32_t vi = 0; vi < h.hdr.num_views && e == cudaSuccess; ++vi) e = launch_single(h, vi, 1, s, d);
   } else {
     if (e == cudaSuccess && h.hdr.total_slots[1] > 0) {
-      launch_batch_phase(t, config, 1, s, d);
+      launch_batch_phase(h, t, config, 1, s, d);
       e = cudaGetLastError();
     }
     for (uint32_t k = 0; k < h.num_single[1] && e == cudaSuccess; ++k) e = launch_single(h, h.single[1][k], 1, s, d);
   }
   if (e != cudaSuccess) return e;
-  k_batch_resolve<<<screen_blocks, kThreads, 0, s>>>(t);
+  k_batch_resolve<<<screen_blocks, kThreads, screen_smem, s>>>(t);
   return cudaGetLastError();
 }
 
