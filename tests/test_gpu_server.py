@@ -139,11 +139,12 @@ def test_mixed_requests_match_rendering_alone(ctx, oracle):
 
 
 def test_both_launch_paths_match_rendering_alone(ctx, oracle):
-    """A batch in which no two views share a cloud runs its views through the
-    single-view kernels; one with a shared cloud runs the batch kernels.
-    One view per batch forces the first path; submitting views of one cloud
-    together with room for them all forces the second.  Both give the
-    oracle's buffers."""
+    """A batch in which no two views share a cloud shares no pass over a
+    cloud's points: the batch launch sends every view through the
+    single-view kernels.  Views of one cloud batched together share passes
+    through the batch kernels.  One view per batch forces the first path;
+    submitting views of one cloud together with room for them all forces the
+    second.  Both give the oracle's buffers."""
     clouds = _clouds()
     dev = [torch.from_numpy(c.copy()).cuda() for c in clouds]
     arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
