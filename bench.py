@@ -94,9 +94,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-batched", action="store_true", help="skip the batched (8 clouds x 8 views) measurement")
     ap.add_argument("--no-served", action="store_true", help="skip the served (Poisson request stream) measurement")
     ap.add_argument("--served-seconds", type=float, default=2.0, help="length of the served request stream")
-    ap.add_argument("--part", choices=["reorder", "batch"],
+    ap.add_argument("--part", choices=["reorder", "batch", "served"],
                     help="time one part alone and print its timings (for running under a profiler): every "
-                         "vertex order of the scan scene (--points, --orders), or the 8-cloud x 8-view batch")
+                         "vertex order of the scan scene (--points, --orders), the 8-cloud x 8-view batch, or "
+                         "the saturated request stream through the server alone (--served-seconds)")
     ap.add_argument("--points", type=int, default=100_000_000, help="scan-scene points for --part reorder")
     ap.add_argument("--orders", default="morton,morton_shuffle128,shuffle,morton63,morton63_shuffle128",
                     help="comma-separated vertex orders for --part reorder")
@@ -1114,7 +1115,9 @@ def run_part(args) -> int:
     own kernels and little else.  reorder: each order of the scan scene from
     its generation order, run twice (the first warms up), CUDA events.  batch:
     the 8 boxes clouds x 8 orbit views (shuffled-Morton order, basic + HQ),
-    prepared once and launched four times with configuration 0."""
+    prepared once and launched four times with configuration 0.  served: the
+    served workload's Poisson stream at 8000 requests/s for --served-seconds
+    through the server, without the plain-launch arm."""
     import torch
     from paper_2104_07526_gb300 import build as lib_build
     from paper_2104_07526_gb300 import pcr, scenes
@@ -1140,6 +1143,9 @@ def run_part(args) -> int:
                 best = a.elapsed_time(b) if best is None else min(best, a.elapsed_time(b))
                 del buf
             out[name] = round(best, 3)
+    elif args.part == "served":
+        out["served"] = run_served(h, pcr, stream, "cuda", args.served_seconds, plain_baseline=False,
+                                   rates=(8000.0,))[0]["served"]
     else:
         clouds = [scenes.boxes(nc, seed=i, device="cuda") for i, nc in enumerate(scenes.BATCH_CLOUD_SIZES)]
         vertex_order(h, pcr, clouds, "cuda")
