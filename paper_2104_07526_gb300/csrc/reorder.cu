@@ -20,6 +20,7 @@
 // Ranks follow index order, so each pass, and the sort, is stable.
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "../../include/pcr.h"
 #include "common.cuh"
@@ -168,8 +169,7 @@ __device__ __forceinline__ uint32_t quantise(float v, float lo, float scale) {
 // Sec. 5: Morton code over the cube with the bounds' minimum corner and the
 // largest extent as side, 10 levels.
 __global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, uint32_t n,
-                                                const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys,
-                                                uint32_t* __restrict__ vals) {
+                                                const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys) {
   const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
   const float hi[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
   float ext = __fsub_rn(hi[0], lo[0]);
@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, u
                spread3(quantise(__uint_as_float(r[u].z), lo[2], scale));
       }
       keys[i] = code;
-      vals[i] = static_cast<uint32_t>(i);
     }
   }
 }
@@ -225,7 +224,7 @@ __device__ __forceinline__ uint32_t quantise21(float v, float lo, float scale) {
 // Writes the code's low 32 bits to keys_lo and its high 31 bits to hi.
 __global__ void __launch_bounds__(256) k_morton63(const uint4* __restrict__ pts, uint32_t n,
                                                   const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys_lo,
-                                                  uint32_t* __restrict__ hi, uint32_t* __restrict__ vals) {
+                                                  uint32_t* __restrict__ hi) {
   const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
   const float top[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
   float ext = __fsub_rn(top[0], lo[0]);
@@ -245,7 +244,6 @@ __global__ void __launch_bounds__(256) k_morton63(const uint4* __restrict__ pts,
     }
     keys_lo[i] = static_cast<uint32_t>(code);
     hi[i] = static_cast<uint32_t>(code >> 32);
-    vals[i] = static_cast<uint32_t>(i);
   }
 }
 
@@ -261,14 +259,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
 // Keys for the random orders: the high half of SplitMix64 output i.  With
 // `copy`, record i of `pts` is also copied there (the source of the final
 // gather), saving a pass.
-__global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t seed, uint32_t* __restrict__ keys,
-                                                     uint32_t* __restrict__ vals, const uint4* __restrict__ pts,
-                                                     uint4* __restrict__ copy) {
-  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < count; i += gridDim.x * 256ull) {
+__global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t seed, uint32_t* __restrict__ keys) {
+  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < count; i += gridDim.x * 256ull)
     keys[i] = static_cast<uint32_t>(splitmix64(seed, i) >> 32);
-    if (vals) vals[i] = static_cast<uint32_t>(i);
-    if (copy) __stcs(copy + i, __ldcs(pts + i));
-  }
 }
 
 // --- radix sort ---------------------------------------------------------------
@@ -349,10 +342,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
 
 
 // Dynamic shared memory of k_sort_scatter: the tile's keys as loaded, each
-// output slot's input slot, the per-warp first slot of each digit, and
-// per-digit starts (tile-local and global).  46 KB: four blocks per SM.
+// output slot's input slot, the per-warp first slot of each digit, and per
+// digit the output position minus the tile slot of its first key.  45 KB:
+// four blocks per SM.
 constexpr size_t kScatterSmem =
-    sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile + sizeof(uint32_t) * (kSortWarps * kRadix + 2 * kRadix);
+    sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile + sizeof(uint32_t) * (kSortWarps * kRadix + kRadix);
 
 // 16-byte asynchronous copy global -> shared (cp.async, completes on
 // cp.async.wait_all); `bytes` < 16 reads only that many and zero-fills.
@@ -362,8 +356,10 @@ __device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_sr
 }
 
 // `cin`/`cout` (may be null): a second 32-bit value carried with each key
-// (the high words of 63-bit codes while their low words are sorted).  `vin`/
-// `vout` may be null when no value is carried.  With REC, the 16-byte point
+// (the high words of 63-bit codes while their low words are sorted).  `vout`
+// may be null when no value is carried; a null `vin` with a `vout` carries
+// each key's input index (the first pass of a sort whose values start as the
+// identity, so they are never written out and read back).  With REC, the 16-byte point
 // record `rin[i]` moves with its key to `rout` (the random order sorts the
 // records themselves: every pass reads them in tile order and writes them in
 // digit runs, instead of one random gather at the end).
@@ -380,9 +376,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
   uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
-  uint32_t* local_start = wbase + kSortWarps * kRadix;              // [kRadix]
-  uint32_t* global_start = local_start + kRadix;                    // [kRadix]
-  uint16_t* s_src = reinterpret_cast<uint16_t*>(global_start + kRadix);  // [kTile]
+  uint32_t* delta = wbase + kSortWarps * kRadix;                    // [kRadix]
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(delta + kRadix);    // [kTile]
   const uint32_t t = threadIdx.x;
   const uint32_t lane = lane_id();
   const uint32_t warp = t >> 5;
@@ -395,7 +390,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   asm volatile("cp.async.commit_group;" ::: "memory");
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] = 0;
-  global_start[t] = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
+  const uint32_t global_start = offsets[static_cast<uint64_t>(t) * tiles + blockIdx.x];
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   // this warp's 768 consecutive keys; pass 1 counts their digits, and each
@@ -429,7 +424,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   }
   uint32_t total;
   const uint32_t start = block_exclusive_scan<kSortThreads>(run, total);
-  local_start[t] = start;
+  delta[t] = global_start - start;  // modulo 2^32: output position = delta + tile slot
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] += start;
   __syncthreads();
@@ -450,17 +445,48 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   }
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
-  // output positions; values are gathered from the tile's 24 KB window
+  // output positions; values are gathered from the tile's 24 KB window.  One
+  // loop per combination of what moves with the keys, chosen once, so each
+  // unrolled loop carries no per-key test.
+  auto write_out = [&](auto values, auto carried) {
+    constexpr int kValues = decltype(values)::value;  // 0 none, 1 loaded, 2 the key's index
+    constexpr bool kCarried = decltype(carried)::value;
+    auto one = [&](uint32_t l) {
+      const uint32_t src = s_src[l];
+      const uint32_t key = s_kin[src];
+      const uint32_t d = (key >> shift) & (kRadix - 1);
+      const uint32_t g = delta[d] + l;
+      kout[g] = key;
+      if constexpr (kValues == 1) vout[g] = __ldg(vin + tile_base + src);
+      if constexpr (kValues == 2) vout[g] = static_cast<uint32_t>(tile_base + src);
+      if constexpr (kCarried) cout[g] = __ldg(cin + tile_base + src);
+      if constexpr (REC) __stcs(rout + g, __ldg(rin + tile_base + src));
+    };
+    // records: one key per iteration (unrolled 2, 3, 4 or 8 times the 800M
+    // shuffle took 36.2, 35.9, 38.1 and 39.2 ms against 35.4); keys and 4-byte
+    // values: eight
+    if constexpr (REC) {
+#pragma unroll 1
+      for (uint32_t l = t; l < total; l += kSortThreads) one(l);
+    } else {
 #pragma unroll 8
-  for (uint32_t l = t; l < total; l += kSortThreads) {
-    const uint32_t src = s_src[l];
-    const uint32_t key = s_kin[src];
-    const uint32_t d = (key >> shift) & (kRadix - 1);
-    const uint32_t g = global_start[d] + (l - local_start[d]);
-    kout[g] = key;
-    if (vout) vout[g] = __ldg(vin + tile_base + src);
-    if (cout) cout[g] = __ldg(cin + tile_base + src);
-    if constexpr (REC) __stcs(rout + g, __ldg(rin + tile_base + src));
+      for (uint32_t l = t; l < total; l += kSortThreads) one(l);
+    }
+  };
+  using C0 = std::integral_constant<int, 0>;
+  using C1 = std::integral_constant<int, 1>;
+  using C2 = std::integral_constant<int, 2>;
+  using Yes = std::true_type;
+  using No = std::false_type;
+  if (!vout) {
+    if (cout) write_out(C0{}, Yes{});
+    else write_out(C0{}, No{});
+  } else if (vin) {
+    if (cout) write_out(C1{}, Yes{});
+    else write_out(C1{}, No{});
+  } else {
+    if (cout) write_out(C2{}, Yes{});
+    else write_out(C2{}, No{});
   }
 }
 
@@ -576,10 +602,11 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 // result ends in buffer index `out` (0 or 1).  With `carry` (may be null),
 // a second value per key moves with it through its own two buffers; with
 // `recs` (may be null), a 16-byte record does.  vals may hold null buffers
-// when no value is needed.
+// when no value is needed.  With `index_values` the values start as each
+// key's index: the first pass makes them, and vals[0] is never read.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
-                       uint32_t* partials, cudaStream_t s, int& out, uint32_t* const* carry = nullptr,
-                       uint4* const* recs = nullptr) {
+                       uint32_t* partials, cudaStream_t s, int& out, bool index_values,
+                       uint32_t* const* carry = nullptr, uint4* const* recs = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
@@ -590,13 +617,14 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
     k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
     e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
+    const uint32_t* vin = (index_values && shift == 0) ? nullptr : vals[out];
     if (recs)
       k_sort_scatter<true><<<tiles, kSortThreads, kScatterSmem, s>>>(
-          keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, nullptr, nullptr, recs[out],
+          keys[out], vin, keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, nullptr, nullptr, recs[out],
           recs[out ^ 1]);
     else
       k_sort_scatter<false><<<tiles, kSortThreads, kScatterSmem, s>>>(
-          keys[out], vals[out], keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
+          keys[out], vin, keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
           carry ? carry[out ^ 1] : nullptr, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -721,10 +749,10 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     // the records themselves are sorted by their random keys (4 passes, an
     // even number: they end back in the caller's buffer); indices ride along
     // only when the permutation is asked for
-    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0], perm_out ? vals[0] : nullptr, nullptr, nullptr);
+    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0]);
     uint32_t* ivals[2] = {perm_out ? vals[0] : nullptr, perm_out ? vals[1] : nullptr};
     uint4* recs[2] = {pts, copy};
-    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, nullptr, recs);
+    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, true, nullptr, recs);
     if (e != cudaSuccess) return e;
     if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes
     if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
@@ -732,8 +760,8 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   } else if (!wide) {
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
-    k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], vals[0]);
-    e = radix_sort(keys, vals, n, 30, counts, partials, s, out);
+    k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0]);
+    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true);
   } else {
     // 63-bit code: the high halves ride along with their keys while the low
     // halves are sorted, in two buffers in the record-copy region (not
@@ -742,14 +770,14 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
                        reinterpret_cast<uint32_t*>(ws + l.pts_copy) + align_up(4ull * n) / 4};
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
-    k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi[0], vals[0]);
+    k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi[0]);
     int a = 0;
-    e = radix_sort(keys, vals, n, 32, counts, partials, s, a, hi);
+    e = radix_sort(keys, vals, n, 32, counts, partials, s, a, true, hi);
     if (e != cudaSuccess) return e;
     uint32_t* hkeys[2] = {hi[a], hi[a ^ 1]};
     uint32_t* hvals[2] = {vals[a], vals[a ^ 1]};
     int b = 0;
-    e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b);
+    e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b, false);
     // the sorted values end in vals[a ^ b]
     out = a ^ b;
   }
@@ -759,9 +787,9 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
-    k_random_keys<<<stream_grid(nb, d), 256, 0, s>>>(nb, seed, bkeys[0], bvals[0], nullptr, nullptr);
+    k_random_keys<<<stream_grid(nb, d), 256, 0, s>>>(nb, seed, bkeys[0]);
     int bout = 0;
-    e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout);
+    e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true);
     if (e != cudaSuccess) return e;
     k_find_last_batch<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, misc);
     if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
