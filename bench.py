@@ -407,39 +407,64 @@ def oracle_baseline(cloud_host_fn, n: int, view, target_s: float) -> dict:
 
 
 def run_small_configs(h, pcr, stream, dev, with_cpu: bool) -> dict:
-    """The two smaller workloads beside the headline one: the 1M-point
-    sphere-and-plane scene (640x480, L2-resident points: launch- and
-    L2-bound) and the 50M-point boxes scene (overview camera, 1920x1080),
-    both in shuffled-Morton order.  Per workload: the GPU frame (clear,
-    early-z render, resolve) with CUDA events, and, as CPU baselines, the
-    oracle's host-parallel and single-threaded frames on the whole cloud."""
+    """The two smaller workloads beside the headline one, each as its
+    configuration states it, in generation order: the 1M-point sphere-and-
+    plane scene (640x480, L2-resident points), basic atomicMin frame; the
+    50M-point boxes scene, every camera (overview, mid, inside a box) with
+    the basic, dedup, early-z and HQ frames.  Beside them, the same frames
+    after the paper's recommended shuffled-Morton reorder.  A basic frame is
+    clear + render + resolve, an HQ frame clear + depth + colours + resolve,
+    timed with CUDA events.  CPU baselines: the oracle's host-parallel and
+    single-threaded basic frames on the whole cloud."""
     import torch
+    basic = {"atomicMin": pcr.PCR_VARIANT_ATOMICMIN, "dedup": pcr.PCR_VARIANT_DEDUP,
+             "early-z": pcr.PCR_VARIANT_EARLYZ, "dedup+early-z": pcr.PCR_VARIANT_DEDUP_EARLYZ}
+    plan = {"sphere1M": (["atomicMin", "early-z"], False), "boxes50M": (list(basic), True)}
     out = {}
     for name in ("sphere1M", "boxes50M"):
         cfg = CONFIGS[name]
+        variants, with_hq = plan[name]
         cloud, views = make_cloud(cfg, dev)
-        vertex_order(h, pcr, [cloud], dev)
-        view = next(v for v in views if v.name == cfg["view"])
         n = cloud.shape[0]
-        fb = pcr.alloc_framebuffer(view.width, view.height, dev)
-        pcr.pcr_upload_points(h, cloud, n)
-        pcr.pcr_set_matrix(h, view.matrix)
-        pcr.pcr_set_viewport(h, view.width, view.height)
+        reps = 200 if n <= 10_000_000 else 50
+        W, H = max(v.width for v in views), max(v.height for v in views)
+        fb = pcr.alloc_framebuffer(W, H, dev)
         pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
 
-        def frame():
-            pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
-            pcr.pcr_render_basic(h, pcr.PCR_VARIANT_EARLYZ, False)
-            pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+        def frames():
+            pcr.pcr_upload_points(h, cloud, n)
+            res = {}
+            for v in views:
+                pcr.pcr_set_matrix(h, v.matrix)
+                pcr.pcr_set_viewport(h, v.width, v.height)
+                row = {}
+                for vname in variants:
+                    def frame(var=basic[vname]):
+                        pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
+                        pcr.pcr_render_basic(h, var, False)
+                        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
+                    row[vname] = round(time_loop(frame, stream, reps=reps, warm=5), 4)
+                if with_hq:
+                    def hq_frame():
+                        pcr.pcr_render_hq(h, 1.01, pcr.PCR_VARIANT_DEDUP_EARLYZ, True)
+                        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, fb["image"], 0)
+                    row["hq"] = round(time_loop(hq_frame, stream, reps=reps, warm=5), 4)
+                res[v.name] = row
+            return res
 
-        reps = 200 if n <= 10_000_000 else 50
-        ms = time_loop(frame, stream, reps=reps, warm=5)
-        row = {"points": n, "width": view.width, "height": view.height, "gpu_frame_ms": ms,
-               "gpu_points_per_s": n / (ms * 1e-3), "frames": reps}
+        original = frames()
+        vertex_order(h, pcr, [cloud], dev)
+        reordered = frames()
+        head = next(v for v in views if v.name == cfg["view"])
+        first = variants[0]
+        ms = original[head.name][first]
+        row = {"points": n, "width": head.width, "height": head.height, "camera": head.name,
+               "order": "original", "variant": first, "gpu_frame_ms": ms, "gpu_points_per_s": n / (ms * 1e-3),
+               "frames": reps, "frame_ms": {"original": original, "morton_shuffle128": reordered}}
         if with_cpu:
             host = cloud.cpu().numpy()
-            t_all = time_oracle(host, view, repeats=2, threads=0)
-            t_one = time_oracle(host, view, repeats=1, threads=1)
+            t_all = time_oracle(host, head, repeats=2, threads=0)
+            t_one = time_oracle(host, head, repeats=1, threads=1)
             row["cpu_baseline"] = {"kind": "oracle", "cores": oracle_threads(), "frame_ms": t_all * 1e3,
                                    "points_per_s": n / t_all, "single_thread_frame_ms": t_one * 1e3,
                                    "single_thread_points_per_s": n / t_one,
