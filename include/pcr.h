@@ -109,8 +109,10 @@ enum {
 enum {
     PCR_DEVICE_ERROR_KEY_RANGE = 1,    /* a resolve found a key naming a point outside the cloud */
     PCR_DEVICE_ERROR_WAIT_TIMEOUT = 2, /* a busy-loop lock wait gave up (a point was dropped) */
-    PCR_DEVICE_ERROR_BOUNDS = 4        /* debug builds: a geometry kernel computed a pixel outside the
-                                          viewport (the point was dropped); release builds never set it */
+    PCR_DEVICE_ERROR_BOUNDS = 4        /* debug builds: a geometry kernel (single-view or batch) computed a
+                                          pixel outside its viewport (the point was dropped), or a reorder
+                                          kernel met an index or destination outside the cloud (the access
+                                          was skipped); release builds never set it */
 };
 
 typedef struct pcr_ctx pcr_ctx;

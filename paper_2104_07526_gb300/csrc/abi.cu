@@ -743,7 +743,12 @@ pcr_status pcr_last_device_error(pcr_ctx* ctx, uint32_t* code) {
   if (!ctx || !code) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
-  return from_cuda(pcr::read_and_clear_error_word(code, ctx->stream));
+  uint32_t batch = 0, reorder = 0;
+  cudaError_t e = pcr::read_and_clear_error_word(code, ctx->stream);
+  if (e == cudaSuccess) e = pcr::read_and_clear_batch_error_word(&batch, ctx->stream);
+  if (e == cudaSuccess) e = pcr::read_and_clear_reorder_error_word(&reorder, ctx->stream);
+  *code |= batch | reorder;
+  return from_cuda(e);
 }
 
 }  // extern "C"

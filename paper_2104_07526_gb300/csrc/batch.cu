@@ -84,6 +84,31 @@ extern __shared__ __align__(16) unsigned char g_smem_tables[];
 
 constexpr uint64_t align256(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
+// Debug builds (PCR_DEBUG) check every visible slot's pixel against its
+// view before any access; a failure sets PCR_DEVICE_ERROR_BOUNDS in this
+// file's error word (read by pcr_last_device_error) and drops the slot.
+#ifdef PCR_DEBUG
+__device__ uint32_t g_batch_error_word;
+#endif
+template <int U>
+__device__ __forceinline__ void debug_check_view_pixels(const ViewParams& vp, const uint32_t (&pix)[U],
+                                                        bool (&vis)[U]) {
+#ifdef PCR_DEBUG
+  const uint64_t npx = static_cast<uint64_t>(vp.width) * vp.height;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (vis[u] && pix[u] >= npx) {
+      atomicOr(&g_batch_error_word, static_cast<uint32_t>(PCR_DEVICE_ERROR_BOUNDS));
+      vis[u] = false;
+    }
+  }
+#else
+  (void)vp;
+  (void)pix;
+  (void)vis;
+#endif
+}
+
 // Copy the header, clouds, views and (phase >= 0) that phase's groups and
 // order into shared memory.
 __device__ __forceinline__ Shared load_tables(const Tables* __restrict__ g, int phase) {
@@ -171,6 +196,7 @@ __device__ __forceinline__ void project_all(const ViewParams& vp, const uint4 (&
   project_slots<U>(vp, r, pix, w, vis);
 #pragma unroll
   for (int u = 0; u < U; ++u) vis[u] = vis[u] && ok[u];
+  debug_check_view_pixels<U>(vp, pix, vis);
 }
 
 // Phase 1: per view of the pass, basic key and HQ depth, each with the
@@ -501,6 +527,22 @@ cudaError_t batch_prewarm(const Device& d) {
   prewarm_phases<512>();
   prewarm_single_view(d);
   return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_batch_error_word(uint32_t* out, cudaStream_t s) {
+  *out = 0;
+#ifdef PCR_DEBUG
+  const uint32_t zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_batch_error_word, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_batch_error_word, &zero, sizeof(uint32_t), 0,
+                                                    cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+#else
+  (void)s;
+  return cudaSuccess;
+#endif
 }
 
 int batch_config_threads(int config) { return 256 << ((config >> 2) & 1); }

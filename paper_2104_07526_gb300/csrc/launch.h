@@ -44,6 +44,10 @@ cudaError_t launch_resolve_hq1r(const unsigned long long* primary, const unsigne
 cudaError_t launch_resolve_hq(const unsigned long long* rg, const unsigned long long* ba, uint64_t npx,
                               uint32_t background, uint32_t* out, cudaStream_t s, const Device& d);
 cudaError_t read_and_clear_error_word(uint32_t* out, cudaStream_t s);
+// Debug builds: the error words of the batch and reorder kernels (0, with no
+// device access, in release builds).
+cudaError_t read_and_clear_batch_error_word(uint32_t* out, cudaStream_t s);
+cudaError_t read_and_clear_reorder_error_word(uint32_t* out, cudaStream_t s);
 // Run the occupancy queries of the single-view kernels the batch launches
 // (before a capture).
 void prewarm_single_view(const Device& d);

@@ -30,6 +30,26 @@ namespace pcr {
 
 namespace {
 
+// Debug builds (PCR_DEBUG) check every gathered index and every scatter
+// destination against the cloud before the access; a failure sets
+// PCR_DEVICE_ERROR_BOUNDS in this file's error word (read by
+// pcr_last_device_error) and skips the access.  Release builds check nothing.
+#ifdef PCR_DEBUG
+__device__ uint32_t g_reorder_error_word;
+#endif
+__device__ __forceinline__ bool debug_in_range(uint64_t i, uint64_t n) {
+#ifdef PCR_DEBUG
+  if (i >= n) {
+    atomicOr(&g_reorder_error_word, static_cast<uint32_t>(PCR_DEVICE_ERROR_BOUNDS));
+    return false;
+  }
+#else
+  (void)i;
+  (void)n;
+#endif
+  return true;
+}
+
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortRounds = 24;  // keys per lane in a tile
@@ -437,7 +457,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
     const uint32_t rank = v & 0xFFu;
     const uint32_t at = ok ? mine[d] : 0u;
     __syncwarp();
-    if (ok) {
+    if (ok && debug_in_range(at + rank, kTile)) {
       s_src[at + rank] = static_cast<uint16_t>(wfirst + r * 32 + lane);
       if (rank == 0) mine[d] = at + ((v >> 8) & 0xFFu);
     }
@@ -456,6 +476,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
       const uint32_t key = s_kin[src];
       const uint32_t d = (key >> shift) & (kRadix - 1);
       const uint32_t g = delta[d] + l;
+      if (!debug_in_range(g, n)) return;
       kout[g] = key;
       if constexpr (kValues == 1) vout[g] = __ldg(vin + tile_base + src);
       if constexpr (kValues == 2) vout[g] = static_cast<uint32_t>(tile_base + src);
@@ -662,6 +683,7 @@ __global__ void __launch_bounds__(256) k_gather_batches(const uint4* __restrict_
     if (k < size) {
       const uint64_t at = static_cast<uint64_t>(t) * kBatch - (t > t_last ? (kBatch - last_size) : 0u) + k;
       const uint32_t p = morton[static_cast<uint64_t>(b) * kBatch + k];
+      if (!debug_in_range(p, n) || !debug_in_range(at, n)) continue;
       dst[at] = src[p];
       if (perm_out) perm_out[at] = p;
     }
@@ -677,6 +699,7 @@ __global__ void __launch_bounds__(256) k_gather16(const uint4* __restrict__ src,
                                                   uint32_t n) {
   for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < n; j += gridDim.x * 256ull) {
     const uint32_t p = perm[j];
+    if (!debug_in_range(p, n)) continue;
     dst[j] = src[p];
     if (perm_out) perm_out[j] = p;
   }
@@ -800,6 +823,22 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
   k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
   return cudaGetLastError();
+}
+
+cudaError_t read_and_clear_reorder_error_word(uint32_t* out, cudaStream_t s) {
+  *out = 0;
+#ifdef PCR_DEBUG
+  const uint32_t zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_reorder_error_word, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_reorder_error_word, &zero, sizeof(uint32_t), 0,
+                                                    cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+#else
+  (void)s;
+  return cudaSuccess;
+#endif
 }
 
 cudaError_t launch_reorder_noalloc(uint4* pts, uint32_t n, uint64_t seed, int mode, uint32_t* perm_out,

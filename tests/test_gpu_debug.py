@@ -176,3 +176,66 @@ def test_release_build_has_no_counters():
     with pcr.Context(0, stream=torch.cuda.current_stream()) as ctx:
         out = (C.c_uint64 * 4)()
         assert pcr.lib().pcr_debug_counters(ctx.handle, out) == pcr.PCR_ERR_UNSUPPORTED
+
+
+@pytest.fixture()
+def debug_lib():
+    """pcr's wrappers bound to the debug library for one test."""
+    build.build(debug=True)
+    saved = pcr._lib
+    pcr._lib = pcr.load_library(pcr.DEBUG_LIB_PATH)
+    try:
+        yield pcr._lib
+    finally:
+        pcr._lib = saved
+
+
+def test_debug_reorder_and_batch_match_the_oracle_with_silent_checks(debug_lib, oracle):
+    """The debug build's range checks in the reorder gathers and scatter and
+    its pixel checks in the batch phases stay silent on correct inputs, and
+    the results are the oracle's."""
+    from gpu_helpers import reorder_gpu
+    with pcr.Context(0, stream=torch.cuda.current_stream()) as c:
+        for n in (1, 6145, 100_003):
+            cloud = scenes.random_cloud(n, seed=n + 11).numpy()
+            for mode in (pcr.PCR_ORDER_MORTON, pcr.PCR_ORDER_MORTON_SHUFFLE128, pcr.PCR_ORDER_SHUFFLE,
+                         pcr.PCR_ORDER_MORTON63, pcr.PCR_ORDER_MORTON63_SHUFFLE128):
+                expect = oracle.reorder(cloud, 99 + n, mode)
+                dev = torch.from_numpy(cloud.copy()).cuda()
+                perm = reorder_gpu(c.handle, dev, 99 + n, mode)
+                assert np.array_equal(perm, expect), (n, mode)
+                assert np.array_equal(dev.cpu().numpy(), oracle.gather(cloud, expect)), (n, mode)
+        assert pcr.pcr_last_device_error(c.handle) == 0
+        # a batch: two clouds, views sharing passes, one alone in its pass
+        sphere = scenes.sphere_plane(20_011, seed=3).numpy()
+        rnd = scenes.random_cloud(3001, seed=4).numpy()
+        clouds = [sphere, rnd]
+        views = [(0, scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), 80, 60), 80, 60, 3),
+                 (0, scenes.camera((1.5, 2.5, 2.0), (0, 0, 0), (0, 0, 1), 64, 48), 64, 48, 2),
+                 (1, scenes.camera((0.2, -2.6, 1.4), (0, 0, 0), (0, 0, 1), 40, 30), 40, 30, 1)]
+        dev = [torch.from_numpy(x.copy()).cuda() for x in clouds]
+        bufs, vs = [], []
+        for (ci, m, W, H, flags) in views:
+            b = pcr.alloc_framebuffer(W, H, "cuda")
+            b["hq_image"] = torch.empty(W * H, dtype=torch.int32, device="cuda")
+            bufs.append(b)
+            kw = {}
+            if flags & pcr.PCR_BATCH_BASIC:
+                kw.update(keys=b["keys"], image=b["image"])
+            if flags & pcr.PCR_BATCH_HQ:
+                kw.update(hq_depth=b["hq_depth"], hq_rg=b["hq_rg"], hq_ba=b["hq_ba"], hq_image=b["hq_image"])
+            vs.append(pcr.batch_view(m, W, H, ci, flags, **kw))
+        ws = torch.empty(pcr.pcr_batch_workspace_size(), dtype=torch.uint8, device="cuda")
+        pcr.pcr_batch_prepare(c.handle, [pcr.batch_cloud(d) for d in dev], vs, 1.01, 0, ws)
+        for config in (0, 8):
+            pcr.pcr_batch_launch(c.handle, ws, config)
+            torch.cuda.synchronize()
+            for (ci, m, W, H, flags), b in zip(views, bufs):
+                if flags & pcr.PCR_BATCH_BASIC:
+                    want = oracle.render_basic(clouds[ci], m, W, H)
+                    assert np.array_equal(b["keys"].cpu().numpy().view(np.uint64), want), config
+                if flags & pcr.PCR_BATCH_HQ:
+                    d, rg, ba = oracle.render_hq(clouds[ci], m, W, H, 1.01)
+                    assert np.array_equal(b["hq_rg"].cpu().numpy().view(np.uint64), rg), config
+                    assert np.array_equal(b["hq_ba"].cpu().numpy().view(np.uint64), ba), config
+        assert pcr.pcr_last_device_error(c.handle) == 0
