@@ -915,7 +915,8 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
     return {"workload": "8 boxes clouds (1M..200M points, 388M total, shuffled-Morton order) x 8 orbit views "
                         "(256^2..2048^2), basic + HQ",
             "per_request_ms": per_ms, "per_request_launches": 7 * len(views), "batched_graph_ms": batched_ms,
-            "batched_launches": 4, "speedup": per_ms / batched_ms, "identical": identical, "config": config,
+            "batched_launches": pcr.pcr_batch_launch_count(h, ws, config), "speedup": per_ms / batched_ms,
+            "identical": identical, "config": config,
             "tuning": {**{k: tuning[k] for k in ("l2_budget_mb", "config", "threads", "unroll1", "unroll2",
                                                  "single_colors", "tried")},
                        "tuned_ms": tuning["best_ms"], "default_ms": tuning["default_ms"],

@@ -382,6 +382,13 @@ PCR_API pcr_status pcr_batch_prepare(pcr_ctx *ctx, const pcr_batch_cloud *clouds
  * (pcr_batch_prepare or pcr_batch_tune). */
 PCR_API pcr_status pcr_batch_launch(pcr_ctx *ctx, const void *dev_workspace, int config);
 
+/* The number of kernel launches pcr_batch_launch(config) makes for a
+ * workspace this context prepared (host computation: the clear and resolve
+ * kernels, the geometry phases that have passes, and the single-view
+ * launches).  Errors: PCR_ERR_ARG for NULL arguments, a bad config, or a
+ * workspace this context has not prepared. */
+PCR_API pcr_status pcr_batch_launch_count(pcr_ctx *ctx, const void *dev_workspace, int config, int *count);
+
 /* Time every launch configuration on the prepared batch (each rendered a few
  * times; the outputs are overwritten) and return the fastest in *config.
  * Synchronises the stream.  Errors: PCR_ERR_ARG on NULL arguments. */

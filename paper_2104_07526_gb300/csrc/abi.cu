@@ -630,6 +630,14 @@ pcr_status pcr_batch_launch(pcr_ctx* ctx, const void* dev_workspace, int config)
   return from_cuda(pcr::batch_launch(plan, dev_workspace, config, ctx->stream, ctx->dev));
 }
 
+pcr_status pcr_batch_launch_count(pcr_ctx* ctx, const void* dev_workspace, int config, int* count) {
+  if (!ctx || !dev_workspace || !count || config < 0 || config >= pcr::batch_num_configs()) return PCR_ERR_ARG;
+  const void* plan = find_plan(ctx, dev_workspace);
+  if (!plan) return PCR_ERR_ARG;
+  *count = pcr::batch_launch_count(plan, config);
+  return PCR_OK;
+}
+
 pcr_status pcr_batch_autotune(pcr_ctx* ctx, const void* dev_workspace, int* config) {
   if (!ctx || !dev_workspace || !config || !aligned(dev_workspace, 256)) return PCR_ERR_ARG;
   const void* plan = find_plan(ctx, dev_workspace);

@@ -545,6 +545,25 @@ cudaError_t read_and_clear_batch_error_word(uint32_t* out, cudaStream_t s) {
 #endif
 }
 
+int batch_launch_count(const void* host_tables, int config) {
+  const Tables& h = *static_cast<const Tables*>(host_tables);
+  auto single = [&](uint32_t vi, int phase) {
+    const BatchView& v = h.views[vi];
+    if (h.clouds[v.cloud].n == 0) return 0;
+    if (phase == 1) return (v.flags & PCR_BATCH_HQ) ? 1 : 0;
+    return ((v.flags & PCR_BATCH_BASIC) ? 1 : 0) + ((v.flags & PCR_BATCH_HQ) ? 1 : 0);
+  };
+  int count = 2 + (h.hdr.total_slots[0] > 0 ? 1 : 0);
+  for (uint32_t k = 0; k < h.num_single[0]; ++k) count += single(h.single[0][k], 0);
+  if (batch_config_single_colors(config)) {
+    for (uint32_t vi = 0; vi < h.hdr.num_views; ++vi) count += single(vi, 1);
+  } else {
+    count += h.hdr.total_slots[1] > 0 ? 1 : 0;
+    for (uint32_t k = 0; k < h.num_single[1]; ++k) count += single(h.single[1][k], 1);
+  }
+  return count;
+}
+
 int batch_config_threads(int config) { return 256 << ((config >> 2) & 1); }
 int batch_config_unroll(int config, int phase) { return (config & (phase == 0 ? 2 : 1)) ? 2 : 4; }
 bool batch_config_single_colors(int config) { return (config & 8) != 0; }

@@ -134,6 +134,8 @@ bool batch_config_single_colors(int config);
 // launches read their views from it during the call).
 cudaError_t batch_launch(const void* host_tables, const void* workspace, int config, cudaStream_t s,
                          const Device& d);
+// Kernel launches batch_launch makes for these tables and configuration.
+int batch_launch_count(const void* host_tables, int config);
 // Run the occupancy queries of every configuration once (before a capture).
 cudaError_t batch_prewarm(const Device& d);
 

@@ -151,6 +151,7 @@ _SIGS = {
     "pcr_batch_tune": [_VP, C.POINTER(PcrBatchCloud), _U32, C.POINTER(PcrBatchView), _U32, _FLT, _U32, _VP, _U64,
                        C.c_char_p, C.POINTER(PcrBatchTuning)],
     "pcr_batch_capture": [_VP, _VP, _INT, C.POINTER(_VP)],
+    "pcr_batch_launch_count": [_VP, _VP, _INT, C.POINTER(_INT)],
     "pcr_graph_launch": [_VP, _VP],
     "pcr_graph_destroy": [_VP],
     "pcr_server_create": [_VP, C.POINTER(PcrServerConfig), C.POINTER(_VP)],
@@ -410,6 +411,13 @@ def pcr_batch_tune(ctx: int, clouds, views, depth_factor: float, background_rgba
                                 _dptr(workspace, "workspace"), _nbytes(workspace) if workspace is not None else 0,
                                 cache_path.encode() if cache_path else None, C.byref(out)), "pcr_batch_tune")
     return {k: getattr(out, k) for k, _ in PcrBatchTuning._fields_}
+
+
+def pcr_batch_launch_count(ctx: int, workspace, config: int) -> int:
+    out = _INT()
+    _check(lib().pcr_batch_launch_count(ctx, _dptr(workspace, "workspace"), config, C.byref(out)),
+           "pcr_batch_launch_count")
+    return out.value
 
 
 def pcr_batch_capture(ctx: int, workspace, config: int) -> int:

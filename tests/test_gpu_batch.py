@@ -164,7 +164,8 @@ def test_batch_rejects_bad_descriptions(ctx):
     with pcr.Context(0, stream=torch.cuda.current_stream()) as other:
         for call in (lambda: pcr.pcr_batch_launch(other.handle, ws, 0),
                      lambda: pcr.pcr_batch_capture(other.handle, ws, 0),
-                     lambda: pcr.pcr_batch_autotune(other.handle, ws)):
+                     lambda: pcr.pcr_batch_autotune(other.handle, ws),
+                     lambda: pcr.pcr_batch_launch_count(other.handle, ws, 0)):
             with pytest.raises(pcr.PcrError) as e:
                 call()
             assert e.value.status == pcr.PCR_ERR_ARG
@@ -188,6 +189,15 @@ def test_batch_table_limits(ctx, oracle):
     for clouds, vs in ((one, views), (many, views_many)):
         expected = _expected(oracle, clouds, vs)
         dev, bufs, ws = _prepare(ctx, clouds, vs)
+        if clouds is many:
+            # every view is alone with its cloud: one-frame views render single-view
+            # in both phases, two-frame views keep one shared phase-1 pass
+            live = [f for (c, _, _, _, f) in vs if clouds[c].shape[0]]
+            singles0 = sum(1 for f in live if f != BASIC | HQ)
+            hq = sum(1 for f in live if f & HQ)
+            expect = 2 + (1 if any(f == BASIC | HQ for f in live) else 0) + singles0 + hq
+            assert pcr.pcr_batch_launch_count(ctx, ws, 0) == expect
+            assert pcr.pcr_batch_launch_count(ctx, ws, 8) == expect
         for config in range(pcr.pcr_batch_num_configs()):
             _poison(bufs)
             pcr.pcr_batch_launch(ctx, ws, config)
