@@ -6,7 +6,8 @@
 // stable sort by the whole code.
 //
 // Radix sort: 8-bit digits, one pass per digit, three steps per pass:
-//   1. k_sort_hist: per tile of 6144 keys, count each digit.
+//   1. k_sort_hist: per tile of 6144 keys, count each digit (the first
+//      pass's counts come from the kernel that made the keys);
 //   2. exclusive scan of the counts in digit-major order, which gives every
 //      (digit, tile) its first output slot;
 //   3. k_sort_scatter: each warp of a tile takes 768 consecutive keys and
@@ -186,10 +187,74 @@ __device__ __forceinline__ uint32_t quantise(float v, float lo, float scale) {
   return static_cast<uint32_t>(f);
 }
 
+// The kernels that make the keys also count the first sort pass's digits:
+// one block per tile of kTile keys makes the tile's keys (thread t takes
+// tile slots t, t + 256, ..., so loads and stores coalesce), keeps them in
+// shared memory, and counts them as k_sort_hist does (lane l of warp w takes
+// slots [768 w + 24 l, + 24) and adds each run of equal digits once), so the
+// first pass's histogram costs no second read of the keys.
+struct alignas(16) TileKeys {
+  uint32_t keys[kTile];  // read as 16-byte vectors by count_tile_digits
+  uint32_t hist[kSortWarps][kRadix];
+};
+
+__device__ __forceinline__ void count_tile_digits(TileKeys& sh, uint32_t valid, uint32_t* __restrict__ counts,
+                                                  uint32_t tiles) {
+  __syncthreads();  // the tile's keys are in place
+  uint32_t* mine = sh.hist[threadIdx.x >> 5];
+  const uint32_t first = (threadIdx.x >> 5) * (kTile / kSortWarps) + lane_id() * kSortRounds;
+  uint32_t cur = 0, run = 0;
+  if (first + kSortRounds <= valid) {
+    const uint4* q = reinterpret_cast<const uint4*>(sh.keys + first);  // 96-byte aligned
+#pragma unroll
+    for (int k = 0; k < kSortRounds / 4; ++k) {
+      const uint4 v = q[k];
+      const uint32_t d[4] = {v.x & (kRadix - 1), v.y & (kRadix - 1), v.z & (kRadix - 1), v.w & (kRadix - 1)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        if (d[e] == cur) {
+          ++run;
+        } else {
+          if (run) atomicAdd(&mine[cur], run);
+          cur = d[e];
+          run = 1;
+        }
+      }
+    }
+  } else {
+    for (uint32_t j = first; j < valid && j < first + kSortRounds; ++j) {
+      const uint32_t d = sh.keys[j] & (kRadix - 1);
+      if (d == cur) {
+        ++run;
+      } else {
+        if (run) atomicAdd(&mine[cur], run);
+        cur = d;
+        run = 1;
+      }
+    }
+  }
+  if (run) atomicAdd(&mine[cur], run);
+  __syncthreads();
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) c += sh.hist[w][threadIdx.x];
+  counts[static_cast<uint64_t>(threadIdx.x) * tiles + blockIdx.x] = c;
+}
+
+__device__ __forceinline__ void zero_tile_hist(TileKeys& sh) {
+#pragma unroll
+  for (int w = 0; w < kSortWarps; ++w) sh.hist[w][threadIdx.x] = 0;
+}
+
+
 // Sec. 5: Morton code over the cube with the bounds' minimum corner and the
 // largest extent as side, 10 levels.
-__global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, uint32_t n,
-                                                const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys) {
+__global__ void __launch_bounds__(kSortThreads) k_morton(const uint4* __restrict__ pts, uint32_t n,
+                                                         const uint32_t* __restrict__ misc,
+                                                         uint32_t* __restrict__ keys, uint32_t* __restrict__ counts,
+                                                         uint32_t tiles) {
+  __shared__ TileKeys sh;
+  zero_tile_hist(sh);
   const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
   const float hi[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
   float ext = __fsub_rn(hi[0], lo[0]);
@@ -199,27 +264,31 @@ __global__ void __launch_bounds__(256) k_morton(const uint4* __restrict__ pts, u
   if (ez > ext) ext = ez;
   const bool degenerate = !(ext > 0.0f) || !(ext < __int_as_float(kInfBits));
   const float scale = degenerate ? 0.0f : __fdiv_rn(1024.0f, ext);
-  const uint64_t step = gridDim.x * 256ull * kStreamUnroll;
-  for (uint64_t i0 = blockIdx.x * 256ull * kStreamUnroll + threadIdx.x; i0 < n; i0 += step) {
+  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
+  const uint32_t valid = static_cast<uint32_t>(n - tile_base < kTile ? n - tile_base : kTile);
+  // kStreamUnroll records per thread in flight at a time
+  for (uint32_t j0 = threadIdx.x; j0 < valid; j0 += kSortThreads * kStreamUnroll) {
     uint4 r[kStreamUnroll];
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) {
-      const uint64_t i = i0 + 256ull * u;
-      r[u] = (!degenerate && i < n) ? __ldcs(pts + i) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t j = j0 + kSortThreads * u;
+      r[u] = (!degenerate && j < valid) ? __ldcs(pts + tile_base + j) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) {
-      const uint64_t i = i0 + 256ull * u;
-      if (i >= n) break;
+      const uint32_t j = j0 + kSortThreads * u;
+      if (j >= valid) break;
       uint32_t code = 0;
       if (!degenerate) {
         code = (spread3(quantise(__uint_as_float(r[u].x), lo[0], scale)) << 2) |
                (spread3(quantise(__uint_as_float(r[u].y), lo[1], scale)) << 1) |
                spread3(quantise(__uint_as_float(r[u].z), lo[2], scale));
       }
-      keys[i] = code;
+      keys[tile_base + j] = code;
+      sh.keys[j] = code;
     }
   }
+  count_tile_digits(sh, valid, counts, tiles);
 }
 
 // Spread the low 21 bits of v so bit i lands on bit 3i.
@@ -242,9 +311,12 @@ __device__ __forceinline__ uint32_t quantise21(float v, float lo, float scale) {
 
 // Sec. 5 with the paper's 21 levels: the same cube, 2^21 cells per axis.
 // Writes the code's low 32 bits to keys_lo and its high 31 bits to hi.
-__global__ void __launch_bounds__(256) k_morton63(const uint4* __restrict__ pts, uint32_t n,
-                                                  const uint32_t* __restrict__ misc, uint32_t* __restrict__ keys_lo,
-                                                  uint32_t* __restrict__ hi) {
+__global__ void __launch_bounds__(kSortThreads) k_morton63(const uint4* __restrict__ pts, uint32_t n,
+                                                           const uint32_t* __restrict__ misc,
+                                                           uint32_t* __restrict__ keys_lo, uint32_t* __restrict__ hi,
+                                                           uint32_t* __restrict__ counts, uint32_t tiles) {
+  __shared__ TileKeys sh;
+  zero_tile_hist(sh);
   const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
   const float top[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
   float ext = __fsub_rn(top[0], lo[0]);
@@ -254,17 +326,21 @@ __global__ void __launch_bounds__(256) k_morton63(const uint4* __restrict__ pts,
   if (ez > ext) ext = ez;
   const bool degenerate = !(ext > 0.0f) || !(ext < __int_as_float(kInfBits));
   const float scale = degenerate ? 0.0f : __fdiv_rn(2097152.0f, ext);
-  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) {
+  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
+  const uint32_t valid = static_cast<uint32_t>(n - tile_base < kTile ? n - tile_base : kTile);
+  for (uint32_t j = threadIdx.x; j < valid; j += kSortThreads) {
     uint64_t code = 0;
     if (!degenerate) {
-      const uint4 r = __ldcs(pts + i);
+      const uint4 r = __ldcs(pts + tile_base + j);
       code = (spread3_21(quantise21(__uint_as_float(r.x), lo[0], scale)) << 2) |
              (spread3_21(quantise21(__uint_as_float(r.y), lo[1], scale)) << 1) |
              spread3_21(quantise21(__uint_as_float(r.z), lo[2], scale));
     }
-    keys_lo[i] = static_cast<uint32_t>(code);
-    hi[i] = static_cast<uint32_t>(code >> 32);
+    keys_lo[tile_base + j] = static_cast<uint32_t>(code);
+    hi[tile_base + j] = static_cast<uint32_t>(code >> 32);
+    sh.keys[j] = static_cast<uint32_t>(code);
   }
+  count_tile_digits(sh, valid, counts, tiles);
 }
 
 // SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): output k of the generator
@@ -276,12 +352,21 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
   return z ^ (z >> 31);
 }
 
-// Keys for the random orders: the high half of SplitMix64 output i.  With
-// `copy`, record i of `pts` is also copied there (the source of the final
-// gather), saving a pass.
-__global__ void __launch_bounds__(256) k_random_keys(uint32_t count, uint64_t seed, uint32_t* __restrict__ keys) {
-  for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < count; i += gridDim.x * 256ull)
-    keys[i] = static_cast<uint32_t>(splitmix64(seed, i) >> 32);
+// Keys for the random orders: the high half of SplitMix64 output i, with the
+// first sort pass's digit counts.
+__global__ void __launch_bounds__(kSortThreads) k_random_keys(uint32_t count, uint64_t seed,
+                                                              uint32_t* __restrict__ keys,
+                                                              uint32_t* __restrict__ counts, uint32_t tiles) {
+  __shared__ TileKeys sh;
+  zero_tile_hist(sh);
+  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
+  const uint32_t valid = static_cast<uint32_t>(count - tile_base < kTile ? count - tile_base : kTile);
+  for (uint32_t j = threadIdx.x; j < valid; j += kSortThreads) {
+    const uint32_t key = static_cast<uint32_t>(splitmix64(seed, tile_base + j) >> 32);
+    keys[tile_base + j] = key;
+    sh.keys[j] = key;
+  }
+  count_tile_digits(sh, valid, counts, tiles);
 }
 
 // --- radix sort ---------------------------------------------------------------
@@ -624,9 +709,11 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 // a second value per key moves with it through its own two buffers; with
 // `recs` (may be null), a 16-byte record does.  vals may hold null buffers
 // when no value is needed.  With `index_values` the values start as each
-// key's index: the first pass makes them, and vals[0] is never read.
+// key's index: the first pass makes them, and vals[0] is never read.  With
+// `first_counted` the kernel that made the keys has already written the
+// first pass's digit counts (k_morton, k_morton63, k_random_keys).
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
-                       uint32_t* partials, cudaStream_t s, int& out, bool index_values,
+                       uint32_t* partials, cudaStream_t s, int& out, bool index_values, bool first_counted,
                        uint32_t* const* carry = nullptr, uint4* const* recs = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
@@ -635,7 +722,7 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kScatterSmem));
   if (e != cudaSuccess) return e;
   for (int shift = 0; shift < key_bits; shift += kDigitBits) {
-    k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
+    if (!(first_counted && shift == 0)) k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
     e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
     const uint32_t* vin = (index_values && shift == 0) ? nullptr : vals[out];
@@ -763,6 +850,7 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   uint32_t* partials = reinterpret_cast<uint32_t*>(ws + l.partials);
   uint32_t* misc = reinterpret_cast<uint32_t*>(ws + l.misc);
   const unsigned grid = stream_grid(n, d);
+  const uint32_t tiles = static_cast<uint32_t>(ceil_div(n, kTile));  // the sort's tiles
   cudaError_t e = cudaSuccess;
   int out = 0;
   // the record copy the final gather reads is made by the first pass over
@@ -772,10 +860,10 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     // the records themselves are sorted by their random keys (4 passes, an
     // even number: they end back in the caller's buffer); indices ride along
     // only when the permutation is asked for
-    k_random_keys<<<grid, 256, 0, s>>>(n, seed, keys[0]);
+    k_random_keys<<<tiles, kSortThreads, 0, s>>>(n, seed, keys[0], counts, tiles);
     uint32_t* ivals[2] = {perm_out ? vals[0] : nullptr, perm_out ? vals[1] : nullptr};
     uint4* recs[2] = {pts, copy};
-    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, true, nullptr, recs);
+    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, true, true, nullptr, recs);
     if (e != cudaSuccess) return e;
     if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes
     if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
@@ -783,8 +871,8 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   } else if (!wide) {
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
-    k_morton<<<grid, 256, 0, s>>>(pts, n, misc, keys[0]);
-    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true);
+    k_morton<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], counts, tiles);
+    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true, true);
   } else {
     // 63-bit code: the high halves ride along with their keys while the low
     // halves are sorted, in two buffers in the record-copy region (not
@@ -793,14 +881,14 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
                        reinterpret_cast<uint32_t*>(ws + l.pts_copy) + align_up(4ull * n) / 4};
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
-    k_morton63<<<grid, 256, 0, s>>>(pts, n, misc, keys[0], hi[0]);
+    k_morton63<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], hi[0], counts, tiles);
     int a = 0;
-    e = radix_sort(keys, vals, n, 32, counts, partials, s, a, true, hi);
+    e = radix_sort(keys, vals, n, 32, counts, partials, s, a, true, true, hi);
     if (e != cudaSuccess) return e;
     uint32_t* hkeys[2] = {hi[a], hi[a ^ 1]};
     uint32_t* hvals[2] = {vals[a], vals[a ^ 1]};
     int b = 0;
-    e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b, false);
+    e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b, false, false);
     // the sorted values end in vals[a ^ b]
     out = a ^ b;
   }
@@ -810,9 +898,10 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
-    k_random_keys<<<stream_grid(nb, d), 256, 0, s>>>(nb, seed, bkeys[0]);
+    const uint32_t btiles = static_cast<uint32_t>(ceil_div(nb, kTile));
+    k_random_keys<<<btiles, kSortThreads, 0, s>>>(nb, seed, bkeys[0], counts, btiles);
     int bout = 0;
-    e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true);
+    e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
     if (e != cudaSuccess) return e;
     k_find_last_batch<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, misc);
     if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
