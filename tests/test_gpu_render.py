@@ -135,6 +135,30 @@ def test_tiny_and_wide_viewports(r, oracle):
             assert np.array_equal(r.render_basic(v), expect), (W, H, v)
 
 
+def test_largest_viewport(r, oracle):
+    """The largest viewport the interface takes, 16384 x 16384 (2^28 pixels:
+    pixel indices near the top of their 32-bit range, a 2 GB key buffer),
+    bit-exact for the basic variants, the HQ buffers and the resolve."""
+    W = H = 16384
+    cloud = scenes.sphere_plane(200_003, seed=21).numpy()
+    m = scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), W, H, 90.0)
+    r.upload(cloud)
+    r.view(m, W, H)
+    expect = oracle.render_basic(cloud, m, W, H)
+    covered = np.nonzero(expect != U64_EMPTY)[0]
+    assert covered.size > 100_000 and covered.max() > (1 << 27)  # pixels in the upper half of the range
+    for v in (pcr.PCR_VARIANT_ATOMICMIN, pcr.PCR_VARIANT_EARLYZ, pcr.PCR_VARIANT_DEDUP_EARLYZ):
+        assert np.array_equal(r.render_basic(v), expect), v
+    pcr.pcr_resolve(r.h, pcr.PCR_RESOLVE_BASIC, r.fb["image"], 0x11223344)
+    torch.cuda.synchronize()
+    assert np.array_equal(r.fb["image"].cpu().numpy().view(np.uint32),
+                          oracle.resolve_basic(expect, cloud, 0x11223344))
+    del expect
+    got = r.render_hq(pcr.PCR_VARIANT_DEDUP_EARLYZ)
+    for a, b in zip(got, oracle.render_hq(cloud, m, W, H, 1.01)):
+        assert np.array_equal(a, b)
+
+
 def test_no_clear_accumulates(r, oracle, sphere):
     """clear=0 merges by minimum: rendering the same cloud twice equals once,
     and a buffer pre-filled with keys keeps the smaller of old and new."""
