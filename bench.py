@@ -929,7 +929,7 @@ def run_batched(h, pcr, stream, dev, reps: int) -> dict:
 def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 3, max_batch_views: int = 64,
                batch_config: int = 0, plain_baseline: bool = True, rates=(2000.0,), streams: int = 3,
                max_batch_clouds: int = 1, policy: int | None = None, max_queue: int = 256,
-               deadline_us: int = 0) -> list:
+               deadline_us: int = 0, l2_budget_mb: int = 0) -> list:
     """16 boxes clouds (1M..300M points, shuffled-Morton order) registered
     with the server from host memory, a 150 GB arena, and for each rate a
     Poisson stream of requests (random cloud, resolution 512^2..3840x2160,
@@ -951,13 +951,13 @@ def run_served(h, pcr, stream, dev, seconds: float, max_inflight: int = 3, max_b
         out.append(served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, max_inflight,
                                   max_batch_views, batch_config, plain_baseline, streams, max_batch_clouds,
                                   pcr.PCR_SERVE_LARGEST_GROUP if policy is None else policy, max_queue,
-                                  deadline_us))
+                                  deadline_us, l2_budget_mb))
     return out
 
 
 def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, max_inflight, max_batch_views,
                    batch_config, plain_baseline, streams, max_batch_clouds, policy=0, max_queue=0,
-                   deadline_us=0) -> dict:
+                   deadline_us=0, l2_budget_mb=0) -> dict:
     import torch
     from paper_2104_07526_gb300 import scenes
     reqs = scenes.serve_requests(int(rate * seconds), rate, seed=7, num_clouds=len(sizes))
@@ -965,7 +965,8 @@ def served_at_rate(h, pcr, dev, dev_clouds, host_clouds, sizes, seconds, rate, m
     srv = pcr.pcr_server_create(h, arena, 3840, 2160, num_slots=128, max_batch_views=max_batch_views,
                                 max_inflight=max_inflight, streams=streams, max_batch_clouds=max_batch_clouds,
                                 batch_config=batch_config, depth_factor=1.01, background_rgba=0,
-                                max_queue=max_queue, deadline_us=deadline_us, policy=policy)
+                                max_queue=max_queue, deadline_us=deadline_us, policy=policy,
+                                l2_budget_mb=l2_budget_mb)
     try:
         for i, hc in enumerate(host_clouds):
             pcr.pcr_server_add_cloud(srv, i, hc)

@@ -464,6 +464,8 @@ typedef struct pcr_server_config {
     uint32_t deadline_us;      /* a request still queued this long after its submission expires
                                   instead of rendering (PCR_REQUEST_EXPIRED), 0 = never */
     uint32_t policy;           /* PCR_SERVE_ARRIVAL or PCR_SERVE_LARGEST_GROUP */
+    uint32_t l2_budget_mb;     /* framebuffer bytes one pass over a cloud may touch, in MB (views of a
+                                  cloud are packed into passes that fit); 0 = 64, at most 1024 */
 } pcr_server_config;
 
 /* Which queued requests a new batch takes (pcr_server_step). */

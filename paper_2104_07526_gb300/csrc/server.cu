@@ -322,7 +322,9 @@ pcr_status launch_one(pcr_server* s, pcr::Inflight& f, bool* launched) {
     v.hq_image = (r.flags & PCR_BATCH_HQ) ? p.hq_image : nullptr;
   }
   pcr::batch_build_tables(bc.data(), static_cast<uint32_t>(bc.size()), bv.data(), static_cast<uint32_t>(bv.size()),
-                          s->cfg.depth_factor, s->cfg.background_rgba, f.staging, pcr::kServedL2Budget);
+                          s->cfg.depth_factor, s->cfg.background_rgba, f.staging,
+                          s->cfg.l2_budget_mb ? static_cast<uint64_t>(s->cfg.l2_budget_mb) << 20
+                                              : pcr::kServedL2Budget);
 
   cudaError_t e = cudaSuccess;
   for (uint32_t id : uploads) {
@@ -406,6 +408,7 @@ pcr_status pcr_server_create(pcr_ctx* ctx, const pcr_server_config* cfg, pcr_ser
   if (!(cfg->depth_factor > 0.0f) || !(cfg->depth_factor < 3.0e38f)) return PCR_ERR_ARG;
   if (cfg->batch_config < 0 || cfg->batch_config >= pcr::batch_num_configs()) return PCR_ERR_ARG;
   if (cfg->policy != PCR_SERVE_ARRIVAL && cfg->policy != PCR_SERVE_LARGEST_GROUP) return PCR_ERR_ARG;
+  if (cfg->l2_budget_mb > 1024) return PCR_ERR_ARG;
   pcr_server* s = new (std::nothrow) pcr_server();
   if (!s) return PCR_ERR_CUDA;
   s->dev = pcr::ctx_device(ctx);

@@ -80,7 +80,8 @@ class PcrServerConfig(C.Structure):
                 ("max_height", C.c_uint32), ("num_slots", C.c_uint32), ("max_batch_views", C.c_uint32),
                 ("max_inflight", C.c_uint32), ("streams", C.c_uint32), ("max_batch_clouds", C.c_uint32),
                 ("batch_config", C.c_int32), ("depth_factor", C.c_float), ("background_rgba", C.c_uint32),
-                ("max_queue", C.c_uint32), ("deadline_us", C.c_uint32), ("policy", C.c_uint32)]
+                ("max_queue", C.c_uint32), ("deadline_us", C.c_uint32), ("policy", C.c_uint32),
+                ("l2_budget_mb", C.c_uint32)]
 
 
 class PcrRequest(C.Structure):
@@ -437,11 +438,11 @@ def pcr_graph_destroy(graph_exec: int):
 def pcr_server_create(ctx: int, arena, max_width: int, max_height: int, num_slots: int, max_batch_views: int = 64,
                       max_inflight: int = 2, streams: int = 0, max_batch_clouds: int = 0, batch_config: int = 0,
                       depth_factor: float = 1.01, background_rgba: int = 0, max_queue: int = 0,
-                      deadline_us: int = 0, policy: int = PCR_SERVE_ARRIVAL) -> int:
+                      deadline_us: int = 0, policy: int = PCR_SERVE_ARRIVAL, l2_budget_mb: int = 0) -> int:
     """arena: CUDA uint8 tensor (the server's device memory)."""
     cfg = PcrServerConfig(_dptr(arena, "arena"), _nbytes(arena), max_width, max_height, num_slots, max_batch_views,
                           max_inflight, streams, max_batch_clouds, batch_config, depth_factor,
-                          background_rgba & 0xFFFFFFFF, max_queue, deadline_us, policy)
+                          background_rgba & 0xFFFFFFFF, max_queue, deadline_us, policy, l2_budget_mb)
     out = _VP()
     _check(lib().pcr_server_create(ctx, C.byref(cfg), C.byref(out)), "pcr_server_create")
     return out.value
