@@ -362,3 +362,39 @@ def test_admission_bound_and_deadline(ctx, oracle):
     with pytest.raises(pcr.PcrError) as e:
         pcr.pcr_server_create(ctx, arena, W, H, 2, policy=7)
     assert e.value.status == pcr.PCR_ERR_ARG
+
+
+def test_l2_budget_changes_passes_not_results(ctx, oracle):
+    """The server's L2 budget decides how a batch's views of one cloud are
+    packed into passes: at 1 MB every view has a pass of its own (single-view
+    kernels), at 1024 MB they all share one.  Results are the same either
+    way; a budget above 1024 MB is refused."""
+    clouds = _clouds()
+    dev = [torch.from_numpy(c.copy()).cuda() for c in clouds]
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(47)
+    reqs = []
+    for _ in range(10):
+        W, H = int(rng.integers(1, 201)), int(rng.integers(1, 151))
+        a = rng.uniform(0, 2 * np.pi)
+        m = scenes.camera((3 * np.cos(a), 3 * np.sin(a), 1.5), (0, 0, 0), (0, 0, 1), W, H)
+        reqs.append((0, m, W, H, int(rng.choice([BASIC, HQ, BASIC | HQ]))))
+    for budget in (1, 1024):
+        srv = pcr.pcr_server_create(ctx, arena, 200, 150, num_slots=12, max_batch_views=12, max_inflight=1,
+                                    background_rgba=BG, l2_budget_mb=budget)
+        try:
+            pcr.pcr_server_add_device_cloud(srv, 0, dev[0])
+            tickets = {pcr.pcr_server_submit(srv, 0, m, W, H, f): (m, W, H, f) for _, m, W, H, f in reqs}
+
+            def finish(t):
+                m, W, H, f = tickets.pop(t)
+                _check_result(ctx, srv, t, clouds[0], m, W, H, f, oracle)
+                pcr.pcr_server_release(srv, t)
+
+            _drain(srv, list(tickets), finish)
+            assert not tickets
+        finally:
+            pcr.pcr_server_destroy(srv)
+    with pytest.raises(pcr.PcrError) as e:
+        pcr.pcr_server_create(ctx, arena, 200, 150, 2, l2_budget_mb=1025)
+    assert e.value.status == pcr.PCR_ERR_ARG
