@@ -48,10 +48,11 @@ FALLBACK_HBM_GBS = 6800.0
 # measured copy bandwidth.
 NOMINAL_HBM_GBS = 8000.0
 # The timed frame's variant.  Every exact variant leaves the same buffer; on
-# GB300 the early depth test alone is the fastest of them on the scan scene,
-# or within 1% of early-z with warp deduplication (the sweep in the JSON line
-# times all of them).
-HEADLINE_VARIANT = "early-z"
+# the scan scene's overview in shuffled-Morton order, early-z with warp
+# deduplication (Sec. 3.4, the paper's fastest) is 1-2% faster than the early
+# test alone, and the two lead the rest (the sweep in the JSON line times all
+# of them).
+HEADLINE_VARIANT = "dedup+early-z"
 # The HQ frames' depth-pass variant (the colour pass sums colours inside the
 # warp for every variant but atomicMin): with the early test the depth pass
 # is the same for early-z and dedup+early-z up to the deduplication, which
