@@ -3,17 +3,19 @@
 // as one CUDA graph.
 //
 // Each pass over a cloud's points projects every point for a group of that
-// cloud's views.  Phase 1 writes the basic key (Sec. 3.1-3.2, with the
-// early depth test) and the high-quality depth (Sec. 3.5) from one
-// projection; phase 2, after all depth buffers are complete, adds the
-// high-quality colours (summed inside the warp first).  A group holds as many views as fit an L2 budget
-// (framebuffer bytes the pass touches), packed first-fit by decreasing size,
-// so the atomics and early depth reads of a pass stay in L2 while the point
-// stream passes through.  The passes of a phase are laid out as one sequence
-// of 128-point slots (each pass padded to a multiple of 128) that a
-// persistent grid walks in uniform chunks: clouds of uneven size need no work
-// queue and nothing waits.  Results equal the per-view calls bit for bit:
-// minima and integer sums do not depend on order.
+// cloud's views.  Phase 1 (index 0 in the tables) writes the basic key (Sec.
+// 3.1-3.2, with the early depth test) and the high-quality depth (Sec. 3.5)
+// from one projection; phase 2 (index 1), after all depth buffers are
+// complete, adds the high-quality colours (summed inside the warp first).  A
+// group holds as many views as fit an L2 budget (framebuffer bytes the pass
+// touches), packed first-fit by decreasing size, so the atomics and early
+// depth reads of a pass stay in L2 while the point stream passes through; a
+// view alone in its pass goes through the single-view kernels instead.  The
+// passes of a phase are laid out as one sequence of 128-point slots (each
+// pass padded to a multiple of 128) that a persistent grid walks in uniform
+// chunks: clouds of uneven size need no work queue and nothing waits.
+// Results equal the per-view calls bit for bit: minima and integer sums do
+// not depend on order.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -41,9 +43,10 @@ struct Tables {
   BatchView views[kBatchMaxViews];
   BatchGroup groups[2][kBatchMaxViews];
   uint16_t order[2][kBatchMaxViews];
-  // Per phase, the views that are alone in their pass (phase 1: with one
-  // flag) and run through the single-view kernels instead; the host reads
-  // these from its copy of the tables when it launches the batch.
+  // Per phase (0: keys and depth, 1: colours), the views that are alone in
+  // their pass (in phase 0 only those with one frame) and run through the
+  // single-view kernels instead; the host reads these from its copy of the
+  // tables when it launches the batch.
   uint32_t num_single[2];
   uint16_t single[2][kBatchMaxViews];
 };
@@ -377,8 +380,8 @@ void launch_batch_phase(const Tables& h, const Tables* t, int config, int phase,
   else launch_phase<256>(t, smem, config, phase, s, d);
 }
 
-// The single-view kernels of one view and phase: phase 0 the basic keys
-// (early-z) and the HQ depth (dedup+early-z), phase 1 the HQ colours (warp
+// The single-view kernels of one view and phase (index): 0 the basic keys
+// (early-z) and the HQ depth (dedup+early-z), 1 the HQ colours (warp
 // aggregated) -- the kernels pcr_render_basic and pcr_render_hq run.
 cudaError_t launch_single(const Tables& h, uint32_t vi, int phase, cudaStream_t s, const Device& d) {
   const BatchView& v = h.views[vi];
@@ -413,9 +416,9 @@ namespace {
 // Pack the views of each cloud that take part in a phase into passes whose
 // framebuffer bytes fit the L2 budget (first fit, largest first); a view
 // larger than the budget gets a pass of its own.  A pass of one view shares
-// no point loads: that view goes to the phase's single-view list instead
-// (in phase 1 only when it asks for one frame; with both, the batch pass
-// still reads its points once for the two).
+// no point loads: that view goes to the phase's single-view list instead (in
+// the keys-and-depth phase, index 0, only when it asks for one frame; with
+// both, the batch pass still reads its points once for the two).
 void build_groups(Tables* t, const pcr_batch_cloud* clouds, uint32_t num_clouds, const pcr_batch_view* views,
                   uint32_t num_views, int phase, uint64_t l2_budget) {
   uint32_t ng = 0, nord = 0, nsingle = 0;
