@@ -1,5 +1,7 @@
 """Batched rendering (many clouds x views in one launch sequence or one CUDA
 graph) against the CPU oracle, bit for bit, for every launch configuration."""
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -233,6 +235,15 @@ def test_batch_tune_chooses_and_caches(ctx, oracle, tmp_path):
     _poison(bufs)
     pcr.pcr_batch_launch(ctx, ws, first["config"])
     _check(bufs, expected, "tuned")
+    # lines it cannot use are skipped: garbage, and entries for this GPU and
+    # shape with a budget or configuration it does not offer
+    with open(cache) as f:
+        line = f.read().splitlines()[0]
+    entry = json.loads(line)
+    with open(cache, "a") as f:
+        f.write("not json at all\n")
+        f.write(json.dumps({**entry, "budget_mb": 77}) + "\n")
+        f.write(json.dumps({**entry, "config": 99}) + "\n")
     again = pcr.pcr_batch_tune(ctx, cs_, vs, 1.01, BG, ws, cache)
     assert again["from_cache"] == 1 and again["tried"] == 0
     assert (again["l2_budget_mb"], again["config"]) == (first["l2_budget_mb"], first["config"])
@@ -241,7 +252,7 @@ def test_batch_tune_chooses_and_caches(ctx, oracle, tmp_path):
     _check(bufs, expected, "from cache")
     with open(cache) as f:
         lines = f.read().splitlines()
-    assert len(lines) == 1 and '"budget_mb": %d' % first["l2_budget_mb"] in lines[0]
+    assert len(lines) == 4 and '"budget_mb": %d' % first["l2_budget_mb"] in lines[0]
     # another shape misses the cache
     other = pcr.pcr_batch_tune(ctx, cs_, vs[:3], 1.01, BG, ws, cache)
     assert other["from_cache"] == 0
