@@ -500,9 +500,16 @@ typedef struct pcr_server_stats {
     uint64_t peak_queue, queued, resident_clouds, resident_bytes;
     uint64_t rejected;         /* submissions refused with PCR_ERR_BUSY */
     uint64_t expired;          /* requests that reached their deadline while queued */
+    uint64_t cancelled;        /* queued requests withdrawn by pcr_server_cancel */
 } pcr_server_stats;
 
-enum { PCR_REQUEST_QUEUED = 0, PCR_REQUEST_RUNNING = 1, PCR_REQUEST_DONE = 2, PCR_REQUEST_EXPIRED = 3 };
+enum {
+    PCR_REQUEST_QUEUED = 0,
+    PCR_REQUEST_RUNNING = 1,
+    PCR_REQUEST_DONE = 2,
+    PCR_REQUEST_EXPIRED = 3,
+    PCR_REQUEST_CANCELLED = 4
+};
 
 /* Create a server on the context's device.  Frame slots (36 bytes per pixel
  * of max_width x max_height each) and one batch workspace per in-flight batch
@@ -553,20 +560,29 @@ PCR_API pcr_status pcr_server_submit(pcr_server *srv, const pcr_request *req, ui
  * which other requests shared its batch. */
 PCR_API pcr_status pcr_server_step(pcr_server *srv, uint32_t *completed);
 
-/* PCR_REQUEST_QUEUED, _RUNNING, _DONE or _EXPIRED for a ticket not yet
- * released. */
+/* PCR_REQUEST_QUEUED, _RUNNING, _DONE, _EXPIRED or _CANCELLED for a ticket
+ * not yet released. */
 PCR_API pcr_status pcr_server_state(pcr_server *srv, uint64_t ticket, int *state);
 
 /* Result of a finished request: device pointers into its frame slot (valid
- * until pcr_server_release) and its time stamps.  An expired request has
- * NULL pointers, flags 0, points 0 and done_us at its expiry. */
+ * until pcr_server_release) and its time stamps.  An expired or cancelled
+ * request has NULL pointers, flags 0, points 0 and done_us at its expiry or
+ * cancellation. */
 PCR_API pcr_status pcr_server_get_result(pcr_server *srv, uint64_t ticket, pcr_server_result *out);
 
-/* Report up to `capacity` tickets that finished or expired since the previous
- * call, in completion order; *count receives how many were written. */
+/* Report up to `capacity` tickets that finished, expired or were cancelled
+ * since the previous call, in completion order; *count receives how many were
+ * written. */
 PCR_API pcr_status pcr_server_poll_completed(pcr_server *srv, uint64_t *tickets, uint32_t capacity, uint32_t *count);
 
-/* Give a finished request's frame slot back (or forget an expired request).
+/* Withdraw a queued request: it leaves the queue unrendered, becomes
+ * PCR_REQUEST_CANCELLED and is reported like a finished one (poll, result,
+ * release).  Errors: PCR_ERR_BUSY if it is already on the GPU (it will
+ * finish); PCR_ERR_ARG for an unknown ticket or one already finished. */
+PCR_API pcr_status pcr_server_cancel(pcr_server *srv, uint64_t ticket);
+
+/* Give a finished request's frame slot back (or forget an expired or
+ * cancelled request).
  * Reads of the slot issued on other streams must have completed first: the
  * slot may be rewritten by the next batch. */
 PCR_API pcr_status pcr_server_release(pcr_server *srv, uint64_t ticket);

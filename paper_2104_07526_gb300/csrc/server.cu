@@ -92,7 +92,7 @@ struct Cloud {
   bool uploaded_once = false;
 };
 
-enum : int { kQueued = 0, kRunning = 1, kDone = 2, kExpired = 3 };
+enum : int { kQueued = 0, kRunning = 1, kDone = 2, kExpired = 3, kCancelled = 4 };
 
 struct Request {
   uint32_t cloud = 0;
@@ -143,9 +143,13 @@ struct pcr_server {
 namespace {
 
 using pcr::kDone;
+using pcr::kCancelled;
 using pcr::kExpired;
 using pcr::kQueued;
 using pcr::kRunning;
+
+// A request that left the server's hands: rendered, expired or cancelled.
+bool finished(int state) { return state == kDone || state == kExpired || state == kCancelled; }
 
 struct SlotPtrs {
   unsigned long long* keys;
@@ -547,9 +551,9 @@ pcr_status pcr_server_state(pcr_server* s, uint64_t ticket, int* state) {
 pcr_status pcr_server_get_result(pcr_server* s, uint64_t ticket, pcr_server_result* out) {
   if (!s || !out) return PCR_ERR_ARG;
   auto it = s->requests.find(ticket);
-  if (it == s->requests.end() || (it->second.state != kDone && it->second.state != kExpired)) return PCR_ERR_ARG;
+  if (it == s->requests.end() || !finished(it->second.state)) return PCR_ERR_ARG;
   const pcr::Request& r = it->second;
-  if (r.state == kExpired) {
+  if (r.state != kDone) {  // expired or cancelled: never rendered
     *out = pcr_server_result{};
     out->width = r.width;
     out->height = r.height;
@@ -585,10 +589,25 @@ pcr_status pcr_server_poll_completed(pcr_server* s, uint64_t* tickets, uint32_t 
   return PCR_OK;
 }
 
+pcr_status pcr_server_cancel(pcr_server* s, uint64_t ticket) {
+  if (!s) return PCR_ERR_ARG;
+  auto it = s->requests.find(ticket);
+  if (it == s->requests.end() || finished(it->second.state)) return PCR_ERR_ARG;
+  if (it->second.state == kRunning) return PCR_ERR_BUSY;
+  const auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+  if (q == s->queue.end()) return PCR_ERR_ARG;
+  s->queue.erase(q);
+  it->second.state = kCancelled;
+  it->second.t_done = pcr::now_us();
+  s->finished.push_back(ticket);
+  ++s->stats.cancelled;
+  return PCR_OK;
+}
+
 pcr_status pcr_server_release(pcr_server* s, uint64_t ticket) {
   if (!s) return PCR_ERR_ARG;
   auto it = s->requests.find(ticket);
-  if (it == s->requests.end() || (it->second.state != kDone && it->second.state != kExpired)) return PCR_ERR_ARG;
+  if (it == s->requests.end() || !finished(it->second.state)) return PCR_ERR_ARG;
   if (it->second.state == kDone) s->free_slots.push_back(it->second.slot);
   s->requests.erase(it);
   return PCR_OK;

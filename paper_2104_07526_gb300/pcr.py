@@ -102,10 +102,11 @@ class PcrServerStats(C.Structure):
     """pcr_server_stats"""
     _fields_ = [(k, C.c_uint64) for k in ("submitted", "completed", "batches", "views_launched", "uploads",
                                           "evictions", "bytes_uploaded", "points_rendered", "peak_queue", "queued",
-                                          "resident_clouds", "resident_bytes", "rejected", "expired")]
+                                          "resident_clouds", "resident_bytes", "rejected", "expired",
+                                          "cancelled")]
 
 
-PCR_REQUEST_QUEUED, PCR_REQUEST_RUNNING, PCR_REQUEST_DONE, PCR_REQUEST_EXPIRED = 0, 1, 2, 3
+PCR_REQUEST_QUEUED, PCR_REQUEST_RUNNING, PCR_REQUEST_DONE, PCR_REQUEST_EXPIRED, PCR_REQUEST_CANCELLED = 0, 1, 2, 3, 4
 
 
 class PcrError(RuntimeError):
@@ -166,6 +167,7 @@ _SIGS = {
     "pcr_server_release": [_VP, _U64],
     "pcr_server_poll_completed": [_VP, C.POINTER(_U64), _U32, C.POINTER(_U32)],
     "pcr_server_stats_get": [_VP, C.POINTER(PcrServerStats)],
+    "pcr_server_cancel": [_VP, _U64],
 }
 
 
@@ -504,6 +506,10 @@ def pcr_server_poll_completed(srv: int, capacity: int = 256) -> list[int]:
 
 def pcr_server_release(srv: int, ticket: int):
     _check(lib().pcr_server_release(srv, ticket), "pcr_server_release")
+
+
+def pcr_server_cancel(srv: int, ticket: int):
+    _check(lib().pcr_server_cancel(srv, ticket), "pcr_server_cancel")
 
 
 def pcr_server_stats_get(srv: int) -> dict:

@@ -398,3 +398,46 @@ def test_l2_budget_changes_passes_not_results(ctx, oracle):
     with pytest.raises(pcr.PcrError) as e:
         pcr.pcr_server_create(ctx, arena, 200, 150, 2, l2_budget_mb=1025)
     assert e.value.status == pcr.PCR_ERR_ARG
+
+
+def test_cancel_queued_requests(ctx, oracle):
+    """pcr_server_cancel withdraws a queued request (reported like a finished
+    one, with no buffers), refuses one already on the GPU (PCR_ERR_BUSY) and
+    unknown or finished tickets (PCR_ERR_ARG); the others render exactly."""
+    cloud = scenes.sphere_plane(30_011, seed=6).numpy()
+    dev = torch.from_numpy(cloud.copy()).cuda()
+    arena = torch.empty(128 << 20, dtype=torch.uint8, device="cuda")
+    W, H = 96, 64
+    m = scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), W, H)
+    srv = pcr.pcr_server_create(ctx, arena, W, H, num_slots=8, max_batch_views=1, max_inflight=1,
+                                background_rgba=BG)
+    try:
+        pcr.pcr_server_add_device_cloud(srv, 0, dev)
+        a = pcr.pcr_server_submit(srv, 0, m, W, H, BASIC)
+        pcr.pcr_server_step(srv)  # a is launched; b and c wait behind it
+        b = pcr.pcr_server_submit(srv, 0, m, W, H, HQ)
+        c = pcr.pcr_server_submit(srv, 0, m, W, H, BASIC | HQ)
+        assert pcr.pcr_server_state(srv, a) == pcr.PCR_REQUEST_RUNNING
+        with pytest.raises(pcr.PcrError) as e:
+            pcr.pcr_server_cancel(srv, a)
+        assert e.value.status == pcr.PCR_ERR_BUSY
+        pcr.pcr_server_cancel(srv, b)
+        assert pcr.pcr_server_state(srv, b) == pcr.PCR_REQUEST_CANCELLED
+        assert b in pcr.pcr_server_poll_completed(srv)
+        res = pcr.pcr_server_get_result(srv, b)
+        assert not res.keys and not res.hq_rg and res.points == 0 and res.done_us >= res.submit_us
+        with pytest.raises(pcr.PcrError) as e:
+            pcr.pcr_server_cancel(srv, b)  # already finished
+        assert e.value.status == pcr.PCR_ERR_ARG
+        pcr.pcr_server_release(srv, b)
+        with pytest.raises(pcr.PcrError) as e:
+            pcr.pcr_server_cancel(srv, 10 ** 9)  # unknown ticket
+        assert e.value.status == pcr.PCR_ERR_ARG
+        _drain(srv, [a, c])
+        for t, f in ((a, BASIC), (c, BASIC | HQ)):
+            _check_result(ctx, srv, t, cloud, m, W, H, f, oracle)
+            pcr.pcr_server_release(srv, t)
+        st = pcr.pcr_server_stats_get(srv)
+        assert st["cancelled"] == 1 and st["completed"] == 2 and st["queued"] == 0
+    finally:
+        pcr.pcr_server_destroy(srv)
