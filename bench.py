@@ -433,7 +433,7 @@ def run_small_configs(h, pcr, stream, dev, with_cpu: bool) -> dict:
         fb = pcr.alloc_framebuffer(W, H, dev)
         pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
 
-        def frames():
+        def frames(graphs: dict | None = None):
             pcr.pcr_upload_points(h, cloud, n)
             res = {}
             for v in views:
@@ -446,6 +446,14 @@ def run_small_configs(h, pcr, stream, dev, with_cpu: bool) -> dict:
                         pcr.pcr_render_basic(h, var, False)
                         pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], 0)
                     row[vname] = round(time_loop(frame, stream, reps=reps, warm=5), 4)
+                    if graphs is not None:
+                        # the same frame recorded once and replayed as one graph launch
+                        pcr.pcr_capture_begin(h)
+                        frame()
+                        g = pcr.pcr_capture_end(h)
+                        graphs.setdefault(v.name, {})[vname] = round(
+                            time_loop(lambda: pcr.pcr_graph_launch(h, g), stream, reps=reps, warm=5), 4)
+                        pcr.pcr_graph_destroy(g)
                 if with_hq:
                     def hq_frame():
                         pcr.pcr_render_hq(h, 1.01, pcr.PCR_VARIANT_DEDUP_EARLYZ, True)
@@ -454,15 +462,19 @@ def run_small_configs(h, pcr, stream, dev, with_cpu: bool) -> dict:
                 res[v.name] = row
             return res
 
-        original = frames()
+        launch_bound = n <= 10_000_000  # small clouds: launches, not the point stream, set the frame time
+        g_orig, g_reord = ({}, {}) if launch_bound else (None, None)
+        original = frames(g_orig)
         vertex_order(h, pcr, [cloud], dev)
-        reordered = frames()
+        reordered = frames(g_reord)
         head = next(v for v in views if v.name == cfg["view"])
         first = variants[0]
         ms = original[head.name][first]
         row = {"points": n, "width": head.width, "height": head.height, "camera": head.name,
                "order": "original", "variant": first, "gpu_frame_ms": ms, "gpu_points_per_s": n / (ms * 1e-3),
                "frames": reps, "frame_ms": {"original": original, "morton_shuffle128": reordered}}
+        if launch_bound:
+            row["graph_frame_ms"] = {"original": g_orig, "morton_shuffle128": g_reord}
         if with_cpu:
             host = cloud.cpu().numpy()
             t_all = time_oracle(host, head, repeats=2, threads=0)

@@ -430,6 +430,22 @@ PCR_API pcr_status pcr_batch_tune(pcr_ctx *ctx, const pcr_batch_cloud *clouds, u
  * a bad config, PCR_ERR_CUDA if capture or instantiation fails. */
 PCR_API pcr_status pcr_batch_capture(pcr_ctx *ctx, const void *dev_workspace, int config, void **graph_exec);
 
+/* Record the context's GPU work into a CUDA graph: between
+ * pcr_capture_begin and pcr_capture_end, the calls that launch work (clear,
+ * render, resolve, the HQ and HQS1R passes, pcr_batch_launch) are recorded
+ * instead of run, with the arguments and context state of each call (buffers
+ * and points are borrowed by the graph: they must outlive it).  Replaying a
+ * frame then costs one launch (pcr_graph_launch) instead of one per kernel,
+ * which matters for small clouds.  Calls that synchronise or copy from the
+ * host (pcr_synchronize, pcr_download, pcr_upload_points_from_host,
+ * pcr_last_device_error, pcr_debug_counters, pcr_check_division, the
+ * reorders, pcr_batch_prepare / _tune / _autotune / _capture,
+ * pcr_server_create, pcr_set_stream) return PCR_ERR_ARG while recording.
+ * Errors: PCR_ERR_ARG if a capture is already open (begin) or none is (end),
+ * PCR_ERR_CUDA if recording or instantiation fails (the capture is closed). */
+PCR_API pcr_status pcr_capture_begin(pcr_ctx *ctx);
+PCR_API pcr_status pcr_capture_end(pcr_ctx *ctx, void **graph_exec);
+
 /* Launch an instantiated graph on the context's stream. */
 PCR_API pcr_status pcr_graph_launch(pcr_ctx *ctx, void *graph_exec);
 

@@ -32,6 +32,10 @@ struct pcr_ctx {
   // a batch launch reads the views it renders through the single-view
   // kernels from it.
   std::unordered_map<const void*, std::vector<unsigned char>> batch_plans;
+  // Between pcr_capture_begin and pcr_capture_end: the private stream being
+  // recorded (it stands in for `stream`, saved in `captured_stream`).
+  cudaStream_t capture = nullptr;
+  cudaStream_t captured_stream = nullptr;
 };
 
 namespace {
@@ -86,7 +90,7 @@ bool view_ready(const pcr_ctx* c) { return c->has_matrix && c->width > 0 && c->h
 pcr_status check_batch(const pcr_ctx* ctx, const pcr_batch_cloud* clouds, uint32_t num_clouds,
                        const pcr_batch_view* views, uint32_t num_views, float depth_factor, const void* dev_workspace,
                        uint64_t workspace_bytes) {
-  if (!ctx || !clouds || !views) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || !clouds || !views) return PCR_ERR_ARG;  // both synchronise: not while capturing
   if (num_clouds == 0 || num_clouds > PCR_BATCH_MAX_CLOUDS || num_views == 0 || num_views > PCR_BATCH_MAX_VIEWS)
     return PCR_ERR_ARG;
   if (!(depth_factor > 0.0f) || !(depth_factor < 3.0e38f)) return PCR_ERR_ARG;
@@ -243,6 +247,7 @@ cudaError_t time_batch(const void* ws, int config, pcr_ctx* ctx, cudaEvent_t a, 
 
 namespace pcr {
 Device ctx_device(pcr_ctx* ctx) { return ctx->dev; }
+bool ctx_capturing(const pcr_ctx* ctx) { return ctx->capture != nullptr; }
 }  // namespace pcr
 
 extern "C" {
@@ -269,12 +274,58 @@ pcr_status pcr_create(pcr_ctx** out, int device) {
 }
 
 pcr_status pcr_destroy(pcr_ctx* ctx) {
+  if (ctx && ctx->capture) {  // an unfinished capture is dropped
+    cudaGraph_t graph = nullptr;
+    cudaStreamEndCapture(ctx->capture, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(ctx->capture);
+    cudaGetLastError();
+  }
   delete ctx;
   return PCR_OK;
 }
 
+pcr_status pcr_capture_begin(pcr_ctx* ctx) {
+  if (!ctx || ctx->capture) return PCR_ERR_ARG;
+  DeviceScope scope(ctx->dev.id);
+  if (!scope.ok()) return PCR_ERR_CUDA;
+  // occupancy queries (and the module loads they may cause) happen before
+  // recording starts
+  pcr::prewarm_single_view(ctx->dev);
+  if (pcr::batch_prewarm(ctx->dev) != cudaSuccess) return PCR_ERR_CUDA;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PCR_ERR_CUDA;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaStreamDestroy(cs);
+    return PCR_ERR_CUDA;
+  }
+  ctx->captured_stream = ctx->stream;
+  ctx->stream = ctx->capture = cs;
+  return PCR_OK;
+}
+
+pcr_status pcr_capture_end(pcr_ctx* ctx, void** graph_exec) {
+  if (!ctx || !graph_exec || !ctx->capture) return PCR_ERR_ARG;
+  *graph_exec = nullptr;
+  DeviceScope scope(ctx->dev.id);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->capture, &graph);
+  cudaStreamDestroy(ctx->capture);
+  ctx->stream = ctx->captured_stream;
+  ctx->capture = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || !scope.ok()) {
+    cudaGetLastError();
+    return PCR_ERR_CUDA;
+  }
+  *graph_exec = exec;
+  return PCR_OK;
+}
+
 pcr_status pcr_set_stream(pcr_ctx* ctx, void* cuda_stream) {
-  if (!ctx) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture) return PCR_ERR_ARG;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
   return PCR_OK;
 }
@@ -288,7 +339,7 @@ pcr_status pcr_upload_points(pcr_ctx* ctx, const void* dev_points, uint64_t n) {
 }
 
 pcr_status pcr_upload_points_from_host(pcr_ctx* ctx, void* dev_points, const void* host_points, uint64_t n) {
-  if (!ctx || n > kMaxPoints) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || n > kMaxPoints) return PCR_ERR_ARG;
   if (n > 0 && (!dev_points || !host_points || !aligned(dev_points, 16))) return PCR_ERR_ARG;
   if (n > 0) {
     DeviceScope scope(ctx->dev.id);
@@ -486,7 +537,7 @@ pcr_status pcr_resolve(pcr_ctx* ctx, int mode, void* dev_rgba_out, uint32_t back
 }
 
 pcr_status pcr_download(pcr_ctx* ctx, void* host_dst, const void* dev_src, uint64_t bytes) {
-  if (!ctx) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture) return PCR_ERR_ARG;
   if (bytes == 0) return PCR_OK;
   if (!host_dst || !dev_src) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
@@ -497,7 +548,7 @@ pcr_status pcr_download(pcr_ctx* ctx, void* host_dst, const void* dev_src, uint6
 }
 
 pcr_status pcr_synchronize(pcr_ctx* ctx) {
-  if (!ctx) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   return from_cuda(cudaStreamSynchronize(ctx->stream));
@@ -511,7 +562,8 @@ pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t* bytes) {
 
 pcr_status pcr_reorder_morton_shuffle128(pcr_ctx* ctx, void* dev_points, uint64_t n, uint64_t seed, int mode,
                                          void* dev_workspace, uint64_t workspace_bytes, uint32_t* dev_perm_out) {
-  if (!ctx || n > kMaxPoints || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_MORTON63_SHUFFLE128) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || n > kMaxPoints || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_MORTON63_SHUFFLE128)
+    return PCR_ERR_ARG;
   if (n == 0) return PCR_OK;
   if (!dev_points || !aligned(dev_points, 16) || (dev_perm_out && !aligned(dev_perm_out, 4))) return PCR_ERR_ARG;
   if (!dev_workspace || !aligned(dev_workspace, 256) || workspace_bytes < pcr::reorder_workspace_bytes(n))
@@ -524,7 +576,7 @@ pcr_status pcr_reorder_morton_shuffle128(pcr_ctx* ctx, void* dev_points, uint64_
 
 pcr_status pcr_reorder_morton_shuffle128_noalloc(pcr_ctx* ctx, void* dev_points, uint64_t n, uint64_t seed,
                                                  int mode, uint32_t* dev_perm_out) {
-  if (!ctx || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_MORTON63_SHUFFLE128) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || mode < PCR_ORDER_MORTON || mode > PCR_ORDER_MORTON63_SHUFFLE128) return PCR_ERR_ARG;
   if (n > PCR_REORDER_NOALLOC_MAX_POINTS) return PCR_ERR_WORKSPACE;
   if (n == 0) return PCR_OK;
   if (!dev_points || !aligned(dev_points, 16) || (dev_perm_out && !aligned(dev_perm_out, 4))) return PCR_ERR_ARG;
@@ -639,7 +691,7 @@ pcr_status pcr_batch_launch_count(pcr_ctx* ctx, const void* dev_workspace, int c
 }
 
 pcr_status pcr_batch_autotune(pcr_ctx* ctx, const void* dev_workspace, int* config) {
-  if (!ctx || !dev_workspace || !config || !aligned(dev_workspace, 256)) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || !dev_workspace || !config || !aligned(dev_workspace, 256)) return PCR_ERR_ARG;
   const void* plan = find_plan(ctx, dev_workspace);
   if (!plan) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
@@ -674,7 +726,7 @@ pcr_status pcr_batch_autotune(pcr_ctx* ctx, const void* dev_workspace, int* conf
 }
 
 pcr_status pcr_batch_capture(pcr_ctx* ctx, const void* dev_workspace, int config, void** graph_exec) {
-  if (!ctx || !dev_workspace || !graph_exec || !aligned(dev_workspace, 256) || config < 0 ||
+  if (!ctx || ctx->capture || !dev_workspace || !graph_exec || !aligned(dev_workspace, 256) || config < 0 ||
       config >= pcr::batch_num_configs())
     return PCR_ERR_ARG;
   *graph_exec = nullptr;
@@ -716,7 +768,8 @@ pcr_status pcr_graph_destroy(void* graph_exec) {
 
 pcr_status pcr_check_division(pcr_ctx* ctx, uint32_t w_first, uint32_t w_count, const uint32_t* dev_c_bits,
                               uint32_t c_first, uint32_t c_count, uint32_t c_step, float size, uint64_t out[5]) {
-  if (!ctx || !out || (c_count > 0 && !dev_c_bits && c_step == 0) || !(size > 0.0f && size <= 16384.0f))
+  if (!ctx || ctx->capture || !out || (c_count > 0 && !dev_c_bits && c_step == 0) ||
+      !(size > 0.0f && size <= 16384.0f))
     return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
@@ -738,7 +791,7 @@ const char* pcr_status_string(pcr_status status) {
 }
 
 pcr_status pcr_debug_counters(pcr_ctx* ctx, uint64_t out[4]) {
-  if (!ctx || !out) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || !out) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   bool available = false;
@@ -748,7 +801,7 @@ pcr_status pcr_debug_counters(pcr_ctx* ctx, uint64_t out[4]) {
 }
 
 pcr_status pcr_last_device_error(pcr_ctx* ctx, uint32_t* code) {
-  if (!ctx || !code) return PCR_ERR_ARG;
+  if (!ctx || ctx->capture || !code) return PCR_ERR_ARG;
   DeviceScope scope(ctx->dev.id);
   if (!scope.ok()) return PCR_ERR_CUDA;
   uint32_t batch = 0, reorder = 0;

@@ -631,11 +631,33 @@ cudaError_t launch_hq_color(int variant, const uint4* pts, uint32_t n, const Vie
   return cudaGetLastError();
 }
 
+template <int P>
+void prewarm_basic(const Device& d) {
+  geometry_grid<k_render_basic<PCR_VARIANT_ATOMICMIN, kUnroll, P>, kUnroll>(1, d);
+  geometry_grid<k_render_basic<PCR_VARIANT_EARLYZ, kUnroll, P>, kUnroll>(1, d);
+  geometry_grid<k_render_basic<PCR_VARIANT_DEDUP, kUnroll, P>, kUnroll>(1, d);
+  geometry_grid<k_render_basic<PCR_VARIANT_DEDUP_EARLYZ, kUnroll, P>, kUnroll>(1, d);
+  geometry_grid<k_render_basic<PCR_VARIANT_REDUCE, kUnroll, P>, kUnroll>(1, d);
+  geometry_grid<k_render_basic<PCR_VARIANT_REDUCE_EARLYZ, kUnroll, P>, kUnroll>(1, d);
+  geometry_grid<k_render_basic<PCR_VARIANT_JUST_SET, kUnroll, P>, kUnroll>(1, d);
+}
+
+// Every single-view geometry kernel's occupancy query (cached per kernel):
+// run once before a stream capture records launches.
 void prewarm_single_view(const Device& d) {
-  geometry_grid<k_render_basic<PCR_VARIANT_EARLYZ, kUnroll, kPayloadIndex>, kUnroll>(1, d);
+  prewarm_basic<kPayloadIndex>(d);
+  prewarm_basic<kPayloadRgb>(d);
+  geometry_grid<k_render_busy<kUnroll>, kUnroll>(1, d);
+  geometry_grid<k_hq_depth<PCR_VARIANT_ATOMICMIN, kUnroll>, kUnroll>(1, d);
+  geometry_grid<k_hq_depth<PCR_VARIANT_EARLYZ, kUnroll>, kUnroll>(1, d);
+  geometry_grid<k_hq_depth<PCR_VARIANT_DEDUP, kUnroll>, kUnroll>(1, d);
   geometry_grid<k_hq_depth<PCR_VARIANT_DEDUP_EARLYZ, kUnroll>, kUnroll>(1, d);
+  geometry_grid<k_hq_color<false, kUnroll, false>, kUnroll>(1, d);
   geometry_grid<k_hq_color<true, kUnroll, kCanPairLoad>, kUnroll>(1, d);
   geometry_grid<k_hq_color<true, kUnroll, false>, kUnroll>(1, d);
+  geometry_grid<k_hq1r_color<false, kUnroll, false>, kUnroll>(1, d);
+  geometry_grid<k_hq1r_color<true, kUnroll, kCanPairLoad>, kUnroll>(1, d);
+  geometry_grid<k_hq1r_color<true, kUnroll, false>, kUnroll>(1, d);
 }
 
 template <bool AGG, bool V8>

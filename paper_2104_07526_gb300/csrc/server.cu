@@ -117,6 +117,7 @@ struct Inflight {
 }  // namespace
 
 Device ctx_device(pcr_ctx* ctx);
+bool ctx_capturing(const pcr_ctx* ctx);
 
 }  // namespace pcr
 
@@ -400,7 +401,7 @@ void destroy(pcr_server* s) {
 extern "C" {
 
 pcr_status pcr_server_create(pcr_ctx* ctx, const pcr_server_config* cfg, pcr_server** out) {
-  if (!ctx || !cfg || !out) return PCR_ERR_ARG;
+  if (!ctx || !cfg || !out || pcr::ctx_capturing(ctx)) return PCR_ERR_ARG;
   *out = nullptr;
   if (!cfg->dev_arena || (reinterpret_cast<uintptr_t>(cfg->dev_arena) & (pcr::kAlign - 1))) return PCR_ERR_ARG;
   if (cfg->max_width < 1 || cfg->max_height < 1 || cfg->max_width > 16384 || cfg->max_height > 16384)

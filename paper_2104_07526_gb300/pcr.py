@@ -154,6 +154,8 @@ _SIGS = {
                        C.c_char_p, C.POINTER(PcrBatchTuning)],
     "pcr_batch_capture": [_VP, _VP, _INT, C.POINTER(_VP)],
     "pcr_batch_launch_count": [_VP, _VP, _INT, C.POINTER(_INT)],
+    "pcr_capture_begin": [_VP],
+    "pcr_capture_end": [_VP, C.POINTER(_VP)],
     "pcr_graph_launch": [_VP, _VP],
     "pcr_graph_destroy": [_VP],
     "pcr_server_create": [_VP, C.POINTER(PcrServerConfig), C.POINTER(_VP)],
@@ -426,6 +428,16 @@ def pcr_batch_launch_count(ctx: int, workspace, config: int) -> int:
 def pcr_batch_capture(ctx: int, workspace, config: int) -> int:
     out = _VP()
     _check(lib().pcr_batch_capture(ctx, _dptr(workspace, "workspace"), config, C.byref(out)), "pcr_batch_capture")
+    return out.value
+
+
+def pcr_capture_begin(ctx: int):
+    _check(lib().pcr_capture_begin(ctx), "pcr_capture_begin")
+
+
+def pcr_capture_end(ctx: int) -> int:
+    out = _VP()
+    _check(lib().pcr_capture_end(ctx, C.byref(out)), "pcr_capture_end")
     return out.value
 
 

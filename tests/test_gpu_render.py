@@ -15,6 +15,7 @@ from paper_2104_07526_gb300 import pcr, scenes
 pytestmark = pytest.mark.gpu
 
 EXACT = pcr.EXACT_VARIANTS
+BG = 0x20304050
 
 
 @pytest.fixture(scope="module")
@@ -410,3 +411,58 @@ def test_mapped_upload_refusals(r):
     assert lib.pcr_upload_points_mapped(r.h, None, 1) == pcr.PCR_ERR_ARG
     assert lib.pcr_upload_points_mapped(r.h, host.data_ptr(), 1024) == pcr.PCR_OK
     r.upload(np.zeros((0, 4), np.int32))
+
+
+def test_captured_frames_replay_exactly(oracle):
+    """pcr_capture_begin / _end record a frame (clear + render + resolve, and
+    an HQ frame) into a graph; each replay gives the oracle's buffers.  While
+    recording, calls that synchronise or copy from the host are refused and
+    nothing runs; an unfinished capture is dropped by pcr_destroy."""
+    from gpu_helpers import ensure_built
+    ensure_built()
+    cloud = scenes.sphere_plane(100_003, seed=13).numpy()
+    W, H = 320, 240
+    m = scenes.camera((0, 0, 4), (0, 0, 0), (0, 1, 0), W, H)
+    pts = torch.from_numpy(cloud.copy()).cuda()
+    fb = pcr.alloc_framebuffer(W, H)
+    hq_image = torch.empty(W * H, dtype=torch.int32, device="cuda")
+    expect = oracle.render_basic(cloud, m, W, H)
+    _, rg, ba = oracle.render_hq(cloud, m, W, H, 1.01)
+    with pcr.Context(0, stream=torch.cuda.current_stream()) as c:
+        h = c.handle
+        pcr.pcr_upload_points(h, pts, pts.shape[0])
+        pcr.pcr_set_matrix(h, m)
+        pcr.pcr_set_viewport(h, W, H)
+        pcr.pcr_set_framebuffer(h, fb["keys"], fb["hq_depth"], fb["hq_rg"], fb["hq_ba"])
+        with pytest.raises(pcr.PcrError):
+            pcr.pcr_capture_end(h)  # nothing open
+        pcr.pcr_capture_begin(h)
+        with pytest.raises(pcr.PcrError):
+            pcr.pcr_capture_begin(h)  # already open
+        for refused in (lambda: pcr.pcr_synchronize(h), lambda: pcr.pcr_last_device_error(h),
+                        lambda: pcr.pcr_set_stream(h, torch.cuda.current_stream())):
+            with pytest.raises(pcr.PcrError) as e:
+                refused()
+            assert e.value.status == pcr.PCR_ERR_ARG
+        pcr.pcr_clear(h, pcr.PCR_CLEAR_KEYS)
+        pcr.pcr_render_basic(h, pcr.PCR_VARIANT_DEDUP_EARLYZ, False)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_BASIC, fb["image"], BG)
+        pcr.pcr_render_hq(h, 1.01, pcr.PCR_VARIANT_DEDUP_EARLYZ, True)
+        pcr.pcr_resolve(h, pcr.PCR_RESOLVE_HQ, hq_image, BG)
+        g = pcr.pcr_capture_end(h)
+        try:
+            for rep in range(3):
+                for t in (fb["keys"], fb["image"], fb["hq_rg"], hq_image):
+                    t.fill_(0x5A5A5A5A)
+                pcr.pcr_graph_launch(h, g)
+                torch.cuda.synchronize()
+                assert np.array_equal(fb["keys"].cpu().numpy().view(np.uint64), expect), rep
+                assert np.array_equal(fb["image"].cpu().numpy().view(np.uint32),
+                                      oracle.resolve_basic(expect, cloud, BG)), rep
+                assert np.array_equal(fb["hq_rg"].cpu().numpy().view(np.uint64), rg), rep
+                assert np.array_equal(hq_image.cpu().numpy().view(np.uint32), oracle.resolve_hq(rg, ba, BG)), rep
+        finally:
+            pcr.pcr_graph_destroy(g)
+        assert pcr.pcr_last_device_error(h) == 0  # the context is usable again after the capture
+    with pcr.Context(0, stream=torch.cuda.current_stream()) as c2:
+        pcr.pcr_capture_begin(c2.handle)  # left open: pcr_destroy drops it
