@@ -62,6 +62,13 @@ constexpr int kScanItems = 16;
 constexpr uint32_t kScanSeg = kScanThreads * kScanItems;
 constexpr uint32_t kBatch = 128;  // Sec. 4: batches of 128 points
 
+// Keys per thread in flight in the write-out of a sort's last pass when it
+// gathers the point records by index.
+#ifndef PCR_GATHER_UNROLL
+#define PCR_GATHER_UNROLL 4
+#endif
+constexpr int kGatherUnroll = PCR_GATHER_UNROLL;
+
 static_assert(kRadix == kSortThreads, "one digit per thread in the sort kernels");
 
 constexpr uint64_t align_up(uint64_t v) { return (v + 255) & ~uint64_t(255); }
@@ -460,14 +467,31 @@ __device__ __forceinline__ void copy16_async(void* smem_dst, const void* gmem_sr
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(gmem_src), "r"(bytes) : "memory");
 }
 
-// `cin`/`cout` (may be null): a second 32-bit value carried with each key
-// (the high words of 63-bit codes while their low words are sorted).  `vout`
-// may be null when no value is carried; a null `vin` with a `vout` carries
-// each key's input index (the first pass of a sort whose values start as the
-// identity, so they are never written out and read back).  With REC, the 16-byte point
-// record `rin[i]` moves with its key to `rout` (the random order sorts the
-// records themselves: every pass reads them in tile order and writes them in
-// digit runs, instead of one random gather at the end).
+// The last pass of a sort may move the point records itself: the record at
+// each key's value (an index into `src`) goes straight to the key's final
+// position, so the permutation makes no round trip through memory and no
+// gather pass follows.  With `rank`, final positions are those of the
+// 128-point batch order (Sec. 4): sorted position g lies in batch g / 128,
+// which goes to batch slot rank[g / 128], and slots after the short last
+// batch start (128 - its size) earlier.
+struct FinalGather {
+  const uint4* src = nullptr;      // records by input index; null: no gather
+  uint4* dst = nullptr;            // records by final position
+  uint32_t* perm_out = nullptr;    // optional: final position -> input index
+  const uint32_t* rank = nullptr;  // optional: batch -> its slot in the batch order
+  uint32_t nb = 0;                 // batches (with rank)
+};
+
+// `kout` may be null: the last pass of a sort writes no keys (nothing reads
+// them).  `cin`/`cout` (may be null): a second 32-bit value carried with each
+// key (the high words of 63-bit codes while their low words are sorted).
+// `vout` may be null when no value is carried; a null `vin` with a `vout`
+// carries each key's input index (the first pass of a sort whose values start
+// as the identity, so they are never written out and read back).  With REC,
+// the 16-byte point record `rin[i]` moves with its key to `rout` (the random
+// order sorts the records themselves: every pass reads them in tile order and
+// writes them in digit runs, instead of one random gather at the end).  With
+// `fin.src` the records move as FinalGather says, and `vout` is not written.
 template <bool REC>
 __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
@@ -477,7 +501,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
                                                                   uint32_t tiles, const uint32_t* __restrict__ cin,
                                                                   uint32_t* __restrict__ cout,
                                                                   const uint4* __restrict__ rin,
-                                                                  uint4* __restrict__ rout) {
+                                                                  uint4* __restrict__ rout, FinalGather fin) {
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
   uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
@@ -553,26 +577,50 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   // output positions; values are gathered from the tile's 24 KB window.  One
   // loop per combination of what moves with the keys, chosen once, so each
   // unrolled loop carries no per-key test.
-  auto write_out = [&](auto values, auto carried) {
+  auto write_out = [&](auto values, auto carried, auto keys, auto gather, auto perm) {
     constexpr int kValues = decltype(values)::value;  // 0 none, 1 loaded, 2 the key's index
     constexpr bool kCarried = decltype(carried)::value;
+    constexpr bool kKeys = decltype(keys)::value;
+    constexpr int kGather = decltype(gather)::value;  // 0 none, 1 to sorted position, 2 to batch order
+    constexpr bool kPerm = decltype(perm)::value;
+    uint32_t t_last = 0, short_by = 0;
+    if constexpr (kGather == 2) {
+      t_last = __ldg(fin.rank + (fin.nb - 1));
+      short_by = fin.nb * kBatch - n;
+    }
     auto one = [&](uint32_t l) {
       const uint32_t src = s_src[l];
       const uint32_t key = s_kin[src];
       const uint32_t d = (key >> shift) & (kRadix - 1);
       const uint32_t g = delta[d] + l;
       if (!debug_in_range(g, n)) return;
-      kout[g] = key;
-      if constexpr (kValues == 1) vout[g] = __ldg(vin + tile_base + src);
-      if constexpr (kValues == 2) vout[g] = static_cast<uint32_t>(tile_base + src);
+      if constexpr (kKeys) kout[g] = key;
+      uint32_t v = 0;
+      if constexpr (kValues == 1) v = __ldg(vin + tile_base + src);
+      if constexpr (kValues == 2) v = static_cast<uint32_t>(tile_base + src);
+      if constexpr (kGather == 0) {
+        if constexpr (kValues != 0) vout[g] = v;
+      } else {
+        uint32_t at = g;
+        if constexpr (kGather == 2) {
+          const uint32_t slot = __ldg(fin.rank + g / kBatch);
+          at = slot * kBatch + g % kBatch - (slot > t_last ? short_by : 0u);
+        }
+        if (!debug_in_range(v, n) || !debug_in_range(at, n)) return;
+        __stcs(fin.dst + at, __ldg(fin.src + v));
+        if constexpr (kPerm) fin.perm_out[at] = v;
+      }
       if constexpr (kCarried) cout[g] = __ldg(cin + tile_base + src);
       if constexpr (REC) __stcs(rout + g, __ldg(rin + tile_base + src));
     };
-    // records: one key per iteration (unrolled 2, 3, 4 or 8 times the 800M
-    // shuffle took 36.2, 35.9, 38.1 and 39.2 ms against 35.4); keys and 4-byte
-    // values: eight
+    // records carried: one key per iteration (unrolled 2, 3, 4 or 8 times the
+    // 800M shuffle took 36.2, 35.9, 38.1 and 39.2 ms against 35.4); records
+    // gathered by index: kGatherUnroll; keys and 4-byte values: eight
     if constexpr (REC) {
 #pragma unroll 1
+      for (uint32_t l = t; l < total; l += kSortThreads) one(l);
+    } else if constexpr (kGather != 0) {
+#pragma unroll kGatherUnroll
       for (uint32_t l = t; l < total; l += kSortThreads) one(l);
     } else {
 #pragma unroll 8
@@ -584,16 +632,39 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   using C2 = std::integral_constant<int, 2>;
   using Yes = std::true_type;
   using No = std::false_type;
-  if (!vout) {
-    if (cout) write_out(C0{}, Yes{});
-    else write_out(C0{}, No{});
-  } else if (vin) {
-    if (cout) write_out(C1{}, Yes{});
-    else write_out(C1{}, No{});
-  } else {
-    if (cout) write_out(C2{}, Yes{});
-    else write_out(C2{}, No{});
+  if constexpr (!REC) {
+    if (fin.src) {
+      auto go = [&](auto values) {
+        if (fin.rank) {
+          if (fin.perm_out) write_out(values, No{}, No{}, C2{}, Yes{});
+          else write_out(values, No{}, No{}, C2{}, No{});
+        } else {
+          if (fin.perm_out) write_out(values, No{}, No{}, C1{}, Yes{});
+          else write_out(values, No{}, No{}, C1{}, No{});
+        }
+      };
+      if (vin) go(C1{});
+      else go(C2{});
+      return;
+    }
   }
+  auto go = [&](auto values) {
+    if constexpr (REC) {
+      if (kout) write_out(values, No{}, Yes{}, C0{}, No{});
+      else write_out(values, No{}, No{}, C0{}, No{});
+    } else {
+      if (kout) {
+        if (cout) write_out(values, Yes{}, Yes{}, C0{}, No{});
+        else write_out(values, No{}, Yes{}, C0{}, No{});
+      } else {
+        if (cout) write_out(values, Yes{}, No{}, C0{}, No{});
+        else write_out(values, No{}, No{}, C0{}, No{});
+      }
+    }
+  };
+  if (!vout) go(C0{});
+  else if (vin) go(C1{});
+  else go(C2{});
 }
 
 // --- exclusive scan (in place) ----------------------------------------------------
@@ -705,16 +776,20 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 }
 
 // Stable sort of count (key, value) pairs on the low key_bits bits.  The
-// result ends in buffer index `out` (0 or 1).  With `carry` (may be null),
-// a second value per key moves with it through its own two buffers; with
-// `recs` (may be null), a 16-byte record does.  vals may hold null buffers
-// when no value is needed.  With `index_values` the values start as each
-// key's index: the first pass makes them, and vals[0] is never read.  With
-// `first_counted` the kernel that made the keys has already written the
-// first pass's digit counts (k_morton, k_morton63, k_random_keys).
+// result ends in buffer index `out` (0 or 1): the values, and the carried
+// words; the last pass writes no keys.  With `carry` (may be null), a second
+// value per key moves with it through its own two buffers; with `recs` (may
+// be null), a 16-byte record does.  vals may hold null buffers when no value
+// is needed.  With `index_values` the values start as each key's index: the
+// first pass makes them, and vals[0] is never read.  With `first_counted` the
+// kernel that made the keys has already written the first pass's digit
+// counts (k_morton, k_morton63, k_random_keys).  With `fin` (may be null) the
+// last pass moves the records as FinalGather says, instead of writing the
+// values.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
                        uint32_t* partials, cudaStream_t s, int& out, bool index_values, bool first_counted,
-                       uint32_t* const* carry = nullptr, uint4* const* recs = nullptr) {
+                       uint32_t* const* carry = nullptr, uint4* const* recs = nullptr,
+                       const FinalGather* fin = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
@@ -722,18 +797,21 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kScatterSmem));
   if (e != cudaSuccess) return e;
   for (int shift = 0; shift < key_bits; shift += kDigitBits) {
+    const bool last = shift + kDigitBits >= key_bits;
     if (!(first_counted && shift == 0)) k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
     e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
     const uint32_t* vin = (index_values && shift == 0) ? nullptr : vals[out];
+    uint32_t* kout = last ? nullptr : keys[out ^ 1];
+    const FinalGather f = (last && fin) ? *fin : FinalGather{};
     if (recs)
       k_sort_scatter<true><<<tiles, kSortThreads, kScatterSmem, s>>>(
-          keys[out], vin, keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, nullptr, nullptr, recs[out],
-          recs[out ^ 1]);
+          keys[out], vin, kout, vals[out ^ 1], count, shift, counts, tiles, nullptr, nullptr, recs[out],
+          recs[out ^ 1], f);
     else
       k_sort_scatter<false><<<tiles, kSortThreads, kScatterSmem, s>>>(
-          keys[out], vin, keys[out ^ 1], vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
-          carry ? carry[out ^ 1] : nullptr, nullptr, nullptr);
+          keys[out], vin, kout, vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
+          carry ? carry[out ^ 1] : nullptr, nullptr, nullptr, f);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     out ^= 1;
@@ -747,6 +825,14 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
 __global__ void k_find_last_batch(const uint32_t* __restrict__ order, uint32_t nb, uint32_t* misc) {
   for (uint64_t t = blockIdx.x * 256ull + threadIdx.x; t < nb; t += gridDim.x * 256ull)
     if (order[t] == nb - 1) misc[6] = static_cast<uint32_t>(t);
+}
+
+// Slot of each batch in the sorted batch order: rank[order[t]] = t.
+__global__ void k_batch_rank(const uint32_t* __restrict__ order, uint32_t nb, uint32_t* __restrict__ rank) {
+  for (uint64_t t = blockIdx.x * 256ull + threadIdx.x; t < nb; t += gridDim.x * 256ull) {
+    const uint32_t b = order[t];
+    if (debug_in_range(b, nb)) rank[b] = static_cast<uint32_t>(t);
+  }
 }
 
 // The shuffled Morton order, gathered: output batch slot t holds batch
@@ -869,10 +955,32 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
     return e;
   } else if (!wide) {
+    // the sort's last pass moves the records from their copy to their final
+    // positions: the sorted positions, or with the batch shuffle, the slots
+    // of the batches' random order, which is sorted first
+    FinalGather fin;
+    fin.src = copy;
+    fin.dst = pts;
+    fin.perm_out = perm_out;
+    if (mode == PCR_ORDER_MORTON_SHUFFLE128) {
+      const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
+      uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
+      uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
+      const uint32_t btiles = static_cast<uint32_t>(ceil_div(nb, kTile));
+      k_random_keys<<<btiles, kSortThreads, 0, s>>>(nb, seed, bkeys[0], counts, btiles);
+      int bout = 0;
+      e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
+      if (e != cudaSuccess) return e;
+      k_batch_rank<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, bkeys[0]);
+      fin.rank = bkeys[0];
+      fin.nb = nb;
+    }
     k_bounds_init<<<1, 32, 0, s>>>(misc);
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
     k_morton<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], counts, tiles);
-    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true, true);
+    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true, true, nullptr, nullptr, &fin);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
   } else {
     // 63-bit code: the high halves ride along with their keys while the low
     // halves are sorted, in two buffers in the record-copy region (not
@@ -893,8 +1001,10 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     out = a ^ b;
   }
   if (e != cudaSuccess) return e;
+  // 63-bit codes: their high halves hold the record-copy region until the
+  // sort ends, so the records are copied and gathered after it
   uint32_t* perm = vals[out];
-  if (mode == PCR_ORDER_MORTON_SHUFFLE128 || mode == PCR_ORDER_MORTON63_SHUFFLE128) {
+  if (mode == PCR_ORDER_MORTON63_SHUFFLE128) {
     const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
@@ -904,12 +1014,12 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
     if (e != cudaSuccess) return e;
     k_find_last_batch<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, misc);
-    if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
+    k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
     k_gather_batches<<<stream_grid(static_cast<uint64_t>(nb) * kBatch, d), 256, 0, s>>>(copy, bvals[bout], perm, n, nb,
                                                                                      misc, pts, perm_out);
     return cudaGetLastError();
   }
-  if (wide) k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
+  k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
   k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
   return cudaGetLastError();
 }
