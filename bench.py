@@ -343,17 +343,19 @@ REORDER_ALGORITHMIC_BYTES_PER_POINT = {
 #   + 8 written (key, index), less the 4 + 4 the first pass does not read (the
 #   kernel that made the keys counted its digits, and it makes the indices),
 #   and 4 + 4 more for the high word the 63-bit orders carry through their
-#   first four passes; batch sort and permutation about 1; separate record
-#   copy (63-bit orders) 16 + 16; record gather 4 (index) + 16 read + 16
-#   written.  The shuffle writes its 4-byte random keys, then each of its
-#   four passes reads 4 (histogram; not the first) and moves the key and the
-#   16-byte record it carries (20 read, 20 written).
+#   first sort (whose last pass writes no keys).  The last pass of the sort
+#   that orders the records writes no key and no index: it moves each record
+#   from the copy to its final position (16 read, 16 written).  Batch sort and
+#   batch slots about 1; separate record copy (63-bit orders) 16 + 16.  The
+#   shuffle writes its 4-byte random keys, then each of its four passes reads
+#   4 (histogram; not the first) and moves the key and the 16-byte record it
+#   carries (20 read, 20 written; the last writes no key).
 REORDER_BYTES_PER_POINT = {
-    "morton": 32 + 20 + 4 * 20 - 8 + 36,
-    "morton_shuffle128": 32 + 20 + 4 * 20 - 8 + 1 + 36,
-    "shuffle": 4 + 4 * (4 + 40) - 4,
-    "morton63": 16 + 24 + 4 * 28 - 8 + 4 * 20 + 32 + 36,
-    "morton63_shuffle128": 16 + 24 + 4 * 28 - 8 + 4 * 20 + 1 + 32 + 36,
+    "morton": 32 + 20 + 4 * 20 - 8 - 8 + 32,
+    "morton_shuffle128": 32 + 20 + 4 * 20 - 8 - 8 + 32 + 1,
+    "shuffle": 4 + 4 * (4 + 40) - 4 - 4,
+    "morton63": 16 + 24 + 4 * 28 - 8 - 4 + 32 + 4 * 20 - 8 + 32,
+    "morton63_shuffle128": 16 + 24 + 4 * 28 - 8 - 4 + 32 + 4 * 20 - 8 + 32 + 1,
 }
 
 

@@ -1,7 +1,7 @@
 // Vertex-order kernels (Sec. 4, and the orderings listed in Sec. 5):
 // bounds, 30-bit and 63-bit Morton codes, a stable LSD radix sort of (32-bit
-// key, 32-bit index) pairs, the 128-point batch shuffle and the record
-// gather.  A 63-bit code sorts as two 32-bit halves: the low half first
+// key, 32-bit index) pairs whose last pass moves the point records to their
+// final positions, and the 128-point batch shuffle.  A 63-bit code sorts as two 32-bit halves: the low half first
 // (the high half carried along), then the high half, both stable, which is a
 // stable sort by the whole code.
 //
@@ -65,7 +65,7 @@ constexpr uint32_t kBatch = 128;  // Sec. 4: batches of 128 points
 // Keys per thread in flight in the write-out of a sort's last pass when it
 // gathers the point records by index.
 #ifndef PCR_GATHER_UNROLL
-#define PCR_GATHER_UNROLL 4
+#define PCR_GATHER_UNROLL 8
 #endif
 constexpr int kGatherUnroll = PCR_GATHER_UNROLL;
 
@@ -778,18 +778,19 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 // Stable sort of count (key, value) pairs on the low key_bits bits.  The
 // result ends in buffer index `out` (0 or 1): the values, and the carried
 // words; the last pass writes no keys.  With `carry` (may be null), a second
-// value per key moves with it through its own two buffers; with `recs` (may
-// be null), a 16-byte record does.  vals may hold null buffers when no value
-// is needed.  With `index_values` the values start as each key's index: the
-// first pass makes them, and vals[0] is never read.  With `first_counted` the
-// kernel that made the keys has already written the first pass's digit
-// counts (k_morton, k_morton63, k_random_keys).  With `fin` (may be null) the
-// last pass moves the records as FinalGather says, instead of writing the
-// values.
+// value per key moves with it through its own two buffers, and with
+// `carry_last` (may be null) the last pass writes the carried words there
+// instead.  With `recs` (may be null), a 16-byte record moves with each key.
+// vals may hold null buffers when no value is needed.  With `index_values`
+// the values start as each key's index: the first pass makes them, and
+// vals[0] is never read.  With `first_counted` the kernel that made the keys
+// has already written the first pass's digit counts (k_morton, k_morton63,
+// k_random_keys).  With `fin` (may be null) the last pass moves the records
+// as FinalGather says, instead of writing the values.
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
                        uint32_t* partials, cudaStream_t s, int& out, bool index_values, bool first_counted,
-                       uint32_t* const* carry = nullptr, uint4* const* recs = nullptr,
-                       const FinalGather* fin = nullptr) {
+                       uint32_t* const* carry = nullptr, uint32_t* carry_last = nullptr,
+                       uint4* const* recs = nullptr, const FinalGather* fin = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
@@ -811,7 +812,7 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
     else
       k_sort_scatter<false><<<tiles, kSortThreads, kScatterSmem, s>>>(
           keys[out], vin, kout, vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
-          carry ? carry[out ^ 1] : nullptr, nullptr, nullptr, f);
+          carry ? (last && carry_last ? carry_last : carry[out ^ 1]) : nullptr, nullptr, nullptr, f);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     out ^= 1;
@@ -819,13 +820,7 @@ cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int
   return cudaSuccess;
 }
 
-// --- shuffled Morton: batches -> permutation -------------------------------------
-
-// Position, in the sorted batch order, of the last (possibly short) batch.
-__global__ void k_find_last_batch(const uint32_t* __restrict__ order, uint32_t nb, uint32_t* misc) {
-  for (uint64_t t = blockIdx.x * 256ull + threadIdx.x; t < nb; t += gridDim.x * 256ull)
-    if (order[t] == nb - 1) misc[6] = static_cast<uint32_t>(t);
-}
+// --- shuffled Morton: batch slots; record copy -------------------------------------
 
 // Slot of each batch in the sorted batch order: rank[order[t]] = t.
 __global__ void k_batch_rank(const uint32_t* __restrict__ order, uint32_t nb, uint32_t* __restrict__ rank) {
@@ -835,47 +830,8 @@ __global__ void k_batch_rank(const uint32_t* __restrict__ order, uint32_t nb, ui
   }
 }
 
-// The shuffled Morton order, gathered: output batch slot t holds batch
-// order[t] of the Morton order; slots after the short last batch start
-// (kBatch - last_size) earlier.  Each record moves straight from its Morton
-// position (perm[new] = old is formed on the fly, and written out only when
-// asked for), so no permutation array makes a round trip through memory.
-__global__ void __launch_bounds__(256) k_gather_batches(const uint4* __restrict__ src,
-                                                        const uint32_t* __restrict__ order,
-                                                        const uint32_t* __restrict__ morton, uint32_t n, uint32_t nb,
-                                                        const uint32_t* __restrict__ misc, uint4* __restrict__ dst,
-                                                        uint32_t* __restrict__ perm_out) {
-  const uint32_t t_last = misc[6];
-  const uint32_t last_size = n - (nb - 1) * kBatch;
-  const uint64_t total = static_cast<uint64_t>(nb) * kBatch;
-  for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < total; j += gridDim.x * 256ull) {
-    const uint32_t t = static_cast<uint32_t>(j / kBatch);
-    const uint32_t k = static_cast<uint32_t>(j % kBatch);
-    const uint32_t b = order[t];
-    const uint32_t size = (b == nb - 1) ? last_size : kBatch;
-    if (k < size) {
-      const uint64_t at = static_cast<uint64_t>(t) * kBatch - (t > t_last ? (kBatch - last_size) : 0u) + k;
-      const uint32_t p = morton[static_cast<uint64_t>(b) * kBatch + k];
-      if (!debug_in_range(p, n) || !debug_in_range(at, n)) continue;
-      dst[at] = src[p];
-      if (perm_out) perm_out[at] = p;
-    }
-  }
-}
-
 __global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, uint32_t n) {
   for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += gridDim.x * 256ull) dst[i] = __ldcs(src + i);
-}
-
-__global__ void __launch_bounds__(256) k_gather16(const uint4* __restrict__ src, const uint32_t* __restrict__ perm,
-                                                  uint4* __restrict__ dst, uint32_t* __restrict__ perm_out,
-                                                  uint32_t n) {
-  for (uint64_t j = blockIdx.x * 256ull + threadIdx.x; j < n; j += gridDim.x * 256ull) {
-    const uint32_t p = perm[j];
-    if (!debug_in_range(p, n)) continue;
-    dst[j] = src[p];
-    if (perm_out) perm_out[j] = p;
-  }
 }
 
 unsigned stream_grid(uint64_t count, const Device& d) {
@@ -939,9 +895,6 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   const uint32_t tiles = static_cast<uint32_t>(ceil_div(n, kTile));  // the sort's tiles
   cudaError_t e = cudaSuccess;
   int out = 0;
-  // the record copy the final gather reads is made by the first pass over
-  // the records, except for the 63-bit code, whose sort uses its region
-  const bool wide = mode == PCR_ORDER_MORTON63 || mode == PCR_ORDER_MORTON63_SHUFFLE128;
   if (mode == PCR_ORDER_SHUFFLE) {
     // the records themselves are sorted by their random keys (4 passes, an
     // even number: they end back in the caller's buffer); indices ride along
@@ -949,62 +902,20 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     k_random_keys<<<tiles, kSortThreads, 0, s>>>(n, seed, keys[0], counts, tiles);
     uint32_t* ivals[2] = {perm_out ? vals[0] : nullptr, perm_out ? vals[1] : nullptr};
     uint4* recs[2] = {pts, copy};
-    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, true, true, nullptr, recs);
+    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, true, true, nullptr, nullptr, recs);
     if (e != cudaSuccess) return e;
     if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes
     if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
     return e;
-  } else if (!wide) {
-    // the sort's last pass moves the records from their copy to their final
-    // positions: the sorted positions, or with the batch shuffle, the slots
-    // of the batches' random order, which is sorted first
-    FinalGather fin;
-    fin.src = copy;
-    fin.dst = pts;
-    fin.perm_out = perm_out;
-    if (mode == PCR_ORDER_MORTON_SHUFFLE128) {
-      const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
-      uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
-      uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
-      const uint32_t btiles = static_cast<uint32_t>(ceil_div(nb, kTile));
-      k_random_keys<<<btiles, kSortThreads, 0, s>>>(nb, seed, bkeys[0], counts, btiles);
-      int bout = 0;
-      e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
-      if (e != cudaSuccess) return e;
-      k_batch_rank<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, bkeys[0]);
-      fin.rank = bkeys[0];
-      fin.nb = nb;
-    }
-    k_bounds_init<<<1, 32, 0, s>>>(misc);
-    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
-    k_morton<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], counts, tiles);
-    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true, true, nullptr, nullptr, &fin);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-  } else {
-    // 63-bit code: the high halves ride along with their keys while the low
-    // halves are sorted, in two buffers in the record-copy region (not
-    // needed until the final gather); then they are the keys.
-    uint32_t* hi[2] = {reinterpret_cast<uint32_t*>(ws + l.pts_copy),
-                       reinterpret_cast<uint32_t*>(ws + l.pts_copy) + align_up(4ull * n) / 4};
-    k_bounds_init<<<1, 32, 0, s>>>(misc);
-    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
-    k_morton63<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], hi[0], counts, tiles);
-    int a = 0;
-    e = radix_sort(keys, vals, n, 32, counts, partials, s, a, true, true, hi);
-    if (e != cudaSuccess) return e;
-    uint32_t* hkeys[2] = {hi[a], hi[a ^ 1]};
-    uint32_t* hvals[2] = {vals[a], vals[a ^ 1]};
-    int b = 0;
-    e = radix_sort(hkeys, hvals, n, 31, counts, partials, s, b, false, false);
-    // the sorted values end in vals[a ^ b]
-    out = a ^ b;
   }
-  if (e != cudaSuccess) return e;
-  // 63-bit codes: their high halves hold the record-copy region until the
-  // sort ends, so the records are copied and gathered after it
-  uint32_t* perm = vals[out];
-  if (mode == PCR_ORDER_MORTON63_SHUFFLE128) {
+  // The sort's last pass moves the records from their copy to their final
+  // positions: the sorted positions, or with the batch shuffle, the slots of
+  // the batches' random order, which is sorted first.
+  FinalGather fin;
+  fin.src = copy;
+  fin.dst = pts;
+  fin.perm_out = perm_out;
+  if (mode == PCR_ORDER_MORTON_SHUFFLE128 || mode == PCR_ORDER_MORTON63_SHUFFLE128) {
     const uint32_t nb = static_cast<uint32_t>(ceil_div(n, kBatch));
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
@@ -1013,14 +924,34 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     int bout = 0;
     e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
     if (e != cudaSuccess) return e;
-    k_find_last_batch<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, misc);
-    k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
-    k_gather_batches<<<stream_grid(static_cast<uint64_t>(nb) * kBatch, d), 256, 0, s>>>(copy, bvals[bout], perm, n, nb,
-                                                                                     misc, pts, perm_out);
+    k_batch_rank<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, bkeys[0]);
+    fin.rank = bkeys[0];
+    fin.nb = nb;
+  }
+  k_bounds_init<<<1, 32, 0, s>>>(misc);
+  if (mode == PCR_ORDER_MORTON || mode == PCR_ORDER_MORTON_SHUFFLE128) {
+    k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
+    k_morton<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], counts, tiles);
+    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true, true, nullptr, nullptr, nullptr, &fin);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
+  // 63-bit code: the high halves ride along with their keys while the low
+  // halves are sorted, in two buffers in the record-copy region; the last
+  // pass leaves them in keys[0] (the low halves are no longer needed), which
+  // frees the region for the record copy.  Then the high halves are sorted,
+  // and that sort's last pass moves the records.
+  uint32_t* hi[2] = {reinterpret_cast<uint32_t*>(ws + l.pts_copy),
+                     reinterpret_cast<uint32_t*>(ws + l.pts_copy) + align_up(4ull * n) / 4};
+  k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
+  k_morton63<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], hi[0], counts, tiles);
+  int a = 0;
+  e = radix_sort(keys, vals, n, 32, counts, partials, s, a, true, true, hi, keys[0]);
+  if (e != cudaSuccess) return e;
+  if (a != 0) return cudaErrorUnknown;  // 4 passes: the values are in vals[0]
   k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
-  k_gather16<<<grid, 256, 0, s>>>(copy, perm, pts, perm_out, n);
+  e = radix_sort(keys, vals, n, 31, counts, partials, s, out, false, false, nullptr, nullptr, nullptr, &fin);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
