@@ -131,7 +131,8 @@ constexpr int kStreamUnroll = 4;
 
 // Per axis min and max over non-NaN coordinates.  -0 is folded into +0 (the
 // codes do not depend on the sign of a zero bound).  With `copy`, the records
-// are also copied there (the source of the final gather), saving a pass.
+// are also copied there (the source the sort's last pass moves them from),
+// saving a pass.
 __global__ void __launch_bounds__(256) k_bounds(const uint4* __restrict__ pts, uint32_t n, uint32_t* misc,
                                                 uint4* __restrict__ copy) {
   uint32_t lo[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
