@@ -736,35 +736,50 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* __restrict__ p
   }
 }
 
+// Thread t scans the 16 consecutive counts [16 t, 16 t + 16) of its block's
+// segment, read and written as four 16-byte vectors (segments start on
+// 16-KB boundaries of the count array), so no shared-memory staging is
+// needed.
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ a, uint64_t len,
                                                             const uint32_t* __restrict__ partials) {
-  __shared__ uint32_t seg[kScanSeg];
-  const uint64_t base = static_cast<uint64_t>(blockIdx.x) * kScanSeg;
-#pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads + threadIdx.x;
-    seg[j * kScanThreads + threadIdx.x] = i < len ? a[i] : 0u;
-  }
-  __syncthreads();
+  static_assert(kScanItems == 16, "four 16-byte vectors per thread");
+  const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kScanSeg + static_cast<uint64_t>(threadIdx.x) * kScanItems;
   uint32_t mine[kScanItems];
+  const bool whole = first + kScanItems <= len;
+  if (whole) {
+    const uint4* q = reinterpret_cast<const uint4*>(a + first);
+#pragma unroll
+    for (int k = 0; k < kScanItems / 4; ++k) {
+      const uint4 v = q[k];
+      mine[4 * k] = v.x;
+      mine[4 * k + 1] = v.y;
+      mine[4 * k + 2] = v.z;
+      mine[4 * k + 3] = v.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j) mine[j] = first + j < len ? a[first + j] : 0u;
+  }
   uint32_t sum = 0;
 #pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    mine[j] = seg[threadIdx.x * kScanItems + j];
-    sum += mine[j];
-  }
+  for (int j = 0; j < kScanItems; ++j) sum += mine[j];
   uint32_t total;
   uint32_t run = block_exclusive_scan<kScanThreads>(sum, total) + partials[blockIdx.x];
 #pragma unroll
   for (int j = 0; j < kScanItems; ++j) {
-    seg[threadIdx.x * kScanItems + j] = run;
-    run += mine[j];
+    const uint32_t v = mine[j];
+    mine[j] = run;
+    run += v;
   }
-  __syncthreads();
+  if (whole) {
+    uint4* q = reinterpret_cast<uint4*>(a + first);
 #pragma unroll
-  for (int j = 0; j < kScanItems; ++j) {
-    const uint64_t i = base + static_cast<uint64_t>(j) * kScanThreads + threadIdx.x;
-    if (i < len) a[i] = seg[j * kScanThreads + threadIdx.x];
+    for (int k = 0; k < kScanItems / 4; ++k)
+      q[k] = make_uint4(mine[4 * k], mine[4 * k + 1], mine[4 * k + 2], mine[4 * k + 3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+      if (first + j < len) a[first + j] = mine[j];
   }
 }
 
