@@ -69,6 +69,11 @@ constexpr uint32_t kBatch = 128;  // Sec. 4: batches of 128 points
 #endif
 constexpr int kGatherUnroll = PCR_GATHER_UNROLL;
 
+// Full tiles take ranking and placement loops without the in-cloud tests.
+#ifndef PCR_FULL_TILES
+#define PCR_FULL_TILES 1
+#endif
+
 static_assert(kRadix == kSortThreads, "one digit per thread in the sort kernels");
 
 constexpr uint64_t align_up(uint64_t v) { return (v + 255) & ~uint64_t(255); }
@@ -531,17 +536,28 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   uint32_t* mine = wbase + warp * kRadix;
   const uint32_t below = (1u << lane) - 1u;
   uint32_t info[kSortRounds];
+  // a full tile (every tile but a cloud's last) needs no test of which keys
+  // lie inside the cloud
+  auto rank_keys = [&](auto full) {
+    constexpr bool kFull = decltype(full)::value;
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const uint32_t j = wfirst + r * 32 + lane;
-    const bool ok = j < valid;
-    const uint32_t d = ok ? (s_kin[j] >> shift) & (kRadix - 1) : 0u;
-    const uint32_t peers = digit_peers(d, __ballot_sync(kFullMask, ok));
-    const uint32_t rank = __popc(peers & below);
-    info[r] = ok ? (rank | (static_cast<uint32_t>(__popc(peers)) << 8) | (d << 16) | 0x80000000u) : 0u;
-    if (ok && rank == 0) mine[d] += __popc(peers);
-    __syncwarp();
-  }
+    for (int r = 0; r < kSortRounds; ++r) {
+      const uint32_t j = wfirst + r * 32 + lane;
+      const bool ok = kFull || j < valid;
+      const uint32_t d = ok ? (s_kin[j] >> shift) & (kRadix - 1) : 0u;
+      const uint32_t peers = digit_peers(d, kFull ? kFullMask : __ballot_sync(kFullMask, ok));
+      const uint32_t rank = __popc(peers & below);
+      info[r] = ok ? (rank | (static_cast<uint32_t>(__popc(peers)) << 8) | (d << 16) | 0x80000000u) : 0u;
+      if (ok && rank == 0) mine[d] += __popc(peers);
+      __syncwarp();
+    }
+  };
+#if PCR_FULL_TILES
+  if (valid == kTile) rank_keys(std::true_type{});
+  else rank_keys(std::false_type{});
+#else
+  rank_keys(std::false_type{});
+#endif
   __syncthreads();
   // digit t: first slot of each warp's keys within the digit, then the
   // digit's first slot within the tile
@@ -559,20 +575,29 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   for (int w = 0; w < kSortWarps; ++w) wbase[w * kRadix + t] += start;
   __syncthreads();
   // pass 2: each key's slot in the tile's digit order, in index order
+  auto place_keys = [&](auto full) {
+    constexpr bool kFull = decltype(full)::value;
 #pragma unroll
-  for (int r = 0; r < kSortRounds; ++r) {
-    const uint32_t v = info[r];
-    const bool ok = (v >> 31) != 0u;
-    const uint32_t d = (v >> 16) & (kRadix - 1);
-    const uint32_t rank = v & 0xFFu;
-    const uint32_t at = ok ? mine[d] : 0u;
-    __syncwarp();
-    if (ok && debug_in_range(at + rank, kTile)) {
-      s_src[at + rank] = static_cast<uint16_t>(wfirst + r * 32 + lane);
-      if (rank == 0) mine[d] = at + ((v >> 8) & 0xFFu);
+    for (int r = 0; r < kSortRounds; ++r) {
+      const uint32_t v = info[r];
+      const bool ok = kFull || (v >> 31) != 0u;
+      const uint32_t d = (v >> 16) & (kRadix - 1);
+      const uint32_t rank = v & 0xFFu;
+      const uint32_t at = ok ? mine[d] : 0u;
+      __syncwarp();
+      if (ok && debug_in_range(at + rank, kTile)) {
+        s_src[at + rank] = static_cast<uint16_t>(wfirst + r * 32 + lane);
+        if (rank == 0) mine[d] = at + ((v >> 8) & 0xFFu);
+      }
+      __syncwarp();
     }
-    __syncwarp();
-  }
+  };
+#if PCR_FULL_TILES
+  if (valid == kTile) place_keys(std::true_type{});
+  else place_keys(std::false_type{});
+#else
+  place_keys(std::false_type{});
+#endif
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
   // output positions; values are gathered from the tile's 24 KB window.  One
