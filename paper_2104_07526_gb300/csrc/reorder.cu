@@ -133,6 +133,11 @@ __global__ void k_bounds_init(uint32_t* misc) {
 }
 
 constexpr int kStreamUnroll = 4;
+#ifndef PCR_MORTON_UNROLL
+#define PCR_MORTON_UNROLL 8
+#endif
+constexpr int kMortonUnroll = PCR_MORTON_UNROLL;  // divides kSortRounds
+static_assert(kSortRounds % kMortonUnroll == 0, "whole rounds of records per tile");
 
 // Per axis min and max over non-NaN coordinates.  -0 is folded into +0 (the
 // codes do not depend on the sign of a zero bound).  With `copy`, the records
@@ -279,16 +284,16 @@ __global__ void __launch_bounds__(kSortThreads) k_morton(const uint4* __restrict
   const float scale = degenerate ? 0.0f : __fdiv_rn(1024.0f, ext);
   const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
   const uint32_t valid = static_cast<uint32_t>(n - tile_base < kTile ? n - tile_base : kTile);
-  // kStreamUnroll records per thread in flight at a time
-  for (uint32_t j0 = threadIdx.x; j0 < valid; j0 += kSortThreads * kStreamUnroll) {
-    uint4 r[kStreamUnroll];
+  // kMortonUnroll records per thread in flight at a time
+  for (uint32_t j0 = threadIdx.x; j0 < valid; j0 += kSortThreads * kMortonUnroll) {
+    uint4 r[kMortonUnroll];
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) {
+    for (int u = 0; u < kMortonUnroll; ++u) {
       const uint32_t j = j0 + kSortThreads * u;
       r[u] = (!degenerate && j < valid) ? __ldcs(pts + tile_base + j) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) {
+    for (int u = 0; u < kMortonUnroll; ++u) {
       const uint32_t j = j0 + kSortThreads * u;
       if (j >= valid) break;
       uint32_t code = 0;

@@ -39,8 +39,8 @@ def test_reorder_matches_oracle(r, oracle, n):
 def test_reorder_scene_with_duplicates(r, oracle, n):
     """Scanline scene (many equal Morton codes: stability decides) at sizes
     spanning many sort tiles with a ragged tail; 5M points is 814 tiles, more
-    than the sort kernel keeps resident at once, so later tiles start only as
-    earlier ones finish and each tile's look-back meets every state."""
+    than the scatter kernel keeps resident at once (4 per SM), so tiles run
+    in several waves."""
     cloud = scenes.scan(n, seed=1).numpy()
     for mode in MODES:
         expect = oracle.reorder(cloud, 42, mode)
@@ -48,6 +48,20 @@ def test_reorder_scene_with_duplicates(r, oracle, n):
         perm = reorder_gpu(r.h, dev, 42, mode)
         assert np.array_equal(perm, expect), mode
     assert pcr.pcr_last_device_error(r.h) == 0
+
+
+@pytest.mark.parametrize("n", [129, 8193, 100_003])
+def test_reorder_without_permutation(r, oracle, n):
+    """Without a permutation output the last sort pass takes its other
+    record-moving loops; the records must be the same."""
+    cloud = scenes.random_cloud(n, seed=n + 3).numpy()
+    for mode in MODES:
+        expect = oracle.gather(cloud, oracle.reorder(cloud, 99, mode))
+        dev = torch.from_numpy(cloud.copy()).cuda()
+        ws = torch.empty(pcr.pcr_reorder_workspace_size(n), dtype=torch.uint8, device="cuda")
+        pcr.pcr_reorder_morton_shuffle128(r.h, dev, n, 99, mode, ws, None)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy(), expect), (n, mode)
 
 
 def test_reorder_degenerate_and_nonfinite(r, oracle):
