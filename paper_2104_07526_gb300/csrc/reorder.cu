@@ -1,16 +1,17 @@
 // Vertex-order kernels (Sec. 4, and the orderings listed in Sec. 5):
 // bounds, 30-bit and 63-bit Morton codes, a stable LSD radix sort of (32-bit
 // key, 32-bit index) pairs whose last pass moves the point records to their
-// final positions, and the 128-point batch shuffle.  A 63-bit code sorts as two 32-bit halves: the low half first
-// (the high half carried along), then the high half, both stable, which is a
-// stable sort by the whole code.
+// final positions, and the 128-point batch shuffle.  A 63-bit code sorts as
+// two 32-bit halves: the low half first (the high half carried along), then
+// the high half, both stable, which is a stable sort by the whole code.
 //
 // Radix sort: 8-bit digits, one pass per digit, three steps per pass:
-//   1. k_sort_hist: per tile of 6144 keys, count each digit (the first
+//   1. k_sort_hist: per tile of 6144 keys (5120 in the random shuffle,
+//      whose passes carry records), count each digit (the first
 //      pass's counts come from the kernel that made the keys);
 //   2. exclusive scan of the counts in digit-major order, which gives every
 //      (digit, tile) its first output slot;
-//   3. k_sort_scatter: each warp of a tile takes 768 consecutive keys and
+//   3. k_sort_scatter: each warp of a tile takes 768 (640) consecutive keys and
 //      counts their digits (per 32 keys, one match.any when their digits
 //      form few runs, else eight ballots, one per digit bit);
 //      one prefix over (digit, warp) then gives every warp its first slot
@@ -53,8 +54,15 @@ __device__ __forceinline__ bool debug_in_range(uint64_t i, uint64_t n) {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortRounds = 24;  // keys per lane in a tile
+constexpr int kSortRounds = 24;  // keys per lane in a tile (Morton codes, batch keys)
 constexpr uint32_t kTile = kSortThreads * kSortRounds;
+// The random shuffle's sort carries 16-byte records: tiles of 20 keys per
+// lane keep each block's record window smaller (800M shuffle 34.4 ms with
+// 24, 30.6 with 20, 30.9 with 16).
+constexpr int kShuffleRounds = 20;
+constexpr int kMinRounds = kShuffleRounds < kSortRounds ? kShuffleRounds : kSortRounds;
+template <int ROUNDS>
+constexpr uint32_t kTileOf = kSortThreads * ROUNDS;
 constexpr int kDigitBits = 8;
 constexpr int kRadix = 1 << kDigitBits;
 constexpr int kScanThreads = 256;
@@ -93,7 +101,7 @@ constexpr uint64_t region(uint64_t& off, uint64_t bytes) {
 
 constexpr Layout layout(uint64_t n) {
   const uint64_t nb = ceil_div(n, kBatch);
-  const uint64_t tiles = ceil_div(n > nb ? n : nb, kTile);
+  const uint64_t tiles = ceil_div(n > nb ? n : nb, kTileOf<kMinRounds>);  // the most any sort has
   const uint64_t count_words = kRadix * (tiles > 0 ? tiles : 1);
   Layout l{};
   uint64_t off = 0;
@@ -211,21 +219,23 @@ __device__ __forceinline__ uint32_t quantise(float v, float lo, float scale) {
 // shared memory, and counts them as k_sort_hist does (lane l of warp w takes
 // slots [768 w + 24 l, + 24) and adds each run of equal digits once), so the
 // first pass's histogram costs no second read of the keys.
+template <int ROUNDS>
 struct alignas(16) TileKeys {
-  uint32_t keys[kTile];  // read as 16-byte vectors by count_tile_digits
+  uint32_t keys[kTileOf<ROUNDS>];  // read as 16-byte vectors by count_tile_digits
   uint32_t hist[kSortWarps][kRadix];
 };
 
-__device__ __forceinline__ void count_tile_digits(TileKeys& sh, uint32_t valid, uint32_t* __restrict__ counts,
+template <int ROUNDS>
+__device__ __forceinline__ void count_tile_digits(TileKeys<ROUNDS>& sh, uint32_t valid, uint32_t* __restrict__ counts,
                                                   uint32_t tiles) {
   __syncthreads();  // the tile's keys are in place
   uint32_t* mine = sh.hist[threadIdx.x >> 5];
-  const uint32_t first = (threadIdx.x >> 5) * (kTile / kSortWarps) + lane_id() * kSortRounds;
+  const uint32_t first = (threadIdx.x >> 5) * (kTileOf<ROUNDS> / kSortWarps) + lane_id() * ROUNDS;
   uint32_t cur = 0, run = 0;
-  if (first + kSortRounds <= valid) {
+  if (first + ROUNDS <= valid) {
     const uint4* q = reinterpret_cast<const uint4*>(sh.keys + first);  // 96-byte aligned
 #pragma unroll
-    for (int k = 0; k < kSortRounds / 4; ++k) {
+    for (int k = 0; k < ROUNDS / 4; ++k) {
       const uint4 v = q[k];
       const uint32_t d[4] = {v.x & (kRadix - 1), v.y & (kRadix - 1), v.z & (kRadix - 1), v.w & (kRadix - 1)};
 #pragma unroll
@@ -240,7 +250,7 @@ __device__ __forceinline__ void count_tile_digits(TileKeys& sh, uint32_t valid, 
       }
     }
   } else {
-    for (uint32_t j = first; j < valid && j < first + kSortRounds; ++j) {
+    for (uint32_t j = first; j < valid && j < first + ROUNDS; ++j) {
       const uint32_t d = sh.keys[j] & (kRadix - 1);
       if (d == cur) {
         ++run;
@@ -259,7 +269,8 @@ __device__ __forceinline__ void count_tile_digits(TileKeys& sh, uint32_t valid, 
   counts[static_cast<uint64_t>(threadIdx.x) * tiles + blockIdx.x] = c;
 }
 
-__device__ __forceinline__ void zero_tile_hist(TileKeys& sh) {
+template <int ROUNDS>
+__device__ __forceinline__ void zero_tile_hist(TileKeys<ROUNDS>& sh) {
 #pragma unroll
   for (int w = 0; w < kSortWarps; ++w) sh.hist[w][threadIdx.x] = 0;
 }
@@ -271,7 +282,7 @@ __global__ void __launch_bounds__(kSortThreads) k_morton(const uint4* __restrict
                                                          const uint32_t* __restrict__ misc,
                                                          uint32_t* __restrict__ keys, uint32_t* __restrict__ counts,
                                                          uint32_t tiles) {
-  __shared__ TileKeys sh;
+  __shared__ TileKeys<kSortRounds> sh;
   zero_tile_hist(sh);
   const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
   const float hi[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
@@ -333,7 +344,7 @@ __global__ void __launch_bounds__(kSortThreads) k_morton63(const uint4* __restri
                                                            const uint32_t* __restrict__ misc,
                                                            uint32_t* __restrict__ keys_lo, uint32_t* __restrict__ hi,
                                                            uint32_t* __restrict__ counts, uint32_t tiles) {
-  __shared__ TileKeys sh;
+  __shared__ TileKeys<kSortRounds> sh;
   zero_tile_hist(sh);
   const float lo[3] = {order_float(misc[0]), order_float(misc[1]), order_float(misc[2])};
   const float top[3] = {order_float(misc[3]), order_float(misc[4]), order_float(misc[5])};
@@ -372,13 +383,15 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t k) {
 
 // Keys for the random orders: the high half of SplitMix64 output i, with the
 // first sort pass's digit counts.
+template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads) k_random_keys(uint32_t count, uint64_t seed,
                                                               uint32_t* __restrict__ keys,
                                                               uint32_t* __restrict__ counts, uint32_t tiles) {
-  __shared__ TileKeys sh;
+  __shared__ TileKeys<ROUNDS> sh;
   zero_tile_hist(sh);
-  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
-  const uint32_t valid = static_cast<uint32_t>(count - tile_base < kTile ? count - tile_base : kTile);
+  constexpr uint32_t kT = kTileOf<ROUNDS>;
+  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kT;
+  const uint32_t valid = static_cast<uint32_t>(count - tile_base < kT ? count - tile_base : kT);
   for (uint32_t j = threadIdx.x; j < valid; j += kSortThreads) {
     const uint32_t key = static_cast<uint32_t>(splitmix64(seed, tile_base + j) >> 32);
     keys[tile_base + j] = key;
@@ -408,7 +421,6 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid) {
   return peers;
 }
 
-constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 768 = kSortRounds x 32
 
 // Per tile, the count of each digit.  Lane l of each warp counts keys
 // [24l, 24l + 24) of the warp's 768 (six 16-byte loads) and adds a run of
@@ -417,6 +429,7 @@ constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;  // 768 = kSortRounds x 32
 // the lower digits) have long runs, which one add per key would turn into
 // many same-address shared-memory atomics.  The eight warps' counters are
 // summed at the end.
+template <int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __restrict__ keys, uint32_t n, int shift,
                                                             uint32_t* __restrict__ counts, uint32_t tiles) {
   __shared__ uint32_t hist[kSortWarps][kRadix];
@@ -424,8 +437,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
   for (int w = 0; w < kSortWarps; ++w) hist[w][threadIdx.x] = 0;
   __syncthreads();
   uint32_t* mine = hist[threadIdx.x >> 5];
-  const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kTile + (threadIdx.x >> 5) * kKeysPerWarp +
-                         lane_id() * kSortRounds;
+  const uint64_t first = static_cast<uint64_t>(blockIdx.x) * kTileOf<ROUNDS> +
+                         (threadIdx.x >> 5) * (kTileOf<ROUNDS> / kSortWarps) + lane_id() * ROUNDS;
   uint32_t cur = 0, run = 0;
   auto count = [&](uint32_t key) {
     const uint32_t d = (key >> shift) & (kRadix - 1);
@@ -437,20 +450,20 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
       run = 1;
     }
   };
-  if (first + kSortRounds <= n) {
+  if (first + ROUNDS <= n) {
     const uint4* q = reinterpret_cast<const uint4*>(keys + first);  // 128-byte aligned
-    uint4 v[kSortRounds / 4];
+    uint4 v[ROUNDS / 4];
 #pragma unroll
-    for (int k = 0; k < kSortRounds / 4; ++k) v[k] = __ldg(q + k);
+    for (int k = 0; k < ROUNDS / 4; ++k) v[k] = __ldg(q + k);
 #pragma unroll
-    for (int k = 0; k < kSortRounds / 4; ++k) {
+    for (int k = 0; k < ROUNDS / 4; ++k) {
       count(v[k].x);
       count(v[k].y);
       count(v[k].z);
       count(v[k].w);
     }
   } else {
-    for (uint64_t i = first; i < n && i < first + kSortRounds; ++i) count(__ldg(keys + i));
+    for (uint64_t i = first; i < n && i < first + ROUNDS; ++i) count(__ldg(keys + i));
   }
   if (run) atomicAdd(&mine[cur], run);
   __syncthreads();
@@ -468,8 +481,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
 // output slot's input slot, the per-warp first slot of each digit, and per
 // digit the output position minus the tile slot of its first key.  45 KB:
 // four blocks per SM.
-constexpr size_t kScatterSmem =
-    sizeof(uint32_t) * kTile + sizeof(uint16_t) * kTile + sizeof(uint32_t) * (kSortWarps * kRadix + kRadix);
+template <int ROUNDS>
+constexpr size_t scatter_smem() {
+  return sizeof(uint32_t) * kTileOf<ROUNDS> + sizeof(uint16_t) * kTileOf<ROUNDS> +
+         sizeof(uint32_t) * (kSortWarps * kRadix + kRadix);
+}
 
 // 16-byte asynchronous copy global -> shared (cp.async, completes on
 // cp.async.wait_all); `bytes` < 16 reads only that many and zero-fills.
@@ -503,7 +519,7 @@ struct FinalGather {
 // order sorts the records themselves: every pass reads them in tile order and
 // writes them in digit runs, instead of one random gather at the end).  With
 // `fin.src` the records move as FinalGather says, and `vout` is not written.
-template <bool REC>
+template <bool REC, int ROUNDS>
 __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t* __restrict__ kin,
                                                                   const uint32_t* __restrict__ vin,
                                                                   uint32_t* __restrict__ kout,
@@ -513,6 +529,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
                                                                   uint32_t* __restrict__ cout,
                                                                   const uint4* __restrict__ rin,
                                                                   uint4* __restrict__ rout, FinalGather fin) {
+  constexpr uint32_t kTile = kTileOf<ROUNDS>;
+  constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;
   extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
   uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
@@ -540,13 +558,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   const uint32_t wfirst = warp * kKeysPerWarp;
   uint32_t* mine = wbase + warp * kRadix;
   const uint32_t below = (1u << lane) - 1u;
-  uint32_t info[kSortRounds];
+  uint32_t info[ROUNDS];
   // a full tile (every tile but a cloud's last) needs no test of which keys
   // lie inside the cloud
   auto rank_keys = [&](auto full) {
     constexpr bool kFull = decltype(full)::value;
 #pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
       const uint32_t j = wfirst + r * 32 + lane;
       const bool ok = kFull || j < valid;
       const uint32_t d = ok ? (s_kin[j] >> shift) & (kRadix - 1) : 0u;
@@ -583,7 +601,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
   auto place_keys = [&](auto full) {
     constexpr bool kFull = decltype(full)::value;
 #pragma unroll
-    for (int r = 0; r < kSortRounds; ++r) {
+    for (int r = 0; r < ROUNDS; ++r) {
       const uint32_t v = info[r];
       const bool ok = kFull || (v >> 31) != 0u;
       const uint32_t d = (v >> 16) & (kRadix - 1);
@@ -605,7 +623,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
 #endif
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
-  // output positions; values are gathered from the tile's 24 KB window.  One
+  // output positions; values are gathered from the tile's window.  One
   // loop per combination of what moves with the keys, chosen once, so each
   // unrolled loop carries no per-key test.
   auto write_out = [&](auto values, auto carried, auto keys, auto gather, auto perm) {
@@ -833,30 +851,32 @@ cudaError_t exclusive_scan(uint32_t* a, uint64_t len, uint32_t* partials, cudaSt
 // has already written the first pass's digit counts (k_morton, k_morton63,
 // k_random_keys).  With `fin` (may be null) the last pass moves the records
 // as FinalGather says, instead of writing the values.
+template <int ROUNDS>
 cudaError_t radix_sort(uint32_t* keys[2], uint32_t* vals[2], uint32_t count, int key_bits, uint32_t* counts,
                        uint32_t* partials, cudaStream_t s, int& out, bool index_values, bool first_counted,
                        uint32_t* const* carry = nullptr, uint32_t* carry_last = nullptr,
                        uint4* const* recs = nullptr, const FinalGather* fin = nullptr) {
   out = 0;
   if (count == 0) return cudaSuccess;
-  const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTile));
-  cudaError_t e = cudaFuncSetAttribute(recs ? k_sort_scatter<true> : k_sort_scatter<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kScatterSmem));
+  constexpr size_t kSmem = scatter_smem<ROUNDS>();
+  const uint32_t tiles = static_cast<uint32_t>(ceil_div(count, kTileOf<ROUNDS>));
+  cudaError_t e = cudaFuncSetAttribute(recs ? k_sort_scatter<true, ROUNDS> : k_sort_scatter<false, ROUNDS>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmem));
   if (e != cudaSuccess) return e;
   for (int shift = 0; shift < key_bits; shift += kDigitBits) {
     const bool last = shift + kDigitBits >= key_bits;
-    if (!(first_counted && shift == 0)) k_sort_hist<<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
+    if (!(first_counted && shift == 0)) k_sort_hist<ROUNDS><<<tiles, kSortThreads, 0, s>>>(keys[out], count, shift, counts, tiles);
     e = exclusive_scan(counts, static_cast<uint64_t>(kRadix) * tiles, partials, s);
     if (e != cudaSuccess) return e;
     const uint32_t* vin = (index_values && shift == 0) ? nullptr : vals[out];
     uint32_t* kout = last ? nullptr : keys[out ^ 1];
     const FinalGather f = (last && fin) ? *fin : FinalGather{};
     if (recs)
-      k_sort_scatter<true><<<tiles, kSortThreads, kScatterSmem, s>>>(
+      k_sort_scatter<true, ROUNDS><<<tiles, kSortThreads, kSmem, s>>>(
           keys[out], vin, kout, vals[out ^ 1], count, shift, counts, tiles, nullptr, nullptr, recs[out],
           recs[out ^ 1], f);
     else
-      k_sort_scatter<false><<<tiles, kSortThreads, kScatterSmem, s>>>(
+      k_sort_scatter<false, ROUNDS><<<tiles, kSortThreads, kSmem, s>>>(
           keys[out], vin, kout, vals[out ^ 1], count, shift, counts, tiles, carry ? carry[out] : nullptr,
           carry ? (last && carry_last ? carry_last : carry[out ^ 1]) : nullptr, nullptr, nullptr, f);
     e = cudaGetLastError();
@@ -945,10 +965,11 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     // the records themselves are sorted by their random keys (4 passes, an
     // even number: they end back in the caller's buffer); indices ride along
     // only when the permutation is asked for
-    k_random_keys<<<tiles, kSortThreads, 0, s>>>(n, seed, keys[0], counts, tiles);
+    const uint32_t stiles = static_cast<uint32_t>(ceil_div(n, kTileOf<kShuffleRounds>));
+    k_random_keys<kShuffleRounds><<<stiles, kSortThreads, 0, s>>>(n, seed, keys[0], counts, stiles);
     uint32_t* ivals[2] = {perm_out ? vals[0] : nullptr, perm_out ? vals[1] : nullptr};
     uint4* recs[2] = {pts, copy};
-    e = radix_sort(keys, ivals, n, 32, counts, partials, s, out, true, true, nullptr, nullptr, recs);
+    e = radix_sort<kShuffleRounds>(keys, ivals, n, 32, counts, partials, s, out, true, true, nullptr, nullptr, recs);
     if (e != cudaSuccess) return e;
     if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes
     if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
@@ -966,9 +987,9 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
     uint32_t* bkeys[2] = {reinterpret_cast<uint32_t*>(ws + l.bkeys0), reinterpret_cast<uint32_t*>(ws + l.bkeys1)};
     uint32_t* bvals[2] = {reinterpret_cast<uint32_t*>(ws + l.bvals0), reinterpret_cast<uint32_t*>(ws + l.bvals1)};
     const uint32_t btiles = static_cast<uint32_t>(ceil_div(nb, kTile));
-    k_random_keys<<<btiles, kSortThreads, 0, s>>>(nb, seed, bkeys[0], counts, btiles);
+    k_random_keys<kSortRounds><<<btiles, kSortThreads, 0, s>>>(nb, seed, bkeys[0], counts, btiles);
     int bout = 0;
-    e = radix_sort(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
+    e = radix_sort<kSortRounds>(bkeys, bvals, nb, 32, counts, partials, s, bout, true, true);
     if (e != cudaSuccess) return e;
     k_batch_rank<<<stream_grid(nb, d), 256, 0, s>>>(bvals[bout], nb, bkeys[0]);
     fin.rank = bkeys[0];
@@ -978,7 +999,8 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   if (mode == PCR_ORDER_MORTON || mode == PCR_ORDER_MORTON_SHUFFLE128) {
     k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, copy);
     k_morton<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], counts, tiles);
-    e = radix_sort(keys, vals, n, 30, counts, partials, s, out, true, true, nullptr, nullptr, nullptr, &fin);
+    e = radix_sort<kSortRounds>(keys, vals, n, 30, counts, partials, s, out, true, true, nullptr, nullptr, nullptr,
+                                &fin);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
   }
@@ -992,11 +1014,12 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   k_bounds<<<grid, 256, 0, s>>>(pts, n, misc, nullptr);
   k_morton63<<<tiles, kSortThreads, 0, s>>>(pts, n, misc, keys[0], hi[0], counts, tiles);
   int a = 0;
-  e = radix_sort(keys, vals, n, 32, counts, partials, s, a, true, true, hi, keys[0]);
+  e = radix_sort<kSortRounds>(keys, vals, n, 32, counts, partials, s, a, true, true, hi, keys[0]);
   if (e != cudaSuccess) return e;
   if (a != 0) return cudaErrorUnknown;  // 4 passes: the values are in vals[0]
   k_copy16<<<grid, 256, 0, s>>>(pts, copy, n);
-  e = radix_sort(keys, vals, n, 31, counts, partials, s, out, false, false, nullptr, nullptr, nullptr, &fin);
+  e = radix_sort<kSortRounds>(keys, vals, n, 31, counts, partials, s, out, false, false, nullptr, nullptr, nullptr,
+                              &fin);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

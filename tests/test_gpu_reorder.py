@@ -23,7 +23,8 @@ def r():
     rend.close()
 
 
-@pytest.mark.parametrize("n", [0, 1, 2, 127, 128, 129, 1000, 6143, 6144, 6145, 8191, 8192, 8193, 12289, 100_003])
+@pytest.mark.parametrize("n", [0, 1, 2, 127, 128, 129, 1000, 5119, 5120, 5121, 6143, 6144, 6145, 8191, 8192, 8193,
+                               10241, 12289, 100_003])
 def test_reorder_matches_oracle(r, oracle, n):
     cloud = scenes.random_cloud(n, seed=n + 7).numpy() if n else np.zeros((0, 4), np.int32)
     for mode in MODES:
