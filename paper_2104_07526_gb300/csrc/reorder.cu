@@ -77,12 +77,8 @@ constexpr uint32_t kBatch = 128;  // Sec. 4: batches of 128 points
 #endif
 constexpr int kGatherUnroll = PCR_GATHER_UNROLL;
 
-// Full tiles take ranking and placement loops without the in-cloud tests.
-#ifndef PCR_FULL_TILES
-#define PCR_FULL_TILES 1
-#endif
-
 static_assert(kRadix == kSortThreads, "one digit per thread in the sort kernels");
+static_assert(kSortRounds % 4 == 0 && kShuffleRounds % 4 == 0, "keys per lane read as 16-byte vectors");
 
 constexpr uint64_t align_up(uint64_t v) { return (v + 255) & ~uint64_t(255); }
 
@@ -216,9 +212,10 @@ __device__ __forceinline__ uint32_t quantise(float v, float lo, float scale) {
 // The kernels that make the keys also count the first sort pass's digits:
 // one block per tile of kTile keys makes the tile's keys (thread t takes
 // tile slots t, t + 256, ..., so loads and stores coalesce), keeps them in
-// shared memory, and counts them as k_sort_hist does (lane l of warp w takes
-// slots [768 w + 24 l, + 24) and adds each run of equal digits once), so the
-// first pass's histogram costs no second read of the keys.
+// shared memory, and counts them as k_sort_hist does (with R keys per lane,
+// lane l of warp w takes slots [32 R w + R l, + R) and adds each run of
+// equal digits once), so the first pass's histogram costs no second read of
+// the keys.
 template <int ROUNDS>
 struct alignas(16) TileKeys {
   uint32_t keys[kTileOf<ROUNDS>];  // read as 16-byte vectors by count_tile_digits
@@ -233,7 +230,7 @@ __device__ __forceinline__ void count_tile_digits(TileKeys<ROUNDS>& sh, uint32_t
   const uint32_t first = (threadIdx.x >> 5) * (kTileOf<ROUNDS> / kSortWarps) + lane_id() * ROUNDS;
   uint32_t cur = 0, run = 0;
   if (first + ROUNDS <= valid) {
-    const uint4* q = reinterpret_cast<const uint4*>(sh.keys + first);  // 96-byte aligned
+    const uint4* q = reinterpret_cast<const uint4*>(sh.keys + first);  // 16-byte aligned: 4 | ROUNDS
 #pragma unroll
     for (int k = 0; k < ROUNDS / 4; ++k) {
       const uint4 v = q[k];
@@ -421,10 +418,10 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid) {
   return peers;
 }
 
-
-// Per tile, the count of each digit.  Lane l of each warp counts keys
-// [24l, 24l + 24) of the warp's 768 (six 16-byte loads) and adds a run of
-// equal digits to its warp's counters once, when the digit changes.
+// Per tile, the count of each digit.  With R keys per lane, lane l of each
+// warp counts keys [R l, R l + R) of the warp's 32 R (16-byte loads) and
+// adds a run of equal digits to its warp's counters once, when the digit
+// changes.
 // Coherent orders (and the passes after the first, whose input is sorted on
 // the lower digits) have long runs, which one add per key would turn into
 // many same-address shared-memory atomics.  The eight warps' counters are
@@ -451,7 +448,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const uint32_t* __re
     }
   };
   if (first + ROUNDS <= n) {
-    const uint4* q = reinterpret_cast<const uint4*>(keys + first);  // 128-byte aligned
+    const uint4* q = reinterpret_cast<const uint4*>(keys + first);  // 16-byte aligned: 4 | ROUNDS
     uint4 v[ROUNDS / 4];
 #pragma unroll
     for (int k = 0; k < ROUNDS / 4; ++k) v[k] = __ldg(q + k);
@@ -479,8 +476,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& t
 
 // Dynamic shared memory of k_sort_scatter: the tile's keys as loaded, each
 // output slot's input slot, the per-warp first slot of each digit, and per
-// digit the output position minus the tile slot of its first key.  45 KB:
-// four blocks per SM.
+// digit the output position minus the tile slot of its first key.  45 KB for
+// 24 keys per lane, 38 KB for 20: four blocks per SM either way.
 template <int ROUNDS>
 constexpr size_t scatter_smem() {
   return sizeof(uint32_t) * kTileOf<ROUNDS> + sizeof(uint16_t) * kTileOf<ROUNDS> +
@@ -575,12 +572,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
       __syncwarp();
     }
   };
-#if PCR_FULL_TILES
   if (valid == kTile) rank_keys(std::true_type{});
   else rank_keys(std::false_type{});
-#else
-  rank_keys(std::false_type{});
-#endif
   __syncthreads();
   // digit t: first slot of each warp's keys within the digit, then the
   // digit's first slot within the tile
@@ -615,12 +608,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
       __syncwarp();
     }
   };
-#if PCR_FULL_TILES
   if (valid == kTile) place_keys(std::true_type{});
   else place_keys(std::false_type{});
-#else
-  place_keys(std::false_type{});
-#endif
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
   // output positions; values are gathered from the tile's window.  One
