@@ -299,7 +299,9 @@ PCR_API pcr_status pcr_reorder_workspace_size(uint64_t n, uint64_t *bytes);
  *     over the PCR_ORDER_MORTON63 order.
  * dev_points: n records, 16-byte aligned.  dev_workspace: at least the
  * pcr_reorder_workspace_size bytes, 256-byte aligned; its contents are
- * scratch.  dev_perm_out: NULL or uint32[n], receives perm[new] = old.
+ * scratch.  dev_perm_out: NULL or uint32[n] (overlapping neither the points
+ * nor the workspace; the call may also use it as scratch before it writes
+ * the result), receives perm[new] = old.
  * Errors: PCR_ERR_ARG for a bad mode, pointer or n; PCR_ERR_WORKSPACE if
  * workspace_bytes is too small or the workspace is NULL. */
 PCR_API pcr_status pcr_reorder_morton_shuffle128(pcr_ctx *ctx, void *dev_points, uint64_t n, uint64_t seed, int mode,

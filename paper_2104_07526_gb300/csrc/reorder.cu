@@ -953,16 +953,16 @@ cudaError_t launch_reorder(uint4* pts, uint32_t n, uint64_t seed, int mode, void
   if (mode == PCR_ORDER_SHUFFLE) {
     // the records themselves are sorted by their random keys (4 passes, an
     // even number: they end back in the caller's buffer); indices ride along
-    // only when the permutation is asked for
+    // only when the permutation is asked for, with the caller's buffer as
+    // the value buffer the last pass writes
     const uint32_t stiles = static_cast<uint32_t>(ceil_div(n, kTileOf<kShuffleRounds>));
     k_random_keys<kShuffleRounds><<<stiles, kSortThreads, 0, s>>>(n, seed, keys[0], counts, stiles);
-    uint32_t* ivals[2] = {perm_out ? vals[0] : nullptr, perm_out ? vals[1] : nullptr};
+    uint32_t* ivals[2] = {perm_out, perm_out ? vals[1] : nullptr};
     uint4* recs[2] = {pts, copy};
     e = radix_sort<kShuffleRounds>(keys, ivals, n, 32, counts, partials, s, out, true, true, nullptr, nullptr, recs);
     if (e != cudaSuccess) return e;
-    if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes
-    if (perm_out) e = cudaMemcpyAsync(perm_out, vals[out], 4ull * n, cudaMemcpyDeviceToDevice, s);
-    return e;
+    if (out != 0) return cudaErrorUnknown;  // 32-bit keys take 4 passes: the values end in ivals[0]
+    return cudaSuccess;
   }
   // The sort's last pass moves the records from their copy to their final
   // positions: the sorted positions, or with the batch shuffle, the slots of
