@@ -526,18 +526,18 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
                                                                   uint32_t* __restrict__ cout,
                                                                   const uint4* __restrict__ rin,
                                                                   uint4* __restrict__ rout, FinalGather fin) {
-  constexpr uint32_t kTile = kTileOf<ROUNDS>;
-  constexpr uint32_t kKeysPerWarp = kTile / kSortWarps;
+  constexpr uint32_t kT = kTileOf<ROUNDS>;  // keys in a tile
+  constexpr uint32_t kKeysPerWarp = kT / kSortWarps;
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* s_kin = smem;                                           // [kTile] the tile's keys
-  uint32_t* wbase = s_kin + kTile;                                  // [kSortWarps][kRadix]
-  uint32_t* delta = wbase + kSortWarps * kRadix;                    // [kRadix]
-  uint16_t* s_src = reinterpret_cast<uint16_t*>(delta + kRadix);    // [kTile]
+  uint32_t* s_kin = smem;                                         // [kT] the tile's keys
+  uint32_t* wbase = s_kin + kT;                                   // [kSortWarps][kRadix]
+  uint32_t* delta = wbase + kSortWarps * kRadix;                  // [kRadix]
+  uint16_t* s_src = reinterpret_cast<uint16_t*>(delta + kRadix);  // [kT]
   const uint32_t t = threadIdx.x;
   const uint32_t lane = lane_id();
   const uint32_t warp = t >> 5;
-  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kTile;
-  const uint32_t valid = static_cast<uint32_t>(n - tile_base < kTile ? n - tile_base : kTile);
+  const uint64_t tile_base = static_cast<uint64_t>(blockIdx.x) * kT;
+  const uint32_t valid = static_cast<uint32_t>(n - tile_base < kT ? n - tile_base : kT);
   for (uint32_t c = t; c * 4 < valid; c += kSortThreads) {
     const uint32_t left = valid - 4 * c;
     copy16_async(s_kin + 4 * c, kin + tile_base + 4ull * c, left >= 4 ? 16u : 4 * left);
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
       __syncwarp();
     }
   };
-  if (valid == kTile) rank_keys(std::true_type{});
+  if (valid == kT) rank_keys(std::true_type{});
   else rank_keys(std::false_type{});
   __syncthreads();
   // digit t: first slot of each warp's keys within the digit, then the
@@ -601,14 +601,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_scatter(const uint32_t
       const uint32_t rank = v & 0xFFu;
       const uint32_t at = ok ? mine[d] : 0u;
       __syncwarp();
-      if (ok && debug_in_range(at + rank, kTile)) {
+      if (ok && debug_in_range(at + rank, kT)) {
         s_src[at + rank] = static_cast<uint16_t>(wfirst + r * 32 + lane);
         if (rank == 0) mine[d] = at + ((v >> 8) & 0xFFu);
       }
       __syncwarp();
     }
   };
-  if (valid == kTile) place_keys(std::true_type{});
+  if (valid == kT) place_keys(std::true_type{});
   else place_keys(std::false_type{});
   __syncthreads();
   // the tile in digit order: consecutive slots of a digit go to consecutive
