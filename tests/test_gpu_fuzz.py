@@ -5,13 +5,13 @@ arbitrary 4x4 matrices of random scale, so w ranges over many binades, takes
 both signs and lands outside the projection's fast reciprocal window) and
 random viewports.  Every exact basic variant, the colour-payload keys, the
 HQ buffers (two depth factors), HQS1R's channel sums and the resolves are
-compared with the oracle's."""
+compared with the oracle's; so are all five vertex orders of random clouds."""
 import numpy as np
 import pytest
 import torch
 
 import constructed as cs
-from gpu_helpers import Renderer
+from gpu_helpers import Renderer, reorder_gpu
 from paper_2104_07526_gb300 import pcr, scenes
 
 pytestmark = pytest.mark.gpu
@@ -96,3 +96,23 @@ def test_random_clouds_cameras_viewports(r, oracle, seed):
         assert np.array_equal(d, e[0]), seed
         for a, b in zip(parts, sums):
             assert np.array_equal(a, b), (seed, factor)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_random_reorders(r, oracle, seed):
+    """Every vertex order on random clouds of random size (tails of both tile
+    sizes, 5120 and 6144 keys, and of the 128-point batches), special
+    coordinates and degenerate extents included: permutation and records
+    against the oracle."""
+    rng = np.random.default_rng(2000 + seed)
+    cloud = random_cloud(rng)
+    if seed % 4 == 3:  # every bulk point on one spot: a zero extent
+        bulk = (np.abs(cloud[:, :3].view(np.float32)) < 1e29).all(axis=1)
+        cloud[bulk, :3] = cloud[np.argmax(bulk), :3]
+    order_seed = int(rng.integers(0, 2 ** 63))
+    for mode in (pcr.PCR_ORDER_MORTON, pcr.PCR_ORDER_MORTON_SHUFFLE128, pcr.PCR_ORDER_SHUFFLE,
+                 pcr.PCR_ORDER_MORTON63, pcr.PCR_ORDER_MORTON63_SHUFFLE128):
+        expect = oracle.reorder(cloud, order_seed, mode)
+        dev = torch.from_numpy(cloud.copy()).cuda()
+        assert np.array_equal(reorder_gpu(r.h, dev, order_seed, mode), expect), (seed, mode)
+        assert np.array_equal(dev.cpu().numpy(), oracle.gather(cloud, expect)), (seed, mode)
