@@ -9,6 +9,7 @@ import torch
 import constructed as cs
 from gpu_helpers import ensure_built
 from paper_2104_07526_gb300 import pcr, scenes
+from random_inputs import random_cloud, random_matrix
 
 pytestmark = pytest.mark.gpu
 
@@ -256,3 +257,33 @@ def test_batch_tune_chooses_and_caches(ctx, oracle, tmp_path):
     # another shape misses the cache
     other = pcr.pcr_batch_tune(ctx, cs_, vs[:3], 1.01, BG, ws, cache)
     assert other["from_cache"] == 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_batch_random_descriptions(ctx, oracle, seed):
+    """Seeded random batches: 1-6 clouds of 0-20000 points, 1-24 views with
+    random clouds, flags, cameras and sizes (a few large enough that a
+    cloud's views need several passes, and clouds with a single view, which
+    take the single-view kernels), in a random launch configuration; every
+    buffer of every view against the oracle."""
+    rng = np.random.default_rng(3000 + seed)
+    clouds = []
+    for _ in range(int(rng.integers(1, 7))):
+        c = random_cloud(rng)
+        clouds.append(c[: int(rng.integers(0, c.shape[0] + 1))] if rng.random() < 0.2 else c)
+    views = []
+    for _ in range(int(rng.integers(1, 25))):
+        c = int(rng.integers(0, len(clouds)))
+        if rng.random() < 0.15:
+            W, H = int(rng.integers(1500, 2600)), int(rng.integers(1500, 2600))
+        else:
+            W, H = int(rng.integers(1, 200)), int(rng.integers(1, 200))
+        flags = (BASIC, HQ, BASIC | HQ)[int(rng.integers(0, 3))]
+        cloud = clouds[c] if clouds[c].shape[0] else np.zeros((1, 4), np.int32)
+        views.append((c, random_matrix(rng, cloud, W, H), W, H, flags))
+    expected = _expected(oracle, clouds, views)
+    dev, bufs, ws = _prepare(ctx, clouds, views)
+    config = int(rng.integers(0, pcr.pcr_batch_num_configs()))
+    _poison(bufs)
+    pcr.pcr_batch_launch(ctx, ws, config)
+    _check(bufs, expected, f"seed {seed} config {config}")
