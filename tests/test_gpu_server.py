@@ -12,6 +12,7 @@ import torch
 import constructed as cs
 from gpu_helpers import ensure_built
 from paper_2104_07526_gb300 import pcr, scenes
+from random_inputs import random_cloud, random_matrix
 
 pytestmark = pytest.mark.gpu
 
@@ -439,5 +440,59 @@ def test_cancel_queued_requests(ctx, oracle):
             pcr.pcr_server_release(srv, t)
         st = pcr.pcr_server_stats_get(srv)
         assert st["cancelled"] == 1 and st["completed"] == 2 and st["queued"] == 0
+    finally:
+        pcr.pcr_server_destroy(srv)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_request_streams(ctx, oracle, seed):
+    """Seeded random servers (slots, batch size, batches in flight, streams,
+    clouds per batch, launch configuration, policy, L2 budget, an arena that
+    sometimes holds only some of the clouds) serving random request streams
+    over random clouds (special coordinates included) with random cameras,
+    sizes and flags, submitted in waves: every result against the oracle."""
+    rng = np.random.default_rng(4000 + seed)
+    clouds = [random_cloud(rng) for _ in range(int(rng.integers(2, 6)))]
+    max_w, max_h = int(rng.integers(8, 160)), int(rng.integers(8, 120))
+    slots = int(rng.integers(2, 10))
+    inflight = int(rng.integers(1, 4))
+    align = lambda b: (b + 255) // 256 * 256  # noqa: E731
+    px = max_w * max_h
+    slot_bytes = 3 * align(8 * px) + 3 * align(4 * px)
+    ws = align(pcr.pcr_batch_workspace_size())
+    biggest = max(align(c.nbytes) for c in clouds)
+    room = int(rng.integers(2, len(clouds) + 1)) * biggest + 1024
+    arena = torch.empty(slots * slot_bytes + inflight * ws + room, dtype=torch.uint8, device="cuda")
+    srv = pcr.pcr_server_create(ctx, arena, max_w, max_h, num_slots=slots,
+                                max_batch_views=int(rng.integers(1, 9)), max_inflight=inflight,
+                                streams=int(rng.integers(1, inflight + 1)),
+                                max_batch_clouds=int(rng.integers(0, 3)),
+                                batch_config=int(rng.integers(0, pcr.pcr_batch_num_configs())),
+                                background_rgba=BG, policy=int(rng.integers(0, 2)),
+                                l2_budget_mb=int(rng.choice([0, 1, 64, 1024])))
+    try:
+        for i, c in enumerate(clouds):
+            pcr.pcr_server_add_cloud(srv, 100 + i, np.ascontiguousarray(c))
+        by_ticket = {}
+
+        def finish(t):
+            c, m, W, H, flags = by_ticket.pop(t)
+            _check_result(ctx, srv, t, clouds[c], m, W, H, flags, oracle)
+            pcr.pcr_server_release(srv, t)
+
+        tickets = []
+        for i in range(int(rng.integers(10, 40))):
+            c = int(rng.integers(0, len(clouds)))
+            W, H = int(rng.integers(1, max_w + 1)), int(rng.integers(1, max_h + 1))
+            flags = int(rng.choice([BASIC, HQ, BASIC | HQ]))
+            m = random_matrix(rng, clouds[c], W, H)
+            t = pcr.pcr_server_submit(srv, 100 + c, m, W, H, flags)
+            by_ticket[t] = (c, m, W, H, flags)
+            tickets.append(t)
+            if rng.random() < 0.3:
+                pcr.pcr_server_step(srv)
+        _drain(srv, tickets, finish)
+        assert not by_ticket
+        assert pcr.pcr_server_stats_get(srv)["completed"] == len(tickets)
     finally:
         pcr.pcr_server_destroy(srv)
